@@ -1,0 +1,335 @@
+"""Seeded synthetic active-space Hamiltonians shared by the oracle, the tests and the bench.
+
+This module only *builds inputs*: one-electron integrals h_pq, two-electron
+integrals (pq|rs) in chemists' notation with exact 8-fold symmetry, the core
+energy and the electron counts.  It contains none of the HCI arithmetic
+(no Slater-Condon rules, no selection, no eigensolver on determinants), so
+both the CPU oracle and the CUDA path may consume it.
+
+The paper's own workloads (pentacene and Fe-porphyrin active spaces with
+cc-pVDZ integrals, Sec. V.B and V.C) need basis sets and a quantum-chemistry
+package that are not available, so they are stood in for by:
+
+* Pariser-Parr-Pople (PPP) pi-Hamiltonians of an 8-site polyene and of a
+  pentacene-shaped 22-site lattice (the (22e,22o) pi space of Sec. V.B),
+  transformed to the Hueckel MO basis;
+* density-fitted random Hamiltonians (pq|rs) = sum_P B^P_pq B^P_rs with an
+  orbital-energy ladder, sized like the (44e,44o) Fe(P) space of Sec. V.C.
+
+All arrays are float64 numpy arrays; eri has shape (n, n, n, n) indexed
+[p, q, r, s] = (pq|rs).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+EV_TO_HA = 1.0 / 27.211386245988
+PPP_T_EV = -2.4          # hopping at the 1.40 A reference bond length
+PPP_U_EV = 11.13         # on-site repulsion
+OHNO_E2_EV_A = 14.397    # e^2/(4 pi eps0) in eV*Angstrom
+REF_BOND_A = 1.40
+
+
+@dataclasses.dataclass
+class Instance:
+    """One active-space problem: H = sum h_pq E_pq + 1/2 sum (pq|rs) e_pqrs + e_core."""
+    name: str
+    norb: int
+    nalpha: int
+    nbeta: int
+    h: np.ndarray          # (n, n) float64, symmetric
+    eri: np.ndarray        # (n, n, n, n) float64, 8-fold symmetric
+    e_core: float = 0.0
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def nelec(self) -> int:
+        return self.nalpha + self.nbeta
+
+
+# ----------------------------------------------------------------------------
+# symmetry helpers (pure input conditioning)
+# ----------------------------------------------------------------------------
+
+def symmetrize_eri(eri: np.ndarray) -> np.ndarray:
+    """Average over the 8 index permutations of real (pq|rs) so that every
+    permutation of the same integral is bit-identical."""
+    e = eri
+    e = 0.5 * (e + e.transpose(1, 0, 2, 3))
+    e = 0.5 * (e + e.transpose(0, 1, 3, 2))
+    e = 0.5 * (e + e.transpose(2, 3, 0, 1))
+    # make the stored values exactly equal across the orbit (averaging in
+    # floating point can leave last-bit differences)
+    out = np.array(e, copy=True)
+    n = e.shape[0]
+    idx = np.indices((n, n, n, n)).reshape(4, -1).T
+    p, q, r, s = idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]
+    a = np.minimum(p, q); b = np.maximum(p, q)
+    c = np.minimum(r, s); d = np.maximum(r, s)
+    ab = a * n + b; cd = c * n + d
+    swap = ab > cd
+    a2 = np.where(swap, c, a); b2 = np.where(swap, d, b)
+    c2 = np.where(swap, a, c); d2 = np.where(swap, b, d)
+    out[p, q, r, s] = e[a2, b2, c2, d2]
+    return out
+
+
+def symmetrize_h(h: np.ndarray) -> np.ndarray:
+    h = 0.5 * (h + h.T)
+    iu = np.triu_indices(h.shape[0], 1)
+    h = np.array(h, copy=True)
+    h[(iu[1], iu[0])] = h[iu]
+    return h
+
+
+def canonical_eigh(m: np.ndarray, degen_tol: float = 1e-9):
+    """Eigen-decomposition with a basis that does not depend on the LAPACK
+    build: inside each (near-)degenerate block the vectors are rebuilt by
+    Gram-Schmidt of the block projector applied to unit vectors, and every
+    vector is sign-fixed so its largest-magnitude component (first on ties)
+    is positive."""
+    w, v = np.linalg.eigh(m)
+    n = len(w)
+    out = np.zeros_like(v)
+    i = 0
+    while i < n:
+        j = i + 1
+        while j < n and abs(w[j] - w[i]) < degen_tol:
+            j += 1
+        blk = v[:, i:j]
+        if j - i == 1:
+            vecs = [blk[:, 0]]
+        else:
+            proj = blk @ blk.T
+            vecs = []
+            for k in range(n):
+                x = proj[:, k].copy()
+                for u in vecs:
+                    x -= (u @ x) * u
+                nx = np.linalg.norm(x)
+                if nx > 1e-6:
+                    vecs.append(x / nx)
+                if len(vecs) == j - i:
+                    break
+        for k, x in enumerate(vecs):
+            amax = np.max(np.abs(x))
+            first = int(np.argmax(np.abs(x) > amax - 1e-12))
+            if x[first] < 0:
+                x = -x
+            out[:, i + k] = x
+        w[i:j] = np.mean(w[i:j]) if j - i > 1 else w[i:j]
+        i = j
+    return w, out
+
+
+# ----------------------------------------------------------------------------
+# PPP pi-Hamiltonians
+# ----------------------------------------------------------------------------
+
+def polyene_geometry(nsites: int = 8, short: float = 1.35, long: float = 1.46) -> np.ndarray:
+    """All-trans zigzag chain, 120 degree bond angles, bonds alternating
+    short/long starting with short."""
+    xy = np.zeros((nsites, 2))
+    for k in range(nsites - 1):
+        b = short if k % 2 == 0 else long
+        ang = math.radians(30.0 if k % 2 == 0 else -30.0)
+        xy[k + 1] = xy[k] + b * np.array([math.cos(ang), math.sin(ang)])
+    return xy
+
+
+def acene_geometry(nrings: int = 5, bond: float = REF_BOND_A) -> np.ndarray:
+    """Linearly fused regular hexagons (pointy-top), sites sorted by (x, y)."""
+    pts = []
+    dx = math.sqrt(3.0) * bond
+    for k in range(nrings):
+        cx = k * dx
+        for m in range(6):
+            ang = math.radians(30.0 + 60.0 * m)
+            pts.append((round(cx + bond * math.cos(ang), 9), round(bond * math.sin(ang), 9)))
+    uniq = sorted(set(pts))
+    return np.array(uniq, dtype=np.float64)
+
+
+def bonded_pairs(xy: np.ndarray, lo: float = 1.2, hi: float = 1.6):
+    n = len(xy)
+    out = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            r = float(np.linalg.norm(xy[i] - xy[j]))
+            if lo < r < hi:
+                out.append((i, j, r))
+    return out
+
+
+def ppp_instance(xy: np.ndarray, name: str, t_ev: float = PPP_T_EV, u_ev: float = PPP_U_EV) -> Instance:
+    """PPP Hamiltonian with Ohno interpolation, half filling, in the Hueckel MO basis.
+
+    Site basis (ZDO): h_ii = -sum_{j!=i} V_ij, h_ij = t_ij on bonds with
+    t_ij = t * (1.40 A / r_ij); (ii|jj) = V_ij, (ii|ii) = U;
+    E_core = sum_{i<j} V_ij.  Energies converted eV -> Hartree.
+    """
+    n = len(xy)
+    dist = np.linalg.norm(xy[:, None, :] - xy[None, :, :], axis=-1)
+    v = u_ev / np.sqrt(1.0 + (u_ev * dist / OHNO_E2_EV_A) ** 2)   # Ohno, V_ii = U
+    t = np.zeros((n, n))
+    bonds = bonded_pairs(xy)
+    for i, j, r in bonds:
+        t[i, j] = t[j, i] = t_ev * (REF_BOND_A / r)
+    h_site = t.copy()
+    for i in range(n):
+        h_site[i, i] = -(v[i].sum() - v[i, i])
+    e_core = float(sum(v[i, j] for i in range(n) for j in range(i + 1, n)))
+    _, cmo = canonical_eigh(t)
+    h_mo = cmo.T @ h_site @ cmo
+    # (pq|rs) = sum_ij C_ip C_iq V_ij C_jr C_js
+    d = np.einsum("ip,iq->ipq", cmo, cmo)
+    eri = np.einsum("ipq,ij,jrs->pqrs", d, v, d, optimize=True)
+    h_mo = symmetrize_h(h_mo * EV_TO_HA)
+    eri = symmetrize_eri(eri * EV_TO_HA)
+    half = n // 2
+    return Instance(name, n, half, n - half, h_mo, eri, e_core * EV_TO_HA,
+                    meta={"kind": "ppp", "nbonds": len(bonds), "sites": n})
+
+
+def ppp_polyene(nsites: int = 8) -> Instance:
+    """Linear polyene, (N e, N o) pi space."""
+    return ppp_instance(polyene_geometry(nsites), f"ppp_polyene_{nsites}")
+
+
+def ppp_pentacene() -> Instance:
+    """Pentacene-shaped 22-site lattice, (22e,22o) pi space."""
+    xy = acene_geometry(5)
+    assert len(xy) == 22
+    return ppp_instance(xy, "ppp_pentacene_22")
+
+
+# ----------------------------------------------------------------------------
+# density-fitted random Hamiltonians
+# ----------------------------------------------------------------------------
+
+def df_instance(norb: int, naux: int, seed: int, nelec: int | None = None,
+                decay: float | None = None, h_diag: np.ndarray | None = None,
+                scale: float | None = None, name: str | None = None) -> Instance:
+    """(pq|rs) = sum_P B^P_pq B^P_rs, B^P = s w_P (G_P + G_P^T)/2 with
+    G_P ~ N(0,1); w_P = 1 or exp(-P/decay); s = sqrt(0.5 / sum_P w_P^2)
+    (so E[(pp|pp)] ~ 0.5 Ha) unless `scale` overrides it; h diagonal."""
+    rng = np.random.default_rng(seed)
+    w = np.ones(naux) if decay is None else np.exp(-np.arange(naux) / decay)
+    s = math.sqrt(0.5 / float(np.sum(w ** 2))) if scale is None else scale
+    g = rng.standard_normal((naux, norb, norb))
+    b = s * w[:, None, None] * 0.5 * (g + g.transpose(0, 2, 1))
+    eri = np.einsum("Ppq,Prs->pqrs", b, b, optimize=True)
+    eri = symmetrize_eri(eri)
+    if h_diag is None:
+        h_diag = np.linspace(-2.0, 1.0, norb)
+    h = np.diag(np.asarray(h_diag, dtype=np.float64))
+    ne = norb if nelec is None else nelec
+    na = (ne + 1) // 2
+    return Instance(name or f"df_{norb}o_{ne}e_s{seed}", norb, na, ne - na, h, eri, 0.0,
+                    meta={"kind": "df", "naux": naux, "seed": seed, "scale": s,
+                          "decay": decay})
+
+
+def df_12o(seed: int = 1708) -> Instance:
+    """(12e,12o), naux = 48, w_P = 1, h = diag(linspace(-2, 1, 12))."""
+    return df_instance(12, 48, seed, name="df_12o_12e")
+
+
+def df_batch(count: int = 64, seed0: int = 7544):
+    """Uneven batch: norb_k = 10 + (k mod 15), nelec = norb, naux = 4 norb."""
+    out = []
+    for k in range(count):
+        n = 10 + (k % 15)
+        out.append(df_instance(n, 4 * n, seed0 + k, name=f"df_batch_{k}_{n}o"))
+    return out
+
+
+# Scale of the (44e,44o) factors: sqrt(0.5/sum w_P^2) gives couplings so
+# strong that the selected space grows without bound at eps1 = 1e-4; the
+# value below is the frozen replacement (see the instance recipe).
+DF44_SCALE = None
+
+
+def df_44o(scale: float | None = None) -> Instance:
+    """(44e,44o), naux = 176, w_P = exp(-P/40), 0.3 Ha HOMO-LUMO gap."""
+    hd = np.concatenate([np.linspace(-2.0, -0.15, 22), np.linspace(0.15, 1.0, 22)])
+    sc = DF44_SCALE if scale is None else scale
+    return df_instance(44, 176, 1707, decay=40.0, h_diag=hd, scale=sc, name="df_44o_44e")
+
+
+def random_kappa(norb: int, seed: int = 1709, sigma: float = 0.01) -> np.ndarray:
+    """Antisymmetric active-active rotation generator, upper entries ~ N(0, sigma^2)."""
+    rng = np.random.default_rng(seed)
+    k = np.zeros((norb, norb))
+    iu = np.triu_indices(norb, 1)
+    k[iu] = sigma * rng.standard_normal(len(iu[0]))
+    return k - k.T
+
+
+def random_tiny(norb: int, nalpha: int, nbeta: int, seed: int, h_scale: float = 1.0,
+                eri_scale: float = 0.3) -> Instance:
+    """Dense random real Hamiltonian for small brute-force checks."""
+    rng = np.random.default_rng(seed)
+    h = symmetrize_h(h_scale * rng.standard_normal((norb, norb)))
+    naux = 2 * norb
+    g = rng.standard_normal((naux, norb, norb))
+    b = 0.5 * (g + g.transpose(0, 2, 1)) * math.sqrt(eri_scale / naux)
+    eri = symmetrize_eri(np.einsum("Ppq,Prs->pqrs", b, b))
+    return Instance(f"tiny_{norb}o_{nalpha}a{nbeta}b_s{seed}", norb, nalpha, nbeta, h, eri,
+                    float(rng.standard_normal()), meta={"kind": "tiny", "seed": seed})
+
+
+# ----------------------------------------------------------------------------
+# determinant sets and vectors (inputs to single-step parity checks)
+# ----------------------------------------------------------------------------
+
+def random_det_keys(norb: int, nalpha: int, nbeta: int, count: int, seed: int) -> np.ndarray:
+    """`count` distinct random determinants as a sorted (count, 2) uint64
+    array of (alpha bits, beta bits); orbital p occupied <=> bit p set."""
+    rng = np.random.default_rng(seed)
+    seen = set()
+    out = []
+    tries = 0
+    while len(out) < count and tries < 50 * count + 1000:
+        tries += 1
+        a = rng.choice(norb, nalpha, replace=False)
+        b = rng.choice(norb, nbeta, replace=False)
+        ka = int(sum(1 << int(x) for x in a))
+        kb = int(sum(1 << int(x) for x in b))
+        if (ka, kb) in seen:
+            continue
+        seen.add((ka, kb))
+        out.append((ka, kb))
+    out.sort()
+    return np.array(out, dtype=np.uint64).reshape(-1, 2)
+
+
+def random_vector(count: int, seed: int, decay: float = 0.0) -> np.ndarray:
+    """Normalised random coefficient vector; with decay > 0 the magnitudes
+    fall off like exp(-decay * k) in random order, mimicking a CI vector."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(count)
+    if decay > 0 and count > 0:
+        x *= np.exp(-decay * rng.permutation(count))
+    nrm = np.linalg.norm(x)
+    return x / nrm if nrm > 0 else x
+
+
+def aufbau_key(nalpha: int, nbeta: int) -> np.ndarray:
+    return np.array([[(1 << nalpha) - 1, (1 << nbeta) - 1]], dtype=np.uint64)
+
+
+def by_name(name: str) -> Instance:
+    """Named workloads: polyene8, pentacene22, df12, df44."""
+    if name == "polyene8":
+        return ppp_polyene(8)
+    if name == "pentacene22":
+        return ppp_pentacene()
+    if name == "df12":
+        return df_12o()
+    if name == "df44":
+        return df_44o()
+    raise KeyError(name)

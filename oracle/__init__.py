@@ -1,0 +1,313 @@
+"""Plain CPU oracle for the variational HCI solve of arXiv:1708.07544.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+CPU-baseline / reference leg of bench.py may import this package.  It
+shares no code with the CUDA library and never imports it.
+
+What each function follows:
+
+* ``select``      -- Eq. (criteria) with the HCI importance function
+                     f(D_a) = max_i |H_ai c_i| (Sec. II.A), by enumerating
+                     every single and double of every D_i (liborc_hci.so).
+* ``hamiltonian`` -- Slater-Condon matrix elements on V (Sec. II.A; the
+                     rules are pinned by the Jordan-Wigner FCI in fci_jw.py).
+* ``ground_state``-- minimum of the energy functional Eq. (variational)
+                     on a fixed V (a library eigensolver stands in for
+                     Davidson: the result is the same lowest eigenpair).
+* ``hci``         -- the variational stage V^{mu+1} = V^mu + C^mu(eps1)
+                     (Sec. II.A, Fig. 1) iterated until C^mu is empty.
+* ``rdm12``       -- the variational RDMs by their definition (Sec. IV).
+* ``rotate`` / ``gradient`` -- vHCISCF gradient Eq. (vdedk2): the
+                     derivative of the rotated integrals contracted with
+                     the RDMs, chained through U = exp(kappa) (Sec. III.B).
+
+Readings where the paper is silent (strict '>', eps1 <= 0 accepts every
+single/double, aufbau start, stop at an empty C^mu, phase of c, spin-summed
+RDM order) are stated in the functions below.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import build as _build
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        d = ctypes.c_double
+        L.orc_diag.argtypes = [ctypes.c_int, P, P, d, P, i64, P]
+        L.orc_hamiltonian.argtypes = [ctypes.c_int, P, P, d, P, i64]
+        L.orc_hamiltonian.restype = P
+        L.orc_csr_nnz.argtypes = [P]
+        L.orc_csr_nnz.restype = i64
+        L.orc_csr_copy.argtypes = [P, P, P, P]
+        L.orc_csr_free.argtypes = [P]
+        L.orc_sigma_rows.argtypes = [ctypes.c_int, P, P, d, P, i64, P, P, i64, P]
+        L.orc_select.argtypes = [ctypes.c_int, P, P, P, P, i64, d, ctypes.c_int, P, i64]
+        L.orc_select.restype = P
+        L.orc_sel_count.argtypes = [P]
+        L.orc_sel_count.restype = i64
+        L.orc_sel_copy.argtypes = [P, P, P]
+        L.orc_sel_free.argtypes = [P]
+        L.orc_rdm12.argtypes = [ctypes.c_int, P, i64, P, P, P]
+        L.orc_num_threads.restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return int(_lib().orc_num_threads())
+
+
+class Problem:
+    """Minimal view of an instance: norb, nalpha, nbeta, h, eri, e_core."""
+
+    def __init__(self, norb, nalpha, nbeta, h, eri, e_core=0.0):
+        self.norb, self.nalpha, self.nbeta = int(norb), int(nalpha), int(nbeta)
+        self.h = _c(h, np.float64)
+        self.eri = _c(eri, np.float64)
+        self.e_core = float(e_core)
+
+    @staticmethod
+    def of(inst) -> "Problem":
+        if isinstance(inst, Problem):
+            return inst
+        return Problem(inst.norb, inst.nalpha, inst.nbeta, inst.h, inst.eri, inst.e_core)
+
+
+# ----------------------------------------------------------------------------
+# determinant-level primitives (C++)
+# ----------------------------------------------------------------------------
+
+def diag(inst, keys) -> np.ndarray:
+    P = Problem.of(inst)
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    out = np.zeros(len(keys))
+    _lib().orc_diag(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), len(keys), _p(out))
+    return out
+
+
+def hamiltonian(inst, keys) -> sp.csr_matrix:
+    """<D_i|H|D_j> on V (Slater-Condon), E_core on the diagonal."""
+    P = Problem.of(inst)
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    L = _lib()
+    h = L.orc_hamiltonian(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), len(keys))
+    try:
+        nnz = L.orc_csr_nnz(h)
+        rp = np.zeros(len(keys) + 1, np.int64)
+        col = np.zeros(nnz, np.int64)
+        val = np.zeros(nnz)
+        L.orc_csr_copy(h, _p(rp), _p(col), _p(val))
+    finally:
+        L.orc_csr_free(h)
+    return sp.csr_matrix((val, col, rp), shape=(len(keys), len(keys)))
+
+
+def sigma_rows(inst, keys, c, rows) -> np.ndarray:
+    """(H c)_i for the listed rows, by enumerating the excitations of D_i."""
+    P = Problem.of(inst)
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    rows = _c(rows, np.int64)
+    out = np.zeros(len(rows))
+    _lib().orc_sigma_rows(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), len(keys), _p(c),
+                          _p(rows), len(rows), _p(out))
+    return out
+
+
+def select(inst, keys, c, eps1, band=1e-12, sources=None):
+    """One selection step, Eq. (criteria) with f_HCI (Sec. II.A).
+
+    Returns (new_keys, f_new, tie_keys): new_keys are the determinants not
+    in V with max_i |H_ai c_i| > eps1 (strict, the paper's 'greater than'),
+    sorted by (alpha, beta); eps1 <= 0 accepts every single and double
+    excitation (reading: the symmetry-zero elements left by the MO
+    transform would otherwise make the set depend on rounding).
+    tie_keys lists determinants with |f - eps1| <= band*eps1, whose
+    membership may legitimately differ under a different summation order.
+    `sources` restricts the D_i that generate (sampled verification).
+    """
+    P = Problem.of(inst)
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    L = _lib()
+    allx = 1 if eps1 <= 0 else 0
+    floor = eps1 * (1.0 - band) if eps1 > 0 else 0.0
+    if sources is not None:
+        src = _c(sources, np.int64)
+        hs = L.orc_select(P.norb, _p(P.h), _p(P.eri), _p(keys), _p(c), len(keys), floor, allx,
+                          _p(src), len(src))
+    else:
+        hs = L.orc_select(P.norb, _p(P.h), _p(P.eri), _p(keys), _p(c), len(keys), floor, allx,
+                          None, 0)
+    try:
+        m = L.orc_sel_count(hs)
+        k = np.zeros((m, 2), np.uint64)
+        f = np.zeros(m)
+        L.orc_sel_copy(hs, _p(k), _p(f))
+    finally:
+        L.orc_sel_free(hs)
+    if eps1 <= 0:
+        return k, f, np.zeros((0, 2), np.uint64)
+    sel = f > eps1
+    tie = np.abs(f - eps1) <= band * eps1
+    return k[sel], f[sel], k[tie]
+
+
+def rdm12(norb, keys, c):
+    """rdm1[p,q] = sum_s <a+_ps a_qs>, rdm2[p,q,r,s] = sum_st <a+_ps a+_rt a_st a_qs>
+    (spin-summed, the order in which E = sum h rdm1 + 1/2 sum (pq|rs) rdm2)."""
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    r1 = np.zeros((norb, norb))
+    r2 = np.zeros((norb,) * 4)
+    _lib().orc_rdm12(norb, _p(keys), len(keys), _p(c), _p(r1), _p(r2))
+    return r1, r2
+
+
+# ----------------------------------------------------------------------------
+# eigenproblem, HCI loop
+# ----------------------------------------------------------------------------
+
+def fix_phase(c: np.ndarray) -> np.ndarray:
+    """Reading: the largest-|c| component (lowest index on ties) is positive."""
+    if len(c) == 0:
+        return c
+    a = np.abs(c)
+    i = int(np.argmax(a))      # argmax returns the first maximum
+    return -c if c[i] < 0 else c
+
+
+def ground_state(inst, keys, v0=None, H=None):
+    """Lowest eigenpair of H restricted to V (Eq. variational on a fixed V)."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    if H is None:
+        H = hamiltonian(inst, keys)
+    nV = len(keys)
+    if nV <= 2500:
+        w, v = np.linalg.eigh(H.toarray())
+        e, c = float(w[0]), v[:, 0]
+    else:
+        if v0 is not None and np.linalg.norm(v0) > 0:
+            v0 = np.asarray(v0, dtype=np.float64)
+            v0 = v0 + 1e-3 * np.random.default_rng(0).standard_normal(nV) / np.sqrt(nV)
+        w, v = spla.eigsh(H, k=1, which="SA", v0=v0, tol=0, ncv=min(nV, 40))
+        e, c = float(w[0]), v[:, 0]
+        r = H @ c - e * c
+        if np.linalg.norm(r) > 1e-9:
+            w, v = spla.eigsh(H, k=1, which="SA", v0=c, tol=0, ncv=min(nV, 80), maxiter=20000)
+            e, c = float(w[0]), v[:, 0]
+    c = c / np.linalg.norm(c)
+    return e, fix_phase(c)
+
+
+def merge(keys, c, new_keys):
+    """Sorted union V + C (Sec. II.A) with c padded by zeros (warm start)."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    new_keys = np.asarray(new_keys, np.uint64).reshape(-1, 2)
+    allk = np.concatenate([keys, new_keys])
+    allc = np.concatenate([np.asarray(c, np.float64), np.zeros(len(new_keys))])
+    order = np.lexsort((allk[:, 1], allk[:, 0]))
+    return allk[order], allc[order]
+
+
+def aufbau(nalpha, nbeta):
+    """Reading: the first V is the aufbau determinant in the given orbital order."""
+    return np.array([[(1 << nalpha) - 1, (1 << nbeta) - 1]], dtype=np.uint64)
+
+
+def hci(inst, eps1, max_iter=30, verbose=False):
+    """Variational HCI (Sec. II.A): V^0 = {aufbau}, c^0 = [1]; repeat
+    select C^mu(eps1), V^{mu+1} = V^mu + C^mu, lowest eigenpair on V^{mu+1};
+    stop when C^mu is empty (reading of 'a designated convergence
+    threshold') or after max_iter iterations."""
+    P = Problem.of(inst)
+    keys = aufbau(P.nalpha, P.nbeta)
+    c = np.array([1.0])
+    e = float(diag(P, keys)[0])
+    history = []
+    for mu in range(max_iter):
+        new, _, ties = select(P, keys, c, eps1)
+        history.append({"mu": mu, "nV": len(keys), "n_new": len(new), "E": e, "n_ties": len(ties)})
+        if verbose:
+            print(history[-1])
+        if len(new) == 0:
+            break
+        keys, c = merge(keys, c, new)
+        e, c = ground_state(P, keys, v0=c)
+    return {"keys": keys, "c": c, "E": e, "history": history}
+
+
+# ----------------------------------------------------------------------------
+# orbital rotation and vHCISCF gradient
+# ----------------------------------------------------------------------------
+
+def expm(kappa):
+    return scipy.linalg.expm(np.asarray(kappa, dtype=np.float64))
+
+
+def rotate(inst, kappa):
+    """h' = U^T h U, (pq|rs)' = sum U_ap U_bq U_cr U_ds (ab|cd), U = exp(kappa)."""
+    P = Problem.of(inst)
+    U = expm(kappa)
+    h2 = U.T @ P.h @ U
+    e2 = np.einsum("abcd,ap,bq,cr,ds->pqrs", P.eri, U, U, U, U, optimize=True)
+    return Problem(P.norb, P.nalpha, P.nbeta, h2, e2, P.e_core), U
+
+
+def energy_from_rdm(inst, rdm1, rdm2):
+    P = Problem.of(inst)
+    return float(np.sum(P.h * rdm1) + 0.5 * np.sum(P.eri * rdm2) + P.e_core)
+
+
+def gradient(inst, kappa, rdm1, rdm2):
+    """Gradient of E(h', eri') with dE/dh' = rdm1, dE/d(pq|rs)' = rdm2/2
+    (Hellmann-Feynman at fixed V, c: dE/dc = 0, Eq. vdedk2), chained
+    through the rotation (all four index positions, no symmetry assumed)
+    and through U = exp(kappa) by the adjoint Frechet derivative of expm.
+    Returns dict(dh, deri, dU, dkappa) with dkappa the derivative with
+    respect to every entry of the full kappa matrix."""
+    P = Problem.of(inst)
+    U = expm(kappa)
+    D = 0.5 * np.asarray(rdm2)
+    g1 = np.asarray(rdm1)
+    dh = U @ g1 @ U.T
+    deri = np.einsum("pqrs,ap,bq,cr,ds->abcd", D, U, U, U, U, optimize=True)
+    gU = P.h @ U @ g1.T + P.h.T @ U @ g1
+    E = P.eri
+    gU = gU + np.einsum("xbcd,bq,cr,ds,yqrs->xy", E, U, U, U, D, optimize=True)
+    gU = gU + np.einsum("axcd,ap,cr,ds,pyrs->xy", E, U, U, U, D, optimize=True)
+    gU = gU + np.einsum("abxd,ap,bq,ds,pqys->xy", E, U, U, U, D, optimize=True)
+    gU = gU + np.einsum("abcx,ap,bq,cr,pqry->xy", E, U, U, U, D, optimize=True)
+    dk = scipy.linalg.expm_frechet(np.asarray(kappa, dtype=np.float64).T, gU, compute_expm=False)
+    return {"dh": dh, "deri": deri, "dU": gU, "dkappa": dk}
+
+
+def energy_fixed_space(inst, kappa, keys, v0=None):
+    """E at fixed V after rotating the integrals by exp(kappa) (for central
+    finite differences of the vHCISCF gradient)."""
+    R, _ = rotate(inst, kappa)
+    e, c = ground_state(R, keys, v0=v0)
+    return e, c
