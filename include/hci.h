@@ -1,0 +1,169 @@
+/*
+ * hci.h -- C ABI of the GB300 (sm_103a) heat-bath CI active-space solver.
+ *
+ * Method: variational Heat-bath Configuration Interaction and the vHCISCF
+ * orbital gradient of Smith, Mussard, Holmes & Sharma, "Cheap and near exact
+ * CASSCF with large active spaces", arXiv:1708.07544 (Sec. II.A, III.B, IV).
+ *
+ * Problem statement (the active-space Hamiltonian handed to the solver,
+ * Sec. III, Fig. 2):
+ *   H = sum_pq h_pq sum_s a+_ps a_qs
+ *     + 1/2 sum_pqrs (pq|rs) sum_st a+_ps a+_rt a_st a_qs + e_core
+ * with real h (n x n, symmetric, row-major) and real (pq|rs) in chemists'
+ * notation (n^4, row-major [p][q][r][s], exact 8-fold permutational
+ * symmetry required: every permutation of one integral must hold the same
+ * bits, because the heat-bath lists and the Slater-Condon rules read
+ * different permutations).
+ *
+ * Determinants: keys[i] = { alpha bits, beta bits } as two uint64 words,
+ * orbital p occupied <=> bit p set; norb <= 64.  A determinant is
+ * prod_{alpha occ ascending} a+ prod_{beta occ ascending} a+ |0>.
+ * Key arrays are [nV][2] uint64, 16-byte aligned, sorted strictly
+ * ascending by (alpha, beta) (lexicographic, unsigned) unless stated.
+ *
+ * Memory and streams: every pointer argument marked "device" is device
+ * memory owned by the caller; "host" pointers are host memory.  All work is
+ * enqueued on the stream given to hci_create (a cudaStream_t passed as
+ * void*; NULL = legacy default stream).  Calls that return a host scalar
+ * synchronise that stream before returning.  The context owns only its
+ * internal workspaces (integral tables, heat-bath lists, the connection
+ * graph of the last space, scratch), allocated with cudaMallocAsync on the
+ * context stream and released by hci_destroy.  A context is not thread-safe.
+ *
+ * Errors: every call returns an hci_status.  On failure hci_last_error()
+ * holds a one-line message.  HCI_ERR_CAPACITY reports, through the
+ * call's size out-argument, the capacity that would have sufficed.
+ */
+#ifndef HCI_GB300_H
+#define HCI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hci_ctx hci_ctx;
+typedef int hci_status;
+
+enum {
+  HCI_OK = 0,
+  HCI_ERR_INVALID = 1,        /* bad argument (norb > 64, counts, null, unsorted...) */
+  HCI_ERR_CAPACITY = 2,       /* output buffer too small; required size returned */
+  HCI_ERR_NOT_CONVERGED = 3,  /* Davidson reached maxit; outputs hold the last iterate */
+  HCI_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  HCI_ERR_NOMEM = 5           /* device allocation failed */
+};
+
+/* Create a solver for one active space.  h: device, n*n doubles; eri:
+ * device, n^4 doubles (copied into the context, so the caller may free
+ * them afterwards).  nalpha, nbeta in [0, norb], norb in [1, 64].
+ * stream: cudaStream_t or NULL.  Derived tables for single-excitation
+ * elements are built here.  (Sec. III: "the active space two electron
+ * integrals ... are passed on to Dice".) */
+hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta, const double* h,
+                      const double* eri, double e_core, void* stream);
+
+/* Release the context and everything it owns (synchronises its stream). */
+hci_status hci_destroy(hci_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  ctx may be
+ * NULL, then the last failure of hci_create on this thread is returned. */
+const char* hci_last_error(const hci_ctx* ctx);
+
+/* Build the heat-bath excitation lists (Sec. II.A and Fig. 1b: double
+ * excitation magnitudes depend only on the orbitals, so they are sorted and
+ * stored before the run).  For every occupied opposite-spin pair (p_a, q_b)
+ * the n^2 targets (r_a, s_b) with |(pr|qs)|, and for every same-spin pair
+ * p<q the n(n-1)/2 targets r<s with |(pr|qs) - (ps|qr)|, each list sorted by
+ * magnitude descending (ties by target ascending).  Idempotent. */
+hci_status hci_build_lists(hci_ctx* ctx);
+
+/* One selection step, Eq. (criteria) with the HCI importance function
+ * f(D_a) = max_i |H_ai c_i| (Sec. II.A): every D_a not in V that is a single
+ * or double excitation of some D_i in V with |H_ai| |c_i| > eps1 (strict;
+ * eps1 <= 0 accepts every single and double).  Doubles come from the
+ * heat-bath walk that stops at |v| <= eps1/|c_i|; singles are screened by
+ * an upper bound and then evaluated exactly.
+ *   keys: device [nV][2], sorted; c: device [nV] doubles;
+ *   new_keys: device [cap][2] output, sorted, unique, disjoint from V;
+ *   n_new: host out, number of new determinants (or the required cap on
+ *   HCI_ERR_CAPACITY).  Builds the lists if needed.  Synchronises. */
+hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys, const double* c, int64_t nV,
+                      uint64_t* new_keys, int64_t cap, int64_t* n_new);
+
+/* V^{mu+1} = V^mu + C^mu (Sec. II.A): sorted union of two disjoint sorted
+ * key sets.  out_keys: device [nV+n_new][2]; out_c: device [nV+n_new],
+ * the old coefficients at their new positions and 0 for the new
+ * determinants (Davidson warm start).  c and out_c may be NULL. */
+hci_status hci_merge(hci_ctx* ctx, const uint64_t* keys, const double* c, int64_t nV,
+                     const uint64_t* new_keys, int64_t n_new, uint64_t* out_keys, double* out_c);
+
+/* sigma = H c on V for nvec vectors (Sec. II.A, the Davidson sigma; Sec. IV:
+ * all single and double connections between pairs of determinants of V).
+ * c, sigma: device, nvec column vectors of length nV stored one after the
+ * other ([nvec][nV]).  The connection graph of V is built on first use and
+ * cached until a call passes a different space (checked by content hash). */
+hci_status hci_sigma(hci_ctx* ctx, const uint64_t* keys, int64_t nV, const double* c,
+                     double* sigma, int nvec);
+
+/* Lowest eigenpair on V, the minimum of the energy functional Eq.
+ * (variational), by FP64 Davidson with a diagonal preconditioner.
+ * c_inout: device [nV], the start vector on entry (zero => unit vector at
+ * the lowest diagonal element), the normalised eigenvector on exit, with
+ * its largest-magnitude component (lowest index on ties) positive.
+ * energy: host out (includes e_core).  Converged when ||H c - E c||_2 <= tol.
+ * iters: host out (may be NULL).  Synchronises. */
+hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout,
+                        double* energy, double tol, int maxit, int* iters);
+
+/* Spin-summed variational RDMs (Sec. IV, Gamma^{c,c}; accumulated over the
+ * connections of V):
+ *   rdm1[p*n+q]            = sum_s <a+_ps a_qs>
+ *   rdm2[((p*n+q)*n+r)*n+s] = sum_st <a+_ps a+_rt a_st a_qs>
+ * so that E = sum h rdm1 + 1/2 sum (pq|rs) rdm2 + e_core.  c must be
+ * normalised for these to be expectation values.  rdm1, rdm2: device. */
+hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, const double* c, double* rdm1,
+                     double* rdm2);
+
+/* The whole variational stage (Sec. II.A, Fig. 1a): V^0 = {aufbau}, then
+ * select / merge / Davidson until C^mu is empty or max_iter selections.
+ * keys_out: device [cap][2]; c_out: device [cap]; nV: host out (required
+ * cap on HCI_ERR_CAPACITY); energy: host out; iters: host out (selection
+ * steps taken, may be NULL).  Synchronises. */
+hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit,
+                     uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV, double* energy,
+                     int* iters);
+
+/* Active-active orbital rotation (Sec. III.A: the integrals depend on the
+ * orbital parameters kappa; Sec. III.B): U = exp(kappa) for an n x n real
+ * kappa (antisymmetric for an orthogonal U), h' = U^T h U,
+ * (pq|rs)' = sum_abcd U_ap U_bq U_cr U_ds (ab|cd).
+ * All pointers device; U, h_out, eri_out are outputs (n*n, n*n, n^4).
+ * stream: cudaStream_t or NULL. */
+hci_status hci_rotate(int norb, const double* kappa, const double* h, const double* eri, double* U,
+                      double* h_out, double* eri_out, void* stream);
+
+/* Backward of E(h', eri') through the rotation, Eq. (vdedk2): given
+ * dE/dh' = rdm1 and dE/d(pq|rs)' = rdm2/2 (Hellmann-Feynman at fixed V and
+ * converged c), returns
+ *   dh     = U rdm1 U^T                      (n*n)
+ *   deri   = 1/2 sum rdm2_pqrs U_ap U_bq U_cr U_ds   (n^4)
+ *   dkappa = dE/dkappa for every entry of the full kappa matrix (n*n),
+ *            through the adjoint Frechet derivative of exp.
+ * Any of dh, deri, dkappa may be NULL.  All pointers device.  Assumes the
+ * 8-fold symmetry of eri and the pair symmetries of rdm2 of a real state. */
+hci_status hci_rotate_backward(int norb, const double* kappa, const double* h, const double* eri,
+                               const double* rdm1, const double* rdm2, double* dh, double* deri,
+                               double* dkappa, void* stream);
+
+/* Statistics of the last calls on this context (host out, any may be NULL):
+ * nnz of the cached connection graph (off-diagonal), candidates emitted by
+ * the last hci_select before deduplication. */
+hci_status hci_stats(const hci_ctx* ctx, int64_t* graph_nnz, int64_t* last_candidates);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HCI_GB300_H */

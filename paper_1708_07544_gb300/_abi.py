@@ -1,0 +1,229 @@
+"""ctypes binding of libhci.so: one Python function per C entry point, same
+names, argument marshalling only (torch tensors -> device pointers).
+
+Keys are int64 torch tensors of shape (nV, 2) holding the (alpha, beta)
+uint64 bit patterns; coefficient vectors and integrals are float64.
+Every computation runs in the CUDA library; there is no CPU fallback, and
+loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhci.so")
+
+HCI_OK = 0
+HCI_ERR_INVALID = 1
+HCI_ERR_CAPACITY = 2
+HCI_ERR_NOT_CONVERGED = 3
+HCI_ERR_CUDA = 4
+HCI_ERR_NOMEM = 5
+_NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5: "NOMEM"}
+
+EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
+           "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
+           "hci_stats"]
+
+
+class HCIError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"HCI_ERR_{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libhci.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libhci.so not built at {p}; run __graft_entry__.build()")
+    L = ctypes.CDLL(p)
+    V = ctypes.c_void_p
+    I = ctypes.c_int
+    I64 = ctypes.c_int64
+    D = ctypes.c_double
+    P = ctypes.POINTER
+    L.hci_create.argtypes = [P(V), I, I, I, V, V, D, V]
+    L.hci_destroy.argtypes = [V]
+    L.hci_last_error.argtypes = [V]
+    L.hci_last_error.restype = ctypes.c_char_p
+    L.hci_build_lists.argtypes = [V]
+    L.hci_select.argtypes = [V, D, V, V, I64, V, I64, P(I64)]
+    L.hci_merge.argtypes = [V, V, V, I64, V, I64, V, V]
+    L.hci_sigma.argtypes = [V, V, I64, V, V, I]
+    L.hci_davidson.argtypes = [V, V, I64, V, P(D), D, I, P(I)]
+    L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
+    L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
+    L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
+    L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
+    L.hci_stats.argtypes = [V, P(I64), P(I64)]
+    for name in EXPORTS:
+        getattr(L, name).restype = I if name != "hci_last_error" else ctypes.c_char_p
+    if path is None:
+        _LIB = L
+    return L
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(status: int, ctx=None):
+    if status != HCI_OK:
+        msg = load().hci_last_error(ctx)
+        raise HCIError(status, (msg or b"").decode())
+
+
+def hci_create(norb, nalpha, nbeta, h, eri, e_core=0.0, stream=None):
+    """Returns an opaque context handle (int)."""
+    L = load()
+    out = ctypes.c_void_p()
+    h = h.to(torch.float64).contiguous()
+    eri = eri.to(torch.float64).contiguous()
+    st = L.hci_create(ctypes.byref(out), int(norb), int(nalpha), int(nbeta), _ptr(h), _ptr(eri), float(e_core),
+                      _stream_ptr(stream))
+    _check(st, None)
+    return out.value
+
+
+def hci_destroy(ctx):
+    _check(load().hci_destroy(ctx), None)
+
+
+def hci_last_error(ctx=None) -> str:
+    return (load().hci_last_error(ctx) or b"").decode()
+
+
+def hci_build_lists(ctx):
+    _check(load().hci_build_lists(ctx), ctx)
+
+
+def hci_select(ctx, eps1, keys, c, cap=None):
+    """New determinants (sorted, unique, not in V) as an (n_new, 2) int64 tensor."""
+    L = load()
+    nV = keys.shape[0]
+    n = ctypes.c_int64(0)
+    if cap is None:
+        cap = max(1024, 4 * nV)
+    out = torch.empty((cap, 2), dtype=torch.int64, device=keys.device)
+    st = L.hci_select(ctx, float(eps1), _ptr(keys), _ptr(c), nV, _ptr(out), cap, ctypes.byref(n))
+    if st == HCI_ERR_CAPACITY:
+        cap = int(n.value)
+        out = torch.empty((max(cap, 1), 2), dtype=torch.int64, device=keys.device)
+        st = L.hci_select(ctx, float(eps1), _ptr(keys), _ptr(c), nV, _ptr(out), cap, ctypes.byref(n))
+    _check(st, ctx)
+    return out[: int(n.value)]
+
+
+def hci_merge(ctx, keys, c, new_keys):
+    L = load()
+    nV, nn = keys.shape[0], new_keys.shape[0]
+    ok = torch.empty((nV + nn, 2), dtype=torch.int64, device=keys.device)
+    oc = torch.empty(nV + nn, dtype=torch.float64, device=keys.device) if c is not None else None
+    _check(L.hci_merge(ctx, _ptr(keys), _ptr(c), nV, _ptr(new_keys) if nn else None, nn, _ptr(ok), _ptr(oc)), ctx)
+    return ok, oc
+
+
+def hci_sigma(ctx, keys, c):
+    """H c for c of shape (nV,) or (nvec, nV)."""
+    L = load()
+    nV = keys.shape[0]
+    nvec = 1 if c.dim() == 1 else c.shape[0]
+    out = torch.empty_like(c)
+    _check(L.hci_sigma(ctx, _ptr(keys), nV, _ptr(c), _ptr(out), nvec), ctx)
+    return out
+
+
+def hci_davidson(ctx, keys, c0=None, tol=1e-10, maxit=400, allow_unconverged=False):
+    """(E, c, iterations); c0 is copied (zero/None => start at the lowest diagonal)."""
+    L = load()
+    nV = keys.shape[0]
+    c = torch.zeros(nV, dtype=torch.float64, device=keys.device) if c0 is None else c0.clone().contiguous()
+    e = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    st = L.hci_davidson(ctx, _ptr(keys), nV, _ptr(c), ctypes.byref(e), float(tol), int(maxit), ctypes.byref(it))
+    if not (allow_unconverged and st == HCI_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    return e.value, c, it.value
+
+
+def hci_rdm12(ctx, keys, c, norb):
+    L = load()
+    r1 = torch.empty((norb, norb), dtype=torch.float64, device=keys.device)
+    r2 = torch.empty((norb,) * 4, dtype=torch.float64, device=keys.device)
+    _check(L.hci_rdm12(ctx, _ptr(keys), keys.shape[0], _ptr(c), _ptr(r1), _ptr(r2)), ctx)
+    return r1, r2
+
+
+def hci_solve(ctx, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 20, device="cuda"):
+    """Whole variational stage; returns (keys, c, E, iterations)."""
+    L = load()
+    nv = ctypes.c_int64(0)
+    e = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    keys = torch.empty((cap, 2), dtype=torch.int64, device=device)
+    c = torch.empty(cap, dtype=torch.float64, device=device)
+    st = L.hci_solve(ctx, float(eps1), int(max_iter), float(dav_tol), int(dav_maxit), _ptr(keys), _ptr(c), cap,
+                     ctypes.byref(nv), ctypes.byref(e), ctypes.byref(it))
+    if st == HCI_ERR_CAPACITY:
+        cap = int(nv.value)
+        keys = torch.empty((cap, 2), dtype=torch.int64, device=device)
+        c = torch.empty(cap, dtype=torch.float64, device=device)
+        st = L.hci_solve(ctx, float(eps1), int(max_iter), float(dav_tol), int(dav_maxit), _ptr(keys), _ptr(c), cap,
+                         ctypes.byref(nv), ctypes.byref(e), ctypes.byref(it))
+    _check(st, ctx)
+    n = int(nv.value)
+    return keys[:n], c[:n], e.value, it.value
+
+
+def hci_rotate(kappa, h, eri, stream=None):
+    """(U, h', eri') with U = exp(kappa)."""
+    L = load()
+    n = h.shape[0]
+    U = torch.empty_like(h)
+    h2 = torch.empty_like(h)
+    e2 = torch.empty_like(eri)
+    _check(L.hci_rotate(n, _ptr(kappa.contiguous()), _ptr(h.contiguous()), _ptr(eri.contiguous()), _ptr(U),
+                        _ptr(h2), _ptr(e2), _stream_ptr(stream)), None)
+    return U, h2, e2
+
+
+def hci_rotate_backward(kappa, h, eri, rdm1, rdm2, want_dh=True, want_deri=True, want_dkappa=True, stream=None):
+    L = load()
+    n = h.shape[0]
+    dh = torch.empty_like(h) if want_dh else None
+    de = torch.empty_like(eri) if want_deri else None
+    dk = torch.empty_like(h) if want_dkappa else None
+    _check(L.hci_rotate_backward(n, _ptr(kappa.contiguous()), _ptr(h.contiguous()), _ptr(eri.contiguous()),
+                                 _ptr(rdm1.contiguous()), _ptr(rdm2.contiguous()), _ptr(dh), _ptr(de), _ptr(dk),
+                                 _stream_ptr(stream)), None)
+    return dh, de, dk
+
+
+def hci_stats(ctx):
+    L = load()
+    a = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(L.hci_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return {"graph_nnz": a.value, "last_candidates": b.value}

@@ -1,0 +1,395 @@
+// FP64 Davidson for the lowest eigenpair on a fixed determinant space:
+// the minimum of the energy functional Eq. (variational) with the
+// normalisation multiplier (Sec. II.A "obtained at each iteration by the
+// Davidson procedure").  Vector operations, the subspace eigenproblem
+// (cyclic Jacobi on one warp) and the phase convention all run on the GPU;
+// the host only reads the Ritz value and the residual norm per iteration.
+#include <cmath>
+
+#include "hci_internal.cuh"
+
+namespace {
+
+constexpr int MAXSUB = 24;          // subspace size before restart (<= 32)
+constexpr int LDG = 32;             // leading dimension of the subspace matrix
+constexpr int DBLOCK = 256;
+
+struct DavDev {
+  double G[LDG * LDG];
+  double y[LDG];
+  double dots[LDG];
+  double theta;
+  double rnorm2;
+  double nrm2;
+  int amax_idx;
+  int pad;
+};
+
+// partial[b][j] = sum over this block's elements of V_j . w (j < k)
+template <int MAXK>
+__global__ void __launch_bounds__(DBLOCK) k_dots(const double* __restrict__ V, int64_t ld, int k,
+                                                 const double* __restrict__ w, int64_t n, double* __restrict__ partial) {
+  double acc[MAXK];
+#pragma unroll
+  for (int j = 0; j < MAXK; ++j) acc[j] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double wv = w[i];
+#pragma unroll
+    for (int j = 0; j < MAXK; ++j)
+      if (j < k) acc[j] = fma(V[(int64_t)j * ld + i], wv, acc[j]);
+  }
+  __shared__ double red[DBLOCK / 32][MAXK];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < MAXK; ++j) {
+    if (j < k) {
+      double a = acc[j];
+      for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[wid][j] = a;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < DBLOCK / 32; ++w2) s += red[w2][threadIdx.x];
+    partial[(int64_t)blockIdx.x * LDG + threadIdx.x] = s;
+  }
+}
+
+// out[j] = sum_b partial[b][j] in a fixed order
+__global__ void k_reduce(const double* __restrict__ partial, int nblocks, int k, double* __restrict__ out) {
+  int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * LDG + j];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[j] = s;
+}
+
+// G[j][col] = G[col][j] = dots[j], j <= col
+__global__ void k_set_gcol(DavDev* d, int col) {
+  int j = threadIdx.x;
+  if (j <= col) {
+    d->G[j * LDG + col] = d->dots[j];
+    d->G[col * LDG + j] = d->dots[j];
+  }
+}
+
+// lowest eigenpair of the k x k subspace matrix by cyclic Jacobi (one warp)
+__global__ void k_jacobi(DavDev* d, int k) {
+  __shared__ double A[32][33];
+  __shared__ double Q[32][33];
+  const int l = threadIdx.x;
+  for (int j = 0; j < 32; ++j) {
+    A[l][j] = (l < k && j < k) ? d->G[l * LDG + j] : 0.0;
+    Q[l][j] = (l == j) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    if (l < k) {
+      for (int j = 0; j < k; ++j) {
+        if (j > l) off += A[l][j] * A[l][j];
+        if (j == l) dia += A[l][j] * A[l][j];
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (off <= 1e-32 * dia || off == 0.0) break;
+    for (int p = 0; p < k - 1; ++p) {
+      for (int q = p + 1; q < k; ++q) {
+        double apq = A[p][q];
+        if (fabs(apq) < 1e-300) continue;
+        double app = A[p][p], aqq = A[q][q];
+        double tau = (aqq - app) / (2.0 * apq);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = t * c;
+        __syncwarp();
+        if (l < k) {
+          double alp = A[l][p], alq = A[l][q];
+          A[l][p] = c * alp - s * alq;
+          A[l][q] = s * alp + c * alq;
+        }
+        __syncwarp();
+        if (l < k) {
+          double apl = A[p][l], aql = A[q][l];
+          A[p][l] = c * apl - s * aql;
+          A[q][l] = s * apl + c * aql;
+          double vlp = Q[l][p], vlq = Q[l][q];
+          Q[l][p] = c * vlp - s * vlq;
+          Q[l][q] = s * vlp + c * vlq;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  __shared__ int s_m;
+  if (l == 0) {
+    int m = 0;
+    for (int j = 1; j < k; ++j)
+      if (A[j][j] < A[m][m]) m = j;
+    s_m = m;
+    d->theta = A[m][m];
+  }
+  __syncwarp();
+  int m = s_m;
+  if (l < LDG) d->y[l] = (l < k) ? Q[l][m] : 0.0;
+}
+
+// x = V y, wy = W y, r = wy - theta x, t = r / (theta - diag) (guarded),
+// partial[b] = sum r^2
+__global__ void __launch_bounds__(DBLOCK) k_ritz(const double* __restrict__ V, const double* __restrict__ W, int64_t ld,
+                                                 int k, const DavDev* __restrict__ d, const double* __restrict__ diag,
+                                                 int64_t n, double* __restrict__ x, double* __restrict__ wy,
+                                                 double* __restrict__ t, double* __restrict__ partial) {
+  __shared__ double ys[LDG];
+  __shared__ double red[DBLOCK / 32];
+  if (threadIdx.x < LDG) ys[threadIdx.x] = d->y[threadIdx.x];
+  __syncthreads();
+  const double theta = d->theta;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double xv = 0.0, wv = 0.0;
+    for (int j = 0; j < k; ++j) {
+      xv = fma(ys[j], V[(int64_t)j * ld + i], xv);
+      wv = fma(ys[j], W[(int64_t)j * ld + i], wv);
+    }
+    double r = wv - theta * xv;
+    double den = theta - diag[i];
+    if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
+    x[i] = xv;
+    wy[i] = wv;
+    t[i] = r / den;
+    acc = fma(r, r, acc);
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < DBLOCK / 32; ++w) s += red[w];
+    partial[(int64_t)blockIdx.x * LDG] = s;
+  }
+}
+
+// t -= sum_j dots_j V_j
+__global__ void k_orth(const double* __restrict__ V, int64_t ld, int k, const DavDev* __restrict__ d,
+                       double* __restrict__ t, int64_t n) {
+  __shared__ double cs[LDG];
+  if (threadIdx.x < LDG) cs[threadIdx.x] = d->dots[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = t[i];
+    for (int j = 0; j < k; ++j) v = fma(-cs[j], V[(int64_t)j * ld + i], v);
+    t[i] = v;
+  }
+}
+
+// x *= 1/sqrt(*s2) (and y likewise if given)
+__global__ void k_scale_by(double* __restrict__ x, double* __restrict__ y, int64_t n, const double* __restrict__ s2) {
+  double f = 1.0 / sqrt(*s2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] *= f;
+    if (y) y[i] *= f;
+  }
+}
+
+__global__ void k_scale_const(double* __restrict__ x, int64_t n, double f) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+
+// argmax |x| (first index on ties): block partials then a final reduce
+__global__ void k_amax_part(const double* __restrict__ x, int64_t n, double* __restrict__ pv, int64_t* __restrict__ pi) {
+  double bv = -1.0;
+  int64_t bi = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = fabs(x[i]);
+    if (a > bv || (a == bv && i < bi)) { bv = a; bi = i; }
+  }
+  for (int o = 16; o; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  __shared__ double sv[32];
+  __shared__ int64_t si[32];
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = bv; si[threadIdx.x >> 5] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] > bv || (sv[w] == bv && si[w] < bi)) { bv = sv[w]; bi = si[w]; }
+    pv[blockIdx.x] = bv;
+    pi[blockIdx.x] = bi;
+  }
+}
+
+__global__ void k_phase_sign(const double* __restrict__ x, const double* __restrict__ pv,
+                             const int64_t* __restrict__ pi, int nb, double* __restrict__ sgn) {
+  double bv = -1.0;
+  int64_t bi = 0;
+  for (int b = 0; b < nb; ++b)
+    if (pv[b] > bv || (pv[b] == bv && pi[b] < bi)) { bv = pv[b]; bi = pi[b]; }
+  *sgn = x[bi] < 0.0 ? -1.0 : 1.0;
+}
+
+__global__ void k_apply_sign(double* __restrict__ x, int64_t n, const double* __restrict__ sgn) {
+  const double s = *sgn;
+  if (s > 0.0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = -x[i];
+}
+
+__global__ void k_unit_min_diag(double* __restrict__ x, const double* __restrict__ diag, int64_t n) {
+  // single block: index of the smallest diagonal element (first on ties)
+  double bv = 1e300;
+  int64_t bi = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = diag[i];
+    if (a < bv || (a == bv && i < bi)) { bv = a; bi = i; }
+  }
+  __shared__ double sv[1024];
+  __shared__ int64_t si[1024];
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < (int)blockDim.x; ++t)
+      if (sv[t] < bv || (sv[t] == bv && si[t] < bi)) { bv = sv[t]; bi = si[t]; }
+    x[bi] = 1.0;
+  }
+}
+
+struct Dav {
+  hci_ctx* ctx;
+  int64_t n, ld;
+  double *V, *W, *x, *wy, *t, *part;
+  DavDev* d;
+  int nblk;
+
+  hci_status dots(const double* Vb, int k, const double* w, double* out) {
+    if (k <= 8) k_dots<8><<<nblk, DBLOCK, 0, ctx->st>>>(Vb, ld, k, w, n, part);
+    else k_dots<LDG><<<nblk, DBLOCK, 0, ctx->st>>>(Vb, ld, k, w, n, part);
+    k_reduce<<<1, 32 * LDG, 0, ctx->st>>>(part, nblk, k, out);
+    HCI_CUDA(ctx, cudaGetLastError());
+    return HCI_OK;
+  }
+  hci_status sigma(int slot) { return sigma_apply(ctx, V + (int64_t)slot * ld, W + (int64_t)slot * ld, 1); }
+};
+
+}  // namespace
+
+extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout, double* energy,
+                                   double tol, int maxit, int* iters) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_davidson: null context");
+  if (nV <= 0 || !keys || !c_inout || !energy)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson: empty space or null pointer");
+  if (iters) *iters = 0;
+  HCI_TRY(graph_ensure(ctx, keys, nV));
+  Dav D;
+  D.ctx = ctx;
+  D.n = nV;
+  D.ld = (nV + 31) & ~(int64_t)31;
+  D.nblk = grid_for(nV, DBLOCK, 152 * 8);
+  HCI_TRY(ensure_buf(ctx, ctx->d_vb, (size_t)D.ld * (MAXSUB + 3) * 8));
+  HCI_TRY(ensure_buf(ctx, ctx->d_wb, (size_t)D.ld * MAXSUB * 8));
+  HCI_TRY(ensure_buf(ctx, ctx->d_part, (size_t)(D.nblk + 1) * LDG * 8));
+  HCI_TRY(ensure_buf(ctx, ctx->d_small, sizeof(DavDev) + (size_t)(D.nblk + 1) * 16));
+  D.V = bp<double>(ctx->d_vb);
+  D.W = bp<double>(ctx->d_wb);
+  D.x = D.V + (int64_t)MAXSUB * D.ld;
+  D.wy = D.x + D.ld;
+  D.t = D.wy + D.ld;
+  D.part = bp<double>(ctx->d_part);
+  D.d = bp<DavDev>(ctx->d_small);
+  double* amax_v = reinterpret_cast<double*>(bp<char>(ctx->d_small) + sizeof(DavDev));
+  int64_t* amax_i = reinterpret_cast<int64_t*>(amax_v + D.nblk);
+  const double* diag = bp<double>(ctx->graph.diag);
+  cudaStream_t st = ctx->st;
+  HCI_CUDA(ctx, cudaMemsetAsync(D.d, 0, sizeof(DavDev), st));
+  // start vector
+  HCI_CUDA(ctx, cudaMemcpyAsync(D.V, c_inout, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+  HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
+  double nrm2 = 0.0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) {
+    HCI_CUDA(ctx, cudaMemsetAsync(D.V, 0, (size_t)nV * 8, st));
+    k_unit_min_diag<<<1, 1024, 0, st>>>(D.V, diag, nV);
+  } else {
+    k_scale_const<<<D.nblk, DBLOCK, 0, st>>>(D.V, nV, 1.0 / std::sqrt(nrm2));
+  }
+  HCI_TRY(D.sigma(0));
+  HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots));
+  k_set_gcol<<<1, 32, 0, st>>>(D.d, 0);
+  int k = 1;
+  bool converged = false;
+  double theta = 0.0, rn = 0.0;
+  int it = 0;
+  for (; it < maxit; ++it) {
+    k_jacobi<<<1, 32, 0, st>>>(D.d, k);
+    k_ritz<<<D.nblk, DBLOCK, 0, st>>>(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
+    k_reduce<<<1, 32, 0, st>>>(D.part, D.nblk, 1, &D.d->rnorm2);
+    HCI_CUDA(ctx, cudaGetLastError());
+    double hv[2];
+    HCI_CUDA(ctx, cudaMemcpyAsync(&hv[0], &D.d->theta, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&hv[1], &D.d->rnorm2, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    theta = hv[0];
+    rn = std::sqrt(hv[1]);
+    if (!std::isfinite(theta) || !std::isfinite(rn))
+      return hci_fail(ctx, HCI_ERR_CUDA, "hci_davidson: non-finite Ritz value or residual");
+    if (rn <= tol) {
+      converged = true;
+      break;
+    }
+    if (k == MAXSUB) {
+      // restart from the current Ritz vector
+      HCI_CUDA(ctx, cudaMemcpyAsync(D.V, D.x, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+      HCI_CUDA(ctx, cudaMemcpyAsync(D.W, D.wy, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+      HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
+      k_scale_by<<<D.nblk, DBLOCK, 0, st>>>(D.V, D.W, nV, &D.d->nrm2);
+      HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots));
+      k_set_gcol<<<1, 32, 0, st>>>(D.d, 0);
+      k = 1;
+    }
+    // orthogonalise the correction twice, normalise
+    for (int pass = 0; pass < 2; ++pass) {
+      HCI_TRY(D.dots(D.V, k, D.t, D.d->dots));
+      k_orth<<<D.nblk, DBLOCK, 0, st>>>(D.V, D.ld, k, D.d, D.t, nV);
+    }
+    HCI_TRY(D.dots(D.t, 1, D.t, &D.d->nrm2));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    if (!(nrm2 > 1e-26)) {
+      // the correction lies in the subspace: no further progress possible
+      break;
+    }
+    double* slot = D.V + (int64_t)k * D.ld;
+    k_scale_const<<<D.nblk, DBLOCK, 0, st>>>(D.t, nV, 1.0 / std::sqrt(nrm2));
+    HCI_CUDA(ctx, cudaMemcpyAsync(slot, D.t, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+    HCI_TRY(D.sigma(k));
+    HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots));
+    k_set_gcol<<<1, 32, 0, st>>>(D.d, k);
+    ++k;
+  }
+  if (iters) *iters = it + (converged ? 1 : 0);
+  // final vector: normalise, fix phase
+  HCI_TRY(D.dots(D.x, 1, D.x, &D.d->nrm2));
+  k_scale_by<<<D.nblk, DBLOCK, 0, st>>>(D.x, nullptr, nV, &D.d->nrm2);
+  k_amax_part<<<D.nblk, DBLOCK, 0, st>>>(D.x, nV, amax_v, amax_i);
+  k_phase_sign<<<1, 1, 0, st>>>(D.x, amax_v, amax_i, D.nblk, &D.d->dots[0]);
+  k_apply_sign<<<D.nblk, DBLOCK, 0, st>>>(D.x, nV, &D.d->dots[0]);
+  HCI_CUDA(ctx, cudaMemcpyAsync(c_inout, D.x, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+  HCI_CUDA(ctx, cudaGetLastError());
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  *energy = theta;
+  if (!converged && rn > tol)
+    return hci_fail(ctx, HCI_ERR_NOT_CONVERGED, "hci_davidson: residual %.3e > tol %.3e after %d iterations", rn, tol,
+                    it);
+  return HCI_OK;
+}

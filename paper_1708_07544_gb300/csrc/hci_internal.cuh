@@ -1,0 +1,123 @@
+// Internal declarations shared by the translation units of libhci.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/hci.h"
+
+#define HCI_MAXORB 64
+
+// Grow-only device buffer, stream-ordered allocation on the context stream.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Connection graph of one determinant space (Sec. IV: "all single and double
+// excitations between pairs of determinants in the variational wavefunction
+// are generated in order to evaluate the Hamiltonian").
+struct Graph {
+  bool valid = false;
+  int64_t nV = 0;
+  uint64_t hash = 0;
+  int64_t nnz = 0;           // off-diagonal entries (both orientations stored)
+  DevBuf rowptr;             // int64 [nV+1]
+  DevBuf col;                // int32 [nnz]
+  DevBuf val;                // double [nnz]
+  DevBuf diag;               // double [nV]
+  DevBuf keys;               // copy of the space's keys [nV][2]
+};
+
+struct Lists {
+  bool built = false;
+  int n = 0;
+  int len_opp = 0, len_same = 0;     // entries per list
+  int npair_same = 0;                // n(n-1)/2
+  DevBuf opp_mag, opp_tgt;           // [n*n][len_opp] double / uint16 (r | s<<8)
+  DevBuf same_mag, same_tgt;         // [npair_same][len_same]
+  DevBuf single_bound;               // [n*n] upper bound of |H| for single p->r
+  double max_opp = 0, max_same = 0, max_single = 0;
+};
+
+struct hci_ctx {
+  int n = 0, na = 0, nb = 0;
+  double ecore = 0;
+  cudaStream_t st = nullptr;
+  DevBuf h, eri;                     // device copies
+  DevBuf jk_same, j_opp;             // n^3 tables for single excitations
+  Lists lists;
+  Graph graph;
+  // scratch
+  DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist;
+  DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
+  DevBuf d_vb, d_wb, d_diag, d_small, d_part;
+  int64_t last_candidates = 0;
+  char err[512] = {0};
+};
+
+// ----------------------------------------------------------------------------
+// error helpers
+// ----------------------------------------------------------------------------
+hci_status hci_fail(hci_ctx* ctx, hci_status code, const char* fmt, ...);
+
+#define HCI_CUDA(ctx, call)                                                                \
+  do {                                                                                     \
+    cudaError_t _e = (call);                                                               \
+    if (_e != cudaSuccess)                                                                 \
+      return hci_fail((ctx), HCI_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,     \
+                      cudaGetErrorString(_e));                                             \
+  } while (0)
+
+#define HCI_TRY(expr)                 \
+  do {                                \
+    hci_status _s = (expr);           \
+    if (_s != HCI_OK) return _s;      \
+  } while (0)
+
+// Ensure buf holds at least `bytes` (contents are NOT preserved on growth).
+hci_status ensure_buf(hci_ctx* ctx, DevBuf& b, size_t bytes);
+void free_buf(cudaStream_t st, DevBuf& b);
+
+template <class T>
+inline T* bp(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+inline int grid_for(int64_t work, int block, int max_blocks = 152 * 16) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+// ----------------------------------------------------------------------------
+// primitives (prims.cu)
+// ----------------------------------------------------------------------------
+// Exclusive scan of int64 values in place-free form: out[i] = sum_{j<i} in[j];
+// returns the total through *total_dev (device pointer, may be NULL).
+hci_status scan_i64(hci_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev);
+// Stable LSD radix sort of 128-bit keys (a = high word, b = low word) on
+// the low `bits_a` / `bits_b` bits.  Result in keys (tmp is scratch of same size).
+hci_status sort_keys(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, int64_t n, int bits_a, int bits_b);
+// 64-bit content hash of a key array (device result).
+hci_status hash_keys(hci_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t* hash_host);
+// Checks that keys are strictly ascending (device reduction); *ok_host = 1 if sorted.
+hci_status check_sorted(hci_ctx* ctx, const uint64_t* keys, int64_t n, int* ok_host);
+
+// graph.cu
+hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
+hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
+hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec);
+
+// device helpers -------------------------------------------------------------
+__device__ __forceinline__ int popc64(uint64_t x) { return __popcll(x); }
+
+// (-1)^(number of set bits of s strictly between orbitals p and r)
+__device__ __forceinline__ double exc_phase(uint64_t s, int p, int r) {
+  int lo = p < r ? p : r, hi = p < r ? r : p;
+  uint64_t mask = ((hi >= 64) ? ~0ull : ((1ull << hi) - 1ull)) & ~((2ull << lo) - 1ull);
+  return (__popcll(s & mask) & 1) ? -1.0 : 1.0;
+}

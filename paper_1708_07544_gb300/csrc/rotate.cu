@@ -1,0 +1,308 @@
+// Active-active orbital rotation of the integrals and its adjoint
+// (Sec. III.A: the integrals depend on kappa through U = exp(kappa);
+// Sec. III.B, Eq. vdedk2: dE/dkappa = sum dH/dkappa contracted with the RDMs).
+//
+// Forward:  h' = U^T h U,  (pq|rs)' = sum U_ap U_bq U_cr U_ds (ab|cd)
+//           as four quarter transforms out[J][p] = sum_a in[a][J] M[a][p]
+//           that each rotate the leading index to the back.
+// Backward: dE/dh = U g1 U^T, dE/d(ab|cd) = sum D_pqrs U_ap U_bq U_cr U_ds
+//           with D = rdm2/2, and dE/dU = h U g1^T + h^T U g1 + 4 sum_bcd
+//           (xb|cd) T[y][b][c][d], T = D with its last three indices
+//           back-transformed (the four index positions of a real state with
+//           8-fold symmetric integrals contribute equally);
+//           dE/dkappa = L_exp(kappa^T, dE/dU), the Frechet derivative of
+//           exp at kappa^T, read off exp([[k^T, G], [0, k^T]]).
+// FP64 on CUDA cores: double-precision tensor throughput on this part is no
+// higher than the FP64 pipe, and the contraction is a small share of a solve.
+#include <cmath>
+
+#include "hci_internal.cuh"
+
+namespace {
+
+// C = alpha * op(A) op(B) + beta * C, m x m row-major, one thread per entry
+__global__ void k_mm(int m, const double* __restrict__ A, int tA, const double* __restrict__ B, int tB,
+                     double* __restrict__ C, double alpha, double beta) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  int i = t / m, j = t % m;
+  double acc = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double a = tA ? A[k * m + i] : A[i * m + k];
+    double b = tB ? B[j * m + k] : B[k * m + j];
+    acc = fma(a, b, acc);
+  }
+  C[t] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * C[t]);
+}
+
+// E = I + X * E / k   (Horner step of the Taylor series), X E in tmp
+__global__ void k_horner(int m, const double* __restrict__ XE, double* __restrict__ E, double invk) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  int i = t / m, j = t % m;
+  E[t] = (i == j ? 1.0 : 0.0) + XE[t] * invk;
+}
+
+__global__ void k_eye_plus(int m, const double* __restrict__ X, double s, double* __restrict__ E) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  int i = t / m, j = t % m;
+  E[t] = (i == j ? 1.0 : 0.0) + s * X[t];
+}
+
+__global__ void k_scale_copy(int64_t cnt, const double* __restrict__ in, double s, double* __restrict__ out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = s * in[t];
+}
+
+// max column abs-sum (1-norm) of an m x m matrix, single block
+__global__ void k_norm1(int m, const double* __restrict__ A, double* out) {
+  __shared__ double s[1024];
+  double v = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double cs = 0.0;
+    for (int i = 0; i < m; ++i) cs += fabs(A[i * m + j]);
+    v = fmax(v, cs);
+  }
+  s[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) r = fmax(r, s[t]);
+    *out = r;
+  }
+}
+
+// block matrix [[K^T, G], [0, K^T]] of size 2n
+__global__ void k_frechet_block(int n, const double* __restrict__ K, const double* __restrict__ G, double* __restrict__ B) {
+  int m = 2 * n;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  int i = t / m, j = t % m;
+  double v = 0.0;
+  if (i < n && j < n) v = K[j * n + i];
+  else if (i >= n && j >= n) v = K[(j - n) * n + (i - n)];
+  else if (i < n && j >= n) v = G[i * n + (j - n)];
+  B[t] = v;
+}
+
+__global__ void k_upper_right(int n, const double* __restrict__ B, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  int i = t / n, j = t % n;
+  out[t] = B[i * 2 * n + n + j];
+}
+
+__global__ void k_eye(int n, double* __restrict__ I) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * n) I[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+// out[J*n + p] = sum_a in[a*N3 + J] * M[a*n + p], J < N3 = n^3
+constexpr int QT_J = 32;
+__global__ void __launch_bounds__(256) k_qtrans(int n, const double* __restrict__ in, const double* __restrict__ M,
+                                                double* __restrict__ out) {
+  extern __shared__ double sm[];
+  double* Ms = sm;               // n*n
+  double* tile = sm + n * n;     // n * QT_J
+  const int64_t N3 = (int64_t)n * n * n;
+  const int64_t J0 = (int64_t)blockIdx.x * QT_J;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ms[t] = M[t];
+  for (int t = threadIdx.x; t < n * QT_J; t += blockDim.x) {
+    int a = t / QT_J, jj = t % QT_J;
+    int64_t J = J0 + jj;
+    tile[a * QT_J + jj] = J < N3 ? in[(int64_t)a * N3 + J] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < QT_J * n; t += blockDim.x) {
+    int jj = t / n, p = t % n;
+    int64_t J = J0 + jj;
+    if (J >= N3) continue;
+    double acc = 0.0;
+    for (int a = 0; a < n; ++a) acc = fma(tile[a * QT_J + jj], Ms[a * n + p], acc);
+    out[J * n + p] = acc;
+  }
+}
+
+// partial[b][x][y] = sum_{J in chunk b} A[x][J] B[y][J]  (A, B: n x K)
+constexpr int NT_CH = 64;
+__global__ void __launch_bounds__(256) k_gemm_nt_part(int n, int64_t K, const double* __restrict__ A,
+                                                      const double* __restrict__ B, double* __restrict__ partial) {
+  extern __shared__ double sm[];
+  double* At = sm;                 // n * NT_CH
+  double* Bt = sm + n * NT_CH;     // n * NT_CH
+  const int64_t J0 = (int64_t)blockIdx.x * NT_CH;
+  for (int t = threadIdx.x; t < n * NT_CH; t += blockDim.x) {
+    int x = t / NT_CH, jj = t % NT_CH;
+    int64_t J = J0 + jj;
+    At[t] = J < K ? A[(int64_t)x * K + J] : 0.0;
+    Bt[t] = J < K ? B[(int64_t)x * K + J] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int x = t / n, y = t % n;
+    double acc = 0.0;
+    for (int jj = 0; jj < NT_CH; ++jj) acc = fma(At[x * NT_CH + jj], Bt[y * NT_CH + jj], acc);
+    partial[(int64_t)blockIdx.x * n * n + t] = acc;
+  }
+}
+
+__global__ void k_sum_parts(int nn, int nparts, const double* __restrict__ partial, double scale,
+                            double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nn) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += partial[(int64_t)b * nn + t];
+  out[t] += scale * s;
+}
+
+struct Scratch {
+  cudaStream_t st;
+  void* ptrs[16];
+  int count = 0;
+  double* get(size_t doubles) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, doubles * 8 + 64, st) != cudaSuccess) return nullptr;
+    ptrs[count++] = p;
+    return reinterpret_cast<double*>(p);
+  }
+  ~Scratch() {
+    for (int i = 0; i < count; ++i) cudaFreeAsync(ptrs[i], st);
+  }
+};
+
+inline unsigned blocks(int64_t work, int b = 256) { return (unsigned)((work + b - 1) / b); }
+
+hci_status mm(cudaStream_t st, int m, const double* A, int tA, const double* B, int tB, double* C, double alpha,
+              double beta) {
+  k_mm<<<blocks((int64_t)m * m), 256, 0, st>>>(m, A, tA, B, tB, C, alpha, beta);
+  return HCI_OK;
+}
+
+// E = exp(A) for an m x m matrix; w1, w2, w3 scratch of m*m
+hci_status expm_dev(cudaStream_t st, int m, const double* A, double* E, double* w1, double* w2, double* w3,
+                    double* dscal) {
+  k_norm1<<<1, 256, 0, st>>>(m, A, dscal);
+  double nrm = 0.0;
+  if (cudaMemcpyAsync(&nrm, dscal, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HCI_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HCI_ERR_CUDA;
+  if (!std::isfinite(nrm)) return HCI_ERR_INVALID;
+  int s = 0;
+  while (nrm / std::ldexp(1.0, s) > 0.5) ++s;
+  const double sc = std::ldexp(1.0, -s);
+  k_scale_copy<<<blocks((int64_t)m * m), 256, 0, st>>>((int64_t)m * m, A, sc, w1);   // X
+  // Horner: E = I + X/18; E = I + X E / k for k = 17..1
+  const int deg = 18;
+  k_eye_plus<<<blocks((int64_t)m * m), 256, 0, st>>>(m, w1, 1.0 / deg, E);
+  for (int k = deg - 1; k >= 1; --k) {
+    mm(st, m, w1, 0, E, 0, w2, 1.0, 0.0);
+    k_horner<<<blocks((int64_t)m * m), 256, 0, st>>>(m, w2, E, 1.0 / k);
+  }
+  for (int i = 0; i < s; ++i) {
+    mm(st, m, E, 0, E, 0, w3, 1.0, 0.0);
+    cudaMemcpyAsync(E, w3, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? HCI_OK : HCI_ERR_CUDA;
+}
+
+void qtrans(cudaStream_t st, int n, const double* in, const double* M, double* out) {
+  const int64_t N3 = (int64_t)n * n * n;
+  size_t smem = (size_t)(n * n + n * QT_J) * 8;
+  k_qtrans<<<blocks(N3, QT_J), 256, smem, st>>>(n, in, M, out);
+}
+
+}  // namespace
+
+extern "C" hci_status hci_rotate(int norb, const double* kappa, const double* h, const double* eri, double* U,
+                                 double* h_out, double* eri_out, void* stream) {
+  const int n = norb;
+  if (n < 1 || n > HCI_MAXORB) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate: norb=%d outside [1,64]", n);
+  if (!kappa || !h || !eri || !U || !h_out || !eri_out)
+    return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch S{st};
+  const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+  double *w1 = S.get(n2), *w2 = S.get(n2), *w3 = S.get(n2), *ds = S.get(8), *t4 = S.get(n4);
+  if (!w1 || !w2 || !w3 || !ds || !t4) return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate: allocation failed");
+  cudaFuncSetAttribute(k_qtrans, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 * 64 + 64 * QT_J) * 8);
+  hci_status s = expm_dev(st, n, kappa, U, w1, w2, w3, ds);
+  if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate: matrix exponential failed");
+  mm(st, n, h, 0, U, 0, w1, 1.0, 0.0);          // h U
+  mm(st, n, U, 1, w1, 0, h_out, 1.0, 0.0);      // U^T h U
+  qtrans(st, n, eri, U, t4);
+  qtrans(st, n, t4, U, eri_out);
+  qtrans(st, n, eri_out, U, t4);
+  qtrans(st, n, t4, U, eri_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate: %s", cudaGetErrorString(e));
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate: %s", cudaGetErrorString(e));
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const double* h, const double* eri,
+                                          const double* rdm1, const double* rdm2, double* dh, double* deri,
+                                          double* dkappa, void* stream) {
+  const int n = norb;
+  if (n < 1 || n > HCI_MAXORB)
+    return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate_backward: norb=%d outside [1,64]", n);
+  if (!kappa || !h || !eri || !rdm1 || !rdm2)
+    return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate_backward: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch S{st};
+  const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+  const int m2 = 2 * n;
+  double *U = S.get(n2), *Ut = S.get(n2), *I = S.get(n2), *w1 = S.get(n2), *gU = S.get(n2);
+  double *b1 = S.get((size_t)m2 * m2), *b2 = S.get((size_t)m2 * m2), *b3 = S.get((size_t)m2 * m2),
+         *b4 = S.get((size_t)m2 * m2), *b5 = S.get((size_t)m2 * m2), *ds = S.get(8);
+  double *D = S.get(n4), *t4 = S.get(n4);
+  if (!U || !Ut || !I || !w1 || !gU || !b1 || !b2 || !b3 || !b4 || !b5 || !ds || !D || !t4)
+    return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed");
+  cudaFuncSetAttribute(k_qtrans, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 * 64 + 64 * QT_J) * 8);
+  cudaFuncSetAttribute(k_gemm_nt_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * NT_CH * 8);
+  hci_status s = expm_dev(st, n, kappa, U, w1, b1, b2, ds);
+  if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_backward: matrix exponential failed");
+  k_eye<<<blocks((int64_t)n2), 256, 0, st>>>(n, I);
+  // U^T as a matrix for the back-transforms: M[a][p] = U[p][a]
+  mm(st, n, U, 1, I, 0, Ut, 1.0, 0.0);
+  if (dh) {
+    mm(st, n, rdm1, 0, U, 1, w1, 1.0, 0.0);     // g1 U^T
+    mm(st, n, U, 0, w1, 0, dh, 1.0, 0.0);       // U g1 U^T
+  }
+  k_scale_copy<<<blocks((int64_t)n4), 256, 0, st>>>((int64_t)n4, rdm2, 0.5, D);
+  if (deri) {
+    qtrans(st, n, D, Ut, t4);
+    qtrans(st, n, t4, Ut, deri);
+    qtrans(st, n, deri, Ut, t4);
+    qtrans(st, n, t4, Ut, deri);
+  }
+  if (dkappa) {
+    // h-part: h U g1^T + h^T U g1
+    mm(st, n, h, 0, U, 0, w1, 1.0, 0.0);
+    mm(st, n, w1, 0, rdm1, 1, gU, 1.0, 0.0);
+    mm(st, n, h, 1, U, 0, w1, 1.0, 0.0);
+    mm(st, n, w1, 0, rdm1, 0, gU, 1.0, 1.0);
+    // T[y][b][c][d] = sum_qrs U_bq U_cr U_ds D[y][q][r][s]
+    double* T = t4;
+    qtrans(st, n, D, I, T);          // (q r s y)
+    qtrans(st, n, T, Ut, D);         // (r s y b)
+    qtrans(st, n, D, Ut, T);         // (s y b c)
+    qtrans(st, n, T, Ut, D);         // (y b c d)
+    const int64_t K = (int64_t)n * n * n;
+    const int nparts = (int)((K + NT_CH - 1) / NT_CH);
+    double* part = S.get((size_t)nparts * n2);
+    if (!part) return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed");
+    k_gemm_nt_part<<<nparts, 256, (size_t)2 * n * NT_CH * 8, st>>>(n, K, eri, D, part);
+    k_sum_parts<<<blocks((int64_t)n2), 256, 0, st>>>((int)n2, nparts, part, 4.0, gU);
+    // dkappa = L_exp(kappa^T, gU)
+    k_frechet_block<<<blocks((int64_t)m2 * m2), 256, 0, st>>>(n, kappa, gU, b1);
+    s = expm_dev(st, m2, b1, b2, b3, b4, b5, ds);
+    if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_backward: Frechet exponential failed");
+    k_upper_right<<<blocks((int64_t)n2), 256, 0, st>>>(n, b2, dkappa);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));
+  return HCI_OK;
+}

@@ -1,0 +1,385 @@
+// Selection step of variational HCI (Sec. II.A, Eq. criteria, Fig. 1b):
+// heat-bath walk over the sorted double-excitation lists, exact singles
+// behind an upper-bound screen, sort-based deduplication against V, and the
+// sorted merge V^{mu+1} = V^mu + C^mu.
+#include "hci_internal.cuh"
+
+namespace {
+
+constexpr int SEL_WARPS = 8;          // warps per CTA in the walk kernels
+
+struct WalkArgs {
+  int n, na, nb;
+  const ulonglong2* keys;
+  const double* c;
+  int64_t nV;
+  double eps1;
+  int accept_all;
+  const double* opp_mag;
+  const uint16_t* opp_tgt;
+  int Lo;
+  const double* same_mag;
+  const uint16_t* same_tgt;
+  int Ls;
+  double max_dbl;        // largest magnitude in any list
+  const double* h;
+  const double* jk_same;
+  const double* j_opp;
+  const double* single_bound;
+  double max_single;
+  ulonglong2* out;
+  int64_t cap;
+  unsigned long long* counter;     // [0] candidates, [1] next det (work queue)
+};
+
+__device__ __forceinline__ void tri_decode_dev(int t, int& lo, int& hi) {
+  int h = (int)((1.0 + sqrt(1.0 + 8.0 * (double)t)) * 0.5);
+  while (h * (h - 1) / 2 > t) --h;
+  while ((h + 1) * h / 2 <= t) ++h;
+  hi = h;
+  lo = t - h * (h - 1) / 2;
+}
+
+// Warp-aggregated append of one optional key per lane.
+__device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, const WalkArgs& A) {
+  const int lane = threadIdx.x & 31;
+  unsigned m = __ballot_sync(0xffffffffu, emit);
+  if (!m) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&A.counter[0], (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (emit) {
+    unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+    if ((int64_t)idx < A.cap) A.out[idx] = key;
+  }
+}
+
+// Compact the occupied orbitals of a spin string into smem (ascending).
+__device__ __forceinline__ void occ_list(uint64_t s, int n, int* occ) {
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  for (int p0 = 0; p0 < n; p0 += 32) {
+    int p = p0 + lane;
+    bool o = p < n && ((s >> p) & 1ull);
+    unsigned m = __ballot_sync(0xffffffffu, o);
+    if (o) occ[base + __popc(m & ((1u << lane) - 1u))] = p;
+    base += __popc(m);
+  }
+  __syncwarp();
+}
+
+// Largest L with mag[L-1]*absc > eps1 (mag sorted descending).
+__device__ __forceinline__ int prefix_len(const double* __restrict__ mag, int len, double absc, double eps1) {
+  int lo = 0, hi = len;       // invariant: entries [0,lo) pass, [hi,len) fail
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (mag[mid] * absc > eps1) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Doubles: one warp per determinant (dynamic queue).  For every occupied
+// pair the list prefix with |v||c_i| > eps1 is walked by the whole warp and
+// every target whose orbitals are empty is emitted.
+__global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_doubles(WalkArgs A) {
+  __shared__ int s_occ[SEL_WARPS][2][HCI_MAXORB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int* occA = s_occ[w][0];
+  int* occB = s_occ[w][1];
+  const int Paa = A.na * (A.na - 1) / 2, Pbb = A.nb * (A.nb - 1) / 2, Pab = A.na * A.nb;
+  const int P = Paa + Pbb + Pab;
+  while (true) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(&A.counter[1], 1ull);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if ((int64_t)i >= A.nV) break;
+    const double absc = fabs(A.c[i]);
+    if (!A.accept_all && !(A.max_dbl * absc > A.eps1)) continue;
+    const ulonglong2 k = A.keys[i];
+    occ_list(k.x, A.n, occA);
+    occ_list(k.y, A.n, occB);
+    for (int base = 0; base < P; base += 32) {
+      int t = base + lane;
+      int kind = -1, p = 0, q = 0, L = 0;
+      const double* mag = nullptr;
+      int listid = 0;
+      if (t < P) {
+        int len;
+        if (t < Paa) {
+          int lo, hi;
+          tri_decode_dev(t, lo, hi);
+          p = occA[lo]; q = occA[hi]; kind = 0;
+          listid = q * (q - 1) / 2 + p;
+          mag = A.same_mag + (int64_t)listid * A.Ls; len = A.Ls;
+        } else if (t < Paa + Pbb) {
+          int lo, hi;
+          tri_decode_dev(t - Paa, lo, hi);
+          p = occB[lo]; q = occB[hi]; kind = 1;
+          listid = q * (q - 1) / 2 + p;
+          mag = A.same_mag + (int64_t)listid * A.Ls; len = A.Ls;
+        } else {
+          int u = t - Paa - Pbb;
+          p = occA[u / A.nb]; q = occB[u % A.nb]; kind = 2;
+          listid = p * A.n + q;
+          mag = A.opp_mag + (int64_t)listid * A.Lo; len = A.Lo;
+        }
+        if (A.accept_all) L = len;
+        else if (mag[0] * absc > A.eps1) L = prefix_len(mag, len, absc, A.eps1);
+      }
+      unsigned act = __ballot_sync(0xffffffffu, L > 0);
+      while (act) {
+        int src = __ffs(act) - 1;
+        act &= act - 1;
+        int sk = __shfl_sync(0xffffffffu, kind, src);
+        int sl = __shfl_sync(0xffffffffu, listid, src);
+        int sp = __shfl_sync(0xffffffffu, p, src);
+        int sq = __shfl_sync(0xffffffffu, q, src);
+        int sL = __shfl_sync(0xffffffffu, L, src);
+        const uint16_t* tg = sk == 2 ? A.opp_tgt + (int64_t)sl * A.Lo : A.same_tgt + (int64_t)sl * A.Ls;
+        for (int k0 = 0; k0 < sL; k0 += 32) {
+          int e = k0 + lane;
+          bool emit = false;
+          ulonglong2 key = k;
+          if (e < sL) {
+            uint16_t tt = tg[e];
+            int r = tt & 0xff, s = tt >> 8;
+            if (sk == 0) {
+              if (!((k.x >> r) & 1ull) && !((k.x >> s) & 1ull)) {
+                emit = true;
+                key.x = k.x ^ (1ull << sp) ^ (1ull << sq) ^ (1ull << r) ^ (1ull << s);
+              }
+            } else if (sk == 1) {
+              if (!((k.y >> r) & 1ull) && !((k.y >> s) & 1ull)) {
+                emit = true;
+                key.y = k.y ^ (1ull << sp) ^ (1ull << sq) ^ (1ull << r) ^ (1ull << s);
+              }
+            } else {
+              if (!((k.x >> r) & 1ull) && !((k.y >> s) & 1ull)) {
+                emit = true;
+                key.x = k.x ^ (1ull << sp) ^ (1ull << r);
+                key.y = k.y ^ (1ull << sq) ^ (1ull << s);
+              }
+            }
+          }
+          warp_emit(emit, key, A);
+        }
+      }
+    }
+  }
+}
+
+// Singles: one warp per determinant; each lane screens (p->r) with the
+// determinant-independent bound, then evaluates H_ai exactly in the same
+// summation order as the textbook rule (k ascending, same spin then
+// opposite spin per k).
+__global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int n = A.n;
+  const int Pa = A.na * (n - A.na), Pb = A.nb * (n - A.nb);
+  const int P = Pa + Pb;
+  while (true) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(&A.counter[1], 1ull);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if ((int64_t)i >= A.nV) break;
+    const double absc = fabs(A.c[i]);
+    if (!A.accept_all && !(A.max_single * absc > A.eps1)) continue;
+    const ulonglong2 k = A.keys[i];
+    for (int base = 0; base < P; base += 32) {
+      int t = base + lane;
+      bool emit = false;
+      ulonglong2 key = k;
+      if (t < P) {
+        int spin = t < Pa ? 0 : 1;
+        int u = spin == 0 ? t : t - Pa;
+        uint64_t s = spin == 0 ? k.x : k.y;
+        uint64_t o = spin == 0 ? k.y : k.x;
+        int nocc = spin == 0 ? A.na : A.nb;
+        int nvirt = n - nocc;
+        int oi = u / nvirt, vi = u % nvirt;
+        // oi-th occupied and vi-th empty orbital of s
+        int p = -1, r = -1, co = 0, cv = 0;
+        for (int x = 0; x < n; ++x) {
+          if ((s >> x) & 1ull) { if (co == oi) p = x; ++co; }
+          else { if (cv == vi) r = x; ++cv; }
+        }
+        if (A.accept_all) {
+          emit = true;
+        } else if (A.single_bound[p * n + r] * absc > A.eps1) {
+          double v = A.h[p * n + r];
+          const double* js = A.jk_same + ((int64_t)p * n + r) * n;
+          const double* jo = A.j_opp + ((int64_t)p * n + r) * n;
+          for (int x = 0; x < n; ++x) {
+            if ((s >> x) & 1ull) v += js[x];
+            if ((o >> x) & 1ull) v += jo[x];
+          }
+          emit = fabs(v) * absc > A.eps1;
+        }
+        if (emit) {
+          uint64_t ns = s ^ (1ull << p) ^ (1ull << r);
+          if (spin == 0) key.x = ns; else key.y = ns;
+        }
+      }
+      warp_emit(emit, key, A);
+    }
+  }
+}
+
+__device__ __forceinline__ bool key_less(ulonglong2 a, ulonglong2 b) {
+  return a.x < b.x || (a.x == b.x && a.y < b.y);
+}
+__device__ __forceinline__ bool key_eq(ulonglong2 a, ulonglong2 b) { return a.x == b.x && a.y == b.y; }
+
+// number of elements of sorted arr[0,n) strictly less than key
+__device__ __forceinline__ int64_t lower_bound(const ulonglong2* __restrict__ arr, int64_t n, ulonglong2 key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (key_less(arr[mid], key)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// flag = first of its run in the sorted candidates and not already in V
+__global__ void k_flag_new(const ulonglong2* __restrict__ cand, int64_t m, const ulonglong2* __restrict__ V,
+                           int64_t nV, int64_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    ulonglong2 k = cand[i];
+    int64_t f = 0;
+    if (i == 0 || !key_eq(k, cand[i - 1])) {
+      int64_t pos = lower_bound(V, nV, k);
+      f = (pos < nV && key_eq(V[pos], k)) ? 0 : 1;
+    }
+    flag[i] = f;
+  }
+}
+
+__global__ void k_compact(const ulonglong2* __restrict__ cand, int64_t m, const int64_t* __restrict__ flag,
+                          const int64_t* __restrict__ pos, ulonglong2* __restrict__ out, int64_t cap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (flag[i] && pos[i] < cap) out[pos[i]] = cand[i];
+  }
+}
+
+__global__ void k_merge_old(const ulonglong2* __restrict__ V, const double* __restrict__ c, int64_t nV,
+                            const ulonglong2* __restrict__ N, int64_t nN, ulonglong2* __restrict__ out,
+                            double* __restrict__ outc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nV; i += (int64_t)gridDim.x * blockDim.x) {
+    ulonglong2 k = V[i];
+    int64_t pos = i + lower_bound(N, nN, k);
+    out[pos] = k;
+    if (outc) outc[pos] = c ? c[i] : 0.0;
+  }
+}
+
+__global__ void k_merge_new(const ulonglong2* __restrict__ V, int64_t nV, const ulonglong2* __restrict__ N,
+                            int64_t nN, ulonglong2* __restrict__ out, double* __restrict__ outc) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nN; j += (int64_t)gridDim.x * blockDim.x) {
+    ulonglong2 k = N[j];
+    int64_t pos = j + lower_bound(V, nV, k);
+    out[pos] = k;
+    if (outc) outc[pos] = 0.0;
+  }
+}
+
+}  // namespace
+
+static hci_status run_walk(hci_ctx* ctx, WalkArgs& A, int64_t* total) {
+  HCI_CUDA(ctx, cudaMemsetAsync(A.counter, 0, 16, ctx->st));
+  const int grid = 152 * 8;
+  k_walk_doubles<<<grid, SEL_WARPS * 32, 0, ctx->st>>>(A);
+  HCI_CUDA(ctx, cudaGetLastError());
+  HCI_CUDA(ctx, cudaMemsetAsync(A.counter + 1, 0, 8, ctx->st));
+  k_singles<<<grid, SEL_WARPS * 32, 0, ctx->st>>>(A);
+  HCI_CUDA(ctx, cudaGetLastError());
+  unsigned long long cnt = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&cnt, A.counter, 8, cudaMemcpyDeviceToHost, ctx->st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  *total = (int64_t)cnt;
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys, const double* c, int64_t nV,
+                                 uint64_t* new_keys, int64_t cap, int64_t* n_new) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_select: null context");
+  if (!n_new) return hci_fail(ctx, HCI_ERR_INVALID, "hci_select: n_new is NULL");
+  *n_new = 0;
+  if (nV < 0 || cap < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_select: negative size");
+  if (nV > 0 && (!keys || !c)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_select: null keys or c");
+  if (cap > 0 && !new_keys) return hci_fail(ctx, HCI_ERR_INVALID, "hci_select: null new_keys");
+  if (nV == 0) return HCI_OK;
+  HCI_TRY(hci_build_lists(ctx));
+  int ok = 0;
+  HCI_TRY(check_sorted(ctx, keys, nV, &ok));
+  if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "hci_select: keys are not strictly ascending");
+  Lists& L = ctx->lists;
+  WalkArgs A;
+  A.n = ctx->n; A.na = ctx->na; A.nb = ctx->nb;
+  A.keys = reinterpret_cast<const ulonglong2*>(keys);
+  A.c = c; A.nV = nV; A.eps1 = eps1; A.accept_all = eps1 <= 0.0 ? 1 : 0;
+  A.opp_mag = bp<double>(L.opp_mag); A.opp_tgt = bp<uint16_t>(L.opp_tgt); A.Lo = L.len_opp;
+  A.same_mag = bp<double>(L.same_mag); A.same_tgt = bp<uint16_t>(L.same_tgt); A.Ls = L.len_same;
+  A.max_dbl = L.max_opp > L.max_same ? L.max_opp : L.max_same;
+  A.h = bp<double>(ctx->h); A.jk_same = bp<double>(ctx->jk_same); A.j_opp = bp<double>(ctx->j_opp);
+  A.single_bound = bp<double>(L.single_bound); A.max_single = L.max_single;
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  A.counter = bp<unsigned long long>(ctx->s_counter);
+  // candidate buffer: grow and rerun when the first guess overflows
+  int64_t guess = ctx->s_cand.bytes / 16;
+  if (guess < (int64_t)1 << 16) guess = (int64_t)1 << 16;
+  HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)guess * 16));
+  A.out = bp<ulonglong2>(ctx->s_cand);
+  A.cap = (int64_t)(ctx->s_cand.bytes / 16);
+  int64_t m = 0;
+  HCI_TRY(run_walk(ctx, A, &m));
+  if (m > A.cap) {
+    HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)(m + m / 8 + 1024) * 16));
+    A.out = bp<ulonglong2>(ctx->s_cand);
+    A.cap = (int64_t)(ctx->s_cand.bytes / 16);
+    int64_t m2 = 0;
+    HCI_TRY(run_walk(ctx, A, &m2));
+    if (m2 != m) return hci_fail(ctx, HCI_ERR_CUDA, "hci_select: candidate count changed between runs");
+  }
+  ctx->last_candidates = m;
+  if (m == 0) return HCI_OK;
+  HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)m * 16));
+  HCI_TRY(sort_keys(ctx, bp<uint64_t>(ctx->s_cand), bp<uint64_t>(ctx->s_cand2), m, ctx->n, ctx->n));
+  HCI_TRY(ensure_buf(ctx, ctx->s_flags, (size_t)(2 * m + 1) * 8));
+  int64_t* flag = bp<int64_t>(ctx->s_flags);
+  int64_t* pos = flag + m;
+  int64_t* total = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 16);
+  k_flag_new<<<grid_for(m, 256), 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->s_cand), m,
+                                                    reinterpret_cast<const ulonglong2*>(keys), nV, flag);
+  HCI_CUDA(ctx, cudaGetLastError());
+  HCI_TRY(scan_i64(ctx, flag, pos, m, total));
+  int64_t cnt = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&cnt, total, 8, cudaMemcpyDeviceToHost, ctx->st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  *n_new = cnt;
+  if (cnt > cap)
+    return hci_fail(ctx, HCI_ERR_CAPACITY, "hci_select: %lld new determinants exceed cap %lld", (long long)cnt,
+                    (long long)cap);
+  k_compact<<<grid_for(m, 256), 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->s_cand), m, flag, pos,
+                                                   reinterpret_cast<ulonglong2*>(new_keys), cap);
+  HCI_CUDA(ctx, cudaGetLastError());
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_merge(hci_ctx* ctx, const uint64_t* keys, const double* c, int64_t nV,
+                                const uint64_t* new_keys, int64_t n_new, uint64_t* out_keys, double* out_c) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_merge: null context");
+  if (nV < 0 || n_new < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_merge: negative size");
+  if ((nV + n_new) > 0 && !out_keys) return hci_fail(ctx, HCI_ERR_INVALID, "hci_merge: null out_keys");
+  const ulonglong2* V = reinterpret_cast<const ulonglong2*>(keys);
+  const ulonglong2* N = reinterpret_cast<const ulonglong2*>(new_keys);
+  ulonglong2* O = reinterpret_cast<ulonglong2*>(out_keys);
+  if (nV > 0)
+    k_merge_old<<<grid_for(nV, 256), 256, 0, ctx->st>>>(V, c, nV, N, n_new, O, out_c);
+  if (n_new > 0)
+    k_merge_new<<<grid_for(n_new, 256), 256, 0, ctx->st>>>(V, nV, N, n_new, O, out_c);
+  HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}

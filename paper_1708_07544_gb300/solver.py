@@ -1,0 +1,93 @@
+"""Convenience wrappers over the C ABI: a solver object per active space and
+the autograd Function of the vHCISCF energy (Sec. III.B, Eq. vdedk2)."""
+from __future__ import annotations
+
+import torch
+
+from . import _abi
+
+
+class HCISolver:
+    """One context of libhci.so bound to (h, eri) on the current CUDA stream."""
+
+    def __init__(self, norb, nalpha, nbeta, h, eri, e_core=0.0, stream=None):
+        self.norb, self.nalpha, self.nbeta = int(norb), int(nalpha), int(nbeta)
+        self.e_core = float(e_core)
+        self.ctx = _abi.hci_create(norb, nalpha, nbeta, h, eri, e_core, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _abi.hci_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def build_lists(self):
+        _abi.hci_build_lists(self.ctx)
+
+    def select(self, eps1, keys, c, cap=None):
+        return _abi.hci_select(self.ctx, eps1, keys, c, cap)
+
+    def merge(self, keys, c, new_keys):
+        return _abi.hci_merge(self.ctx, keys, c, new_keys)
+
+    def sigma(self, keys, c):
+        return _abi.hci_sigma(self.ctx, keys, c)
+
+    def davidson(self, keys, c0=None, tol=1e-10, maxit=400, allow_unconverged=False):
+        return _abi.hci_davidson(self.ctx, keys, c0, tol, maxit, allow_unconverged)
+
+    def rdm12(self, keys, c):
+        return _abi.hci_rdm12(self.ctx, keys, c, self.norb)
+
+    def solve(self, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 20):
+        keys, c, e, it = _abi.hci_solve(self.ctx, eps1, max_iter, dav_tol, dav_maxit, cap)
+        return {"keys": keys, "c": c, "E": e, "iters": it}
+
+    def stats(self):
+        return _abi.hci_stats(self.ctx)
+
+
+class HCIEnergy(torch.autograd.Function):
+    """E(h, eri, kappa) = variational HCI energy of the rotated integrals.
+
+    forward: U = exp(kappa), h' = U^T h U, eri' = U^4 eri, variational HCI
+    on (h', eri') -> E; the selected space V is saved.
+    backward: c is recomputed by Davidson on the saved V (not stored), the
+    RDMs give dE/dh' = rdm1 and dE/deri' = rdm2/2 (dE/dc = 0 at the
+    variational minimum), and the rotation's adjoint returns dE/dh, dE/deri
+    and dE/dkappa for every entry of the full kappa matrix.
+    """
+
+    @staticmethod
+    def forward(ctx, h, eri, kappa, nalpha, nbeta, e_core, eps1, max_iter=30, dav_tol=1e-10):
+        n = h.shape[0]
+        _, h2, e2 = _abi.hci_rotate(kappa, h, eri)
+        with HCISolver(n, nalpha, nbeta, h2, e2, e_core) as s:
+            out = s.solve(eps1, max_iter, dav_tol)
+        ctx.save_for_backward(h, eri, kappa, out["keys"])
+        ctx.cfg = (n, nalpha, nbeta, e_core, dav_tol)
+        ctx.nV = out["keys"].shape[0]
+        return torch.tensor(out["E"], dtype=torch.float64, device=h.device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        h, eri, kappa, keys = ctx.saved_tensors
+        n, na, nb, e_core, tol = ctx.cfg
+        _, h2, e2 = _abi.hci_rotate(kappa, h, eri)
+        with HCISolver(n, na, nb, h2, e2, e_core) as s:
+            _, c, _ = s.davidson(keys, None, tol)
+            r1, r2 = s.rdm12(keys, c)
+        dh, de, dk = _abi.hci_rotate_backward(kappa, h, eri, r1, r2)
+        g = gE.to(torch.float64)
+        return g * dh, g * de, g * dk, None, None, None, None, None, None
