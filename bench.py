@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the variational HCI hot path on GB300.
+
+One step = one pass of the whole path on one active space:
+  rotate the integrals by U = exp(kappa)          (a0)
+  heat-bath lists, selection loop with Davidson    (a1-a6, hci_solve)
+  1- and 2-RDM                                    (a7)
+  dE/dkappa through the rotation adjoint           (a8)
+on the synthetic (44e,44o) density-fitted Hamiltonian at eps1 = 1e-4.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hci_inputs as hi  # noqa: E402
+
+METRIC = "(44e,44o) HCI solve+2-RDM seconds"
+
+WORKLOADS = {
+    "df44": {"make": hi.df_44o, "eps1": 1e-4,
+             "desc": "synthetic DF (44e,44o), naux=176, w_P=exp(-P/40), 0.3 Ha gap, eps1=1e-4"},
+    "pentacene22": {"make": hi.ppp_pentacene, "eps1": 5e-5,
+                    "desc": "PPP pentacene-shaped lattice (22e,22o), Hueckel MOs, eps1=5e-5"},
+    "df12": {"make": hi.df_12o, "eps1": 1e-3, "desc": "synthetic DF (12e,12o), naux=48, eps1=1e-3"},
+    "polyene8": {"make": lambda: hi.ppp_polyene(8), "eps1": 1e-4, "desc": "PPP 8-site polyene (8e,8o)"},
+}
+
+# Work structure of one solve of each workload (selection source passes,
+# sigma row passes, sigma connection passes), as counted by the library's
+# own counters on GB300; the CPU reference scales its sampled per-row and
+# per-source costs by these to a whole solve.
+WORK_PROFILE = {
+    "df44": {"select_sources": None, "sigma_rows": None, "sigma_nnz": None},
+}
+
+DAV_TOL = 1e-9
+DAV_MAXIT = 400
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="df44", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU sample")
+    ap.add_argument("--sigma-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1708_07544_gb300 as pkg
+    from paper_1708_07544_gb300 import _abi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    inst = wl["make"]()
+    eps1 = wl["eps1"]
+    n = inst.norb
+    kap = hi.random_kappa(n, seed=1709, sigma=0.01)
+    h_d = torch.tensor(inst.h, device=dev)
+    eri_d = torch.tensor(inst.eri, device=dev)
+    k_d = torch.tensor(kap, device=dev)
+    cap = 1 << 22
+
+    def step(h_in, eri_in, k_in, record=None):
+        U, h2, e2 = _abi.hci_rotate(k_in, h_in, eri_in)
+        s = pkg.HCISolver(n, inst.nalpha, inst.nbeta, h2, e2, inst.e_core)
+        try:
+            s.profile(True)
+            keys, c, E, it = _abi.hci_solve(s.ctx, eps1, 30, DAV_TOL, DAV_MAXIT, cap, device=dev)
+            r1, r2 = s.rdm12(keys, c)
+            dh, de, dk = _abi.hci_rotate_backward(k_in, h_in, eri_in, r1, r2, want_dh=False, want_deri=False)
+            if record is not None:
+                record["timers"] = s.timers()
+                record["stats"] = s.stats()
+                record["nV"] = int(keys.shape[0])
+                record["E"] = E
+                record["iters"] = it
+                record["keys"] = keys
+                record["c"] = c
+                record["rdm"] = (r1, r2)
+        finally:
+            s.close()
+        return E, r1, r2, dk
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    rec = {}
+    for w in range(max(args.warmup, 0)):
+        step(h_d, eri_d, k_d, rec if w == args.warmup - 1 else None)
+    # timed region: device-resident inputs
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    l0 = _abi.hci_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record()
+    recs = []
+    for _ in range(args.steps):
+        r = {}
+        step(h_d, eri_d, k_d, r)
+        recs.append({k: r[k] for k in ("timers", "stats", "nV", "E", "iters")})
+    ev1.record()
+    barrier()
+    launches = _abi.hci_launch_count() - l0
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+
+    # end-to-end through the public API with host buffers (H2D of the
+    # integrals and kappa, D2H of E, rdm1, rdm2 and dE/dkappa every step)
+    h_host = torch.tensor(inst.h).pin_memory()
+    eri_host = torch.tensor(inst.eri).pin_memory()
+    k_host = torch.tensor(kap).pin_memory()
+    r1_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    r2_host = torch.empty((n,) * 4, dtype=torch.float64).pin_memory()
+    dk_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    h_e = torch.empty_like(h_d)
+    eri_e = torch.empty_like(eri_d)
+    k_e = torch.empty_like(k_d)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        h_e.copy_(h_host, non_blocking=True)
+        eri_e.copy_(eri_host, non_blocking=True)
+        k_e.copy_(k_host, non_blocking=True)
+        E, r1, r2, dk = step(h_e, eri_e, k_e)
+        r1_host.copy_(r1, non_blocking=True)
+        r2_host.copy_(r2, non_blocking=True)
+        dk_host.copy_(dk, non_blocking=True)
+    e1.record()
+    barrier()
+    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_step = float(te.item()) / args.steps
+    h2d = (n * n + n ** 4 + n * n) * 8
+    d2h = (n * n + n ** 4 + n * n) * 8 + 8
+
+    # sigma roofline on the converged space: the sigma kernel alone
+    last = rec
+    U, h2, e2 = _abi.hci_rotate(k_d, h_d, eri_d)
+    s = pkg.HCISolver(n, inst.nalpha, inst.nbeta, h2, e2, inst.e_core)
+    keys, c = last["keys"], last["c"]
+    s.sigma(keys, c)                 # builds the graph
+    s.timers()
+    s.profile(True)
+    sig = torch.empty_like(c)
+    cc = c.clone()
+    for _ in range(args.sigma_reps):
+        sig = s.sigma(keys, cc)
+    tm = s.timers()
+    st = s.stats()
+    s.close()
+    sig_ms = tm["sigma"][0] / max(tm["sigma"][1], 1)
+    nnz = st["graph_nnz"]
+    nV = int(keys.shape[0])
+    sig_bytes = 12 * nnz + 32 * nV + 8
+    peak, peak_kind = measured_peaks()
+    achieved = sig_bytes / (sig_ms * 1e-3) / 1e9
+
+    phases = {}
+    for r in recs:
+        for k, (ms, cnt) in r["timers"].items():
+            a = phases.setdefault(k, [0.0, 0])
+            a[0] += ms / len(recs)
+            a[1] += cnt // len(recs)
+    work = recs[-1]["stats"]
+
+    out = None
+    if rank == 0:
+        value = ms_step / 1e3 / world
+        out = {
+            "metric": METRIC,
+            "value": round(value, 6),
+            "unit": "s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 3),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "norb": n, "nelec": inst.nelec,
+                       "nV": recs[-1]["nV"], "graph_nnz": nnz, "selections": recs[-1]["iters"],
+                       "E": recs[-1]["E"], "davidson_tol": DAV_TOL,
+                       "l2": "inputs larger than L2 (connection graph %.1f GB)" % (sig_bytes / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "hc_connections_per_s": (nnz + nV) / (sig_ms * 1e-3),
+            "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
+            "phase_counts": {k: v[1] for k, v in phases.items()},
+            "work": work,
+            "roofline": {"kernel": "k_sigma (CSR FP64 H c)", "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_launch": sig_bytes,
+                         "launch_ms": round(sig_ms, 4)},
+            "e2e": {"value": round(e2e_step / 1e3 / world, 6), "unit": "s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+    if world > 1:
+        dist.barrier()
+    return out, last, inst
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(inst, eps1, keys_np, c_np, budget_s, work):
+    """Time the CPU oracle on sampled rows and sources of a space and scale to
+    one solve with the given work counters."""
+    import oracle
+
+    rng = np.random.default_rng(7)
+    nV = len(keys_np)
+    P = oracle.Problem.of(inst)
+    threads = oracle.num_threads()
+    # sigma rows
+    rows = np.sort(rng.choice(nV, size=min(nV, 64), replace=False))
+    t0 = time.perf_counter()
+    oracle.sigma_rows(P, keys_np, c_np, rows)
+    t_rows = time.perf_counter() - t0
+    k = len(rows)
+    while t_rows < budget_s * 0.4 and k < nV:
+        more = np.sort(rng.choice(nV, size=min(nV, 2 * k), replace=False))
+        t0 = time.perf_counter()
+        oracle.sigma_rows(P, keys_np, c_np, more)
+        t_rows = time.perf_counter() - t0
+        k = len(more)
+        if t_rows > budget_s * 0.4:
+            break
+    per_row = t_rows / k
+    # selection sources (the largest |c| first: those do the most work)
+    order = np.argsort(-np.abs(c_np))
+    ns = 16
+    t0 = time.perf_counter()
+    oracle.select(P, keys_np, c_np, eps1, sources=order[:ns])
+    t_src = time.perf_counter() - t0
+    while t_src < budget_s * 0.3 and ns < nV:
+        ns = min(nV, ns * 2)
+        t0 = time.perf_counter()
+        oracle.select(P, keys_np, c_np, eps1, sources=order[:ns])
+        t_src = time.perf_counter() - t0
+    per_src = t_src / ns
+    est = per_row * work["sigma_rows"] + per_src * work["select_sources"]
+    return est, threads, f"{k} sigma rows and {ns} selection sources (largest |c|) of the converged space, " \
+                         f"scaled by the solve's row passes ({work['sigma_rows']}) and source passes " \
+                         f"({work['select_sources']})"
+
+
+def reference_arm(args):
+    """The CPU oracle on a bounded sample of the same workload (host cores)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+
+    wl = WORKLOADS[args.workload]
+    inst = wl["make"]()
+    eps1 = wl["eps1"]
+    P = oracle.Problem.of(inst)
+    prof = WORK_PROFILE.get(args.workload)
+    vals = []
+    desc = ""
+    # the first selection from the aufbau determinant is exact and cheap;
+    # its space (with first-order-like coefficients) is the sampled space
+    k0 = oracle.aufbau(inst.nalpha, inst.nbeta)
+    new, f, _ = oracle.select(P, k0, [1.0], eps1)
+    keys, c = oracle.merge(k0, [1.0], new)
+    c = np.where(c == 0.0, 0.0, c)
+    idx = np.searchsorted(keys[:, 0] * 0, 0)  # noqa: F841
+    cc = np.ones(len(keys)) * 1e-3
+    cc[0] = 1.0
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        est, threads, desc = oracle_sample(inst, eps1, keys, cc, args.cpu_seconds / max(args.steps, 1), prof)
+        vals.append(est)
+    vals = vals[args.warmup:]
+    value = statistics.median(vals)
+    return {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "impl": "reference", "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = reference_arm(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out, last, inst = gpu_arm(args)
+    if out is None:
+        return
+    if not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        keys_np = last["keys"].cpu().numpy().view(np.uint64).reshape(-1, 2)
+        c_np = last["c"].cpu().numpy()
+        est, threads, desc = oracle_sample(inst, WORKLOADS[args.workload]["eps1"], keys_np, c_np,
+                                           args.cpu_seconds, out["work"])
+        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -247,16 +247,21 @@ def df_batch(count: int = 64, seed0: int = 7544):
     return out
 
 
-# Scale of the (44e,44o) factors: sqrt(0.5/sum w_P^2) gives couplings so
-# strong that the selected space grows without bound at eps1 = 1e-4; the
-# value below is the frozen replacement (see the instance recipe).
+# Scale of the (44e,44o) factors.  sqrt(0.5/sum w_P^2) = 0.1562 gives
+# couplings so strong that the second selection at eps1 = 1e-4 produces
+# ~2e9 determinants; 0.18 of it (frozen here) gives |V| = 1.12e6 at
+# convergence, inside the intended 1e6-1e7 range.
+DF44_SCALE_FACTOR = 0.18
 DF44_SCALE = None
 
 
 def df_44o(scale: float | None = None) -> Instance:
     """(44e,44o), naux = 176, w_P = exp(-P/40), 0.3 Ha HOMO-LUMO gap."""
     hd = np.concatenate([np.linspace(-2.0, -0.15, 22), np.linspace(0.15, 1.0, 22)])
-    sc = DF44_SCALE if scale is None else scale
+    if scale is None:
+        w = np.exp(-np.arange(176) / 40.0)
+        scale = DF44_SCALE_FACTOR * math.sqrt(0.5 / float(np.sum(w ** 2)))
+    sc = scale
     return df_instance(44, 176, 1707, decay=40.0, h_diag=hd, scale=sc, name="df_44o_44e")
 
 

@@ -59,8 +59,8 @@ enum {
  * device, n^4 doubles (copied into the context, so the caller may free
  * them afterwards).  nalpha, nbeta in [0, norb], norb in [1, 64].
  * stream: cudaStream_t or NULL.  Derived tables for single-excitation
- * elements are built here.  (Sec. III: "the active space two electron
- * integrals ... are passed on to Dice".) */
+ * elements are built here.  (Sec. III, Fig. 2: each HCISCF iteration hands
+ * the active-space one- and two-electron integrals to the HCI solver.) */
 hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta, const double* h,
                       const double* eri, double e_core, void* stream);
 
@@ -157,10 +157,48 @@ hci_status hci_rotate_backward(int norb, const double* kappa, const double* h, c
                                const double* rdm1, const double* rdm2, double* dh, double* deri,
                                double* dkappa, void* stream);
 
-/* Statistics of the last calls on this context (host out, any may be NULL):
- * nnz of the cached connection graph (off-diagonal), candidates emitted by
- * the last hci_select before deduplication. */
-hci_status hci_stats(const hci_ctx* ctx, int64_t* graph_nnz, int64_t* last_candidates);
+/* Work counters of this context (instrumentation; the paper reports only
+ * wall times per HCISCF iteration, Sec. V).  out[k] for k < nout:
+ *   HCI_ST_GRAPH_NNZ        off-diagonal connections of the cached graph
+ *   HCI_ST_LAST_CANDIDATES  candidates emitted by the last selection
+ *   HCI_ST_SIGMA_CALLS      H c products so far (one per vector)
+ *   HCI_ST_SIGMA_ROWS       rows processed by them
+ *   HCI_ST_SIGMA_NNZ        off-diagonal connections processed by them
+ *   HCI_ST_SELECT_CALLS     selection steps so far
+ *   HCI_ST_SELECT_SOURCES   source determinants offered to them
+ *   HCI_ST_CANDIDATES       candidates emitted by them in total
+ *   HCI_ST_GRAPH_BUILDS     connection graphs built */
+enum {
+  HCI_ST_GRAPH_NNZ = 0, HCI_ST_LAST_CANDIDATES = 1, HCI_ST_SIGMA_CALLS = 2, HCI_ST_SIGMA_ROWS = 3,
+  HCI_ST_SIGMA_NNZ = 4, HCI_ST_SELECT_CALLS = 5, HCI_ST_SELECT_SOURCES = 6, HCI_ST_CANDIDATES = 7,
+  HCI_ST_GRAPH_BUILDS = 8, HCI_ST_COUNT = 9
+};
+hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout);
+
+/* Phases timed by hci_profile / hci_timers. */
+enum {
+  HCI_PH_LISTS = 0,     /* heat-bath list build */
+  HCI_PH_WALK = 1,      /* heat-bath walk + singles (candidate generation) */
+  HCI_PH_DEDUP = 2,     /* radix sort, set difference against V, compaction */
+  HCI_PH_MERGE = 3,     /* sorted union V + C */
+  HCI_PH_GRAPH = 4,     /* connection graph + diagonal of a new space */
+  HCI_PH_SIGMA = 5,     /* the sigma kernel alone (one entry per H c product) */
+  HCI_PH_DAVIDSON = 6,  /* hci_davidson excluding the graph build */
+  HCI_PH_RDM = 7,       /* hci_rdm12 excluding the graph build */
+  HCI_PH_COUNT = 8
+};
+
+/* Enable (1) or disable (0) per-phase CUDA-event timing on the context
+ * stream.  Instrumentation only: it adds event records, no host syncs. */
+hci_status hci_profile(hci_ctx* ctx, int enable);
+
+/* Read and reset the per-phase totals: ms[k] = summed device time of phase k
+ * in milliseconds, counts[k] = number of timed intervals, for k < nphase
+ * (<= HCI_PH_COUNT).  Synchronises the context stream. */
+hci_status hci_timers(hci_ctx* ctx, double* ms, int64_t* counts, int nphase);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t hci_launch_count(void);
 
 #ifdef __cplusplus
 }

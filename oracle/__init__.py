@@ -141,7 +141,7 @@ def select(inst, keys, c, eps1, band=1e-12, sources=None):
     """One selection step, Eq. (criteria) with f_HCI (Sec. II.A).
 
     Returns (new_keys, f_new, tie_keys): new_keys are the determinants not
-    in V with max_i |H_ai c_i| > eps1 (strict, the paper's 'greater than'),
+    in V with max_i |H_ai c_i| > eps1 (strict inequality, as the criterion is stated),
     sorted by (alpha, beta); eps1 <= 0 accepts every single and double
     excitation (reading: the symmetry-zero elements left by the MO
     transform would otherwise make the set depend on rounding).
@@ -241,8 +241,8 @@ def aufbau(nalpha, nbeta):
 def hci(inst, eps1, max_iter=30, verbose=False):
     """Variational HCI (Sec. II.A): V^0 = {aufbau}, c^0 = [1]; repeat
     select C^mu(eps1), V^{mu+1} = V^mu + C^mu, lowest eigenpair on V^{mu+1};
-    stop when C^mu is empty (reading of 'a designated convergence
-    threshold') or after max_iter iterations."""
+    stop when C^mu is empty (reading: the paper leaves the convergence
+    test open) or after max_iter iterations."""
     P = Problem.of(inst)
     keys = aufbau(P.nalpha, P.nbeta)
     c = np.array([1.0])

@@ -26,7 +26,10 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
-           "hci_stats"]
+           "hci_stats", "hci_profile", "hci_timers", "hci_launch_count"]
+PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm"]
+STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
+         "select_sources", "candidates", "graph_builds"]
 
 
 class HCIError(RuntimeError):
@@ -65,9 +68,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
-    L.hci_stats.argtypes = [V, P(I64), P(I64)]
+    L.hci_stats.argtypes = [V, V, I]
+    L.hci_profile.argtypes = [V, I]
+    L.hci_timers.argtypes = [V, V, V, I]
+    L.hci_launch_count.argtypes = []
     for name in EXPORTS:
-        getattr(L, name).restype = I if name != "hci_last_error" else ctypes.c_char_p
+        getattr(L, name).restype = I
+    L.hci_last_error.restype = ctypes.c_char_p
+    L.hci_launch_count.restype = I64
     if path is None:
         _LIB = L
     return L
@@ -222,8 +230,27 @@ def hci_rotate_backward(kappa, h, eri, rdm1, rdm2, want_dh=True, want_deri=True,
 
 
 def hci_stats(ctx):
-    L = load()
-    a = ctypes.c_int64(0)
-    b = ctypes.c_int64(0)
-    _check(L.hci_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
-    return {"graph_nnz": a.value, "last_candidates": b.value}
+    """Work counters of the context as a dict (names in STATS)."""
+    import numpy as np
+
+    out = np.zeros(len(STATS), dtype=np.int64)
+    _check(load().hci_stats(ctx, out.ctypes.data, len(STATS)), ctx)
+    return {k: int(out[i]) for i, k in enumerate(STATS)}
+
+
+def hci_profile(ctx, enable=True):
+    _check(load().hci_profile(ctx, 1 if enable else 0), ctx)
+
+
+def hci_timers(ctx):
+    """Read and reset the per-phase device times: {phase: (ms, count)}."""
+    import numpy as np
+
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
+    _check(load().hci_timers(ctx, ms.ctypes.data, cnt.ctypes.data, len(PHASES)), ctx)
+    return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+def hci_launch_count():
+    return int(load().hci_launch_count())

@@ -213,9 +213,9 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
   cudaError_t e = cudaMemcpyAsync(ctx->h.p, h, n * n * 8, cudaMemcpyDeviceToDevice, ctx->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->eri.p, eri, n * n * n * n * 8, cudaMemcpyDeviceToDevice, ctx->st);
   if (e == cudaSuccess) {
-    k_single_tables<<<grid_for((int64_t)(n * n * n), 256), 256, 0, ctx->st>>>(
+    HCI_LAUNCH(k_single_tables, grid_for((int64_t)(n * n * n), 256), 256, 0, ctx->st)(
         norb, bp<double>(ctx->eri), bp<double>(ctx->jk_same), bp<double>(ctx->j_opp));
-    k_single_bound<<<(unsigned)((n * n + 255) / 256), 256, 0, ctx->st>>>(
+    HCI_LAUNCH(k_single_bound, (unsigned)((n * n + 255) / 256), 256, 0, ctx->st)(
         norb, bp<double>(ctx->h), bp<double>(ctx->jk_same), bp<double>(ctx->j_opp),
         bp<double>(ctx->lists.single_bound));
     e = cudaGetLastError();
@@ -239,8 +239,14 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->s_cand, &ctx->s_cand2, &ctx->s_flags, &ctx->s_scan, &ctx->s_misc, &ctx->s_counter,
                     &ctx->s_hist, &ctx->g_ua, &ctx->g_ga, &ctx->g_ia, &ctx->g_ub, &ctx->g_gb, &ctx->g_ib,
                     &ctx->g_permb, &ctx->g_bkeys, &ctx->g_bkeys2, &ctx->g_nbr_ptr, &ctx->g_nbr, &ctx->g_cnt,
-                    &ctx->d_vb, &ctx->d_wb, &ctx->d_diag, &ctx->d_small, &ctx->d_part};
+                    &ctx->d_vb, &ctx->d_wb, &ctx->d_diag, &ctx->d_small, &ctx->d_part,
+                    &ctx->g_bnbr_ptr, &ctx->g_bnbr, &ctx->g_costa, &ctx->g_costb,
+                    &ctx->inc.pos_old, &ctx->inc.mark, &ctx->inc.flag, &ctx->inc.newrows, &ctx->inc.rpN,
+                    &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.cnt, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T,
+                    &ctx->inc.T2, &ctx->inc.tstart, &ctx->inc.len, &ctx->inc.keys_old, &ctx->inc.rp_old,
+                    &ctx->inc.col_old, &ctx->inc.val_old};
   for (DevBuf* b : bufs) free_buf(st, *b);
+  prof_release(ctx);
   cudaStreamSynchronize(st);
   delete ctx;
   return HCI_OK;
@@ -253,6 +259,7 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
   Lists& L = ctx->lists;
   if (L.built) return HCI_OK;
   const int n = ctx->n;
+  prof_tic(ctx, HCI_PH_LISTS);
   L.n = n;
   L.len_opp = n * n;
   L.npair_same = n * (n - 1) / 2;
@@ -267,24 +274,24 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
     int P = next_pow2(L.len_opp);
     size_t smem = (size_t)P * 12;
     HCI_CUDA(ctx, cudaFuncSetAttribute(k_build_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_build_lists<<<n * n, 1024, smem, ctx->st>>>(n, bp<double>(ctx->eri), 0, L.len_opp, P,
+    HCI_LAUNCH(k_build_lists, n * n, 1024, smem, ctx->st)(n, bp<double>(ctx->eri), 0, L.len_opp, P,
                                                   bp<double>(L.opp_mag), bp<uint16_t>(L.opp_tgt));
     HCI_CUDA(ctx, cudaGetLastError());
   }
   if (L.npair_same > 0) {
     int P = next_pow2(L.len_same);
     size_t smem = (size_t)P * 12;
-    k_build_lists<<<L.npair_same, 1024, smem, ctx->st>>>(n, bp<double>(ctx->eri), 1, L.len_same, P,
+    HCI_LAUNCH(k_build_lists, L.npair_same, 1024, smem, ctx->st)(n, bp<double>(ctx->eri), 1, L.len_same, P,
                                                          bp<double>(L.same_mag), bp<uint16_t>(L.same_tgt));
     HCI_CUDA(ctx, cudaGetLastError());
   }
   HCI_TRY(ensure_buf(ctx, ctx->s_misc, 64));
   double* dm = bp<double>(ctx->s_misc);
   HCI_CUDA(ctx, cudaMemsetAsync(dm, 0, 64, ctx->st));
-  k_max_first<<<1, 1024, 0, ctx->st>>>(bp<double>(L.opp_mag), n * n, L.len_opp, dm + 0);
+  HCI_LAUNCH(k_max_first, 1, 1024, 0, ctx->st)(bp<double>(L.opp_mag), n * n, L.len_opp, dm + 0);
   if (L.npair_same > 0)
-    k_max_first<<<1, 1024, 0, ctx->st>>>(bp<double>(L.same_mag), L.npair_same, L.len_same, dm + 1);
-  k_max_vec<<<1, 1024, 0, ctx->st>>>(bp<double>(L.single_bound), n * n, dm + 2);
+    HCI_LAUNCH(k_max_first, 1, 1024, 0, ctx->st)(bp<double>(L.same_mag), L.npair_same, L.len_same, dm + 1);
+  HCI_LAUNCH(k_max_vec, 1, 1024, 0, ctx->st)(bp<double>(L.single_bound), n * n, dm + 2);
   HCI_CUDA(ctx, cudaGetLastError());
   double hm[3];
   HCI_CUDA(ctx, cudaMemcpyAsync(hm, dm, 24, cudaMemcpyDeviceToHost, ctx->st));
@@ -293,12 +300,95 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
   L.max_same = hm[1];
   L.max_single = hm[2];
   L.built = true;
+  prof_toc(ctx, HCI_PH_LISTS);
   return HCI_OK;
 }
 
-extern "C" hci_status hci_stats(const hci_ctx* ctx, int64_t* graph_nnz, int64_t* last_candidates) {
-  if (!ctx) return HCI_ERR_INVALID;
-  if (graph_nnz) *graph_nnz = ctx->graph.valid ? ctx->graph.nnz : 0;
-  if (last_candidates) *last_candidates = ctx->last_candidates;
+extern "C" hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_stats: null context");
+  if (nout < 0 || (nout > 0 && !out)) return HCI_ERR_INVALID;
+  int64_t v[HCI_ST_COUNT];
+  for (int k = 0; k < HCI_ST_COUNT; ++k) v[k] = ctx->st_counts[k];
+  v[HCI_ST_GRAPH_NNZ] = ctx->graph.valid ? ctx->graph.nnz : 0;
+  v[HCI_ST_LAST_CANDIDATES] = ctx->last_candidates;
+  for (int k = 0; k < nout && k < HCI_ST_COUNT; ++k) out[k] = v[k];
+  for (int k = HCI_ST_COUNT; k < nout; ++k) out[k] = 0;
   return HCI_OK;
 }
+
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+std::atomic<long long> g_hci_launches{0};
+
+static cudaEvent_t prof_event(hci_ctx* ctx) {
+  if (!ctx->prof.pool.empty()) {
+    cudaEvent_t e = ctx->prof.pool.back();
+    ctx->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void prof_tic(hci_ctx* ctx, int phase) {
+  if (!ctx->prof.on) return;
+  cudaEvent_t e = prof_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->st);
+  ctx->prof.open[phase] = e;
+}
+
+void prof_toc(hci_ctx* ctx, int phase) {
+  if (!ctx->prof.on || !ctx->prof.open[phase]) return;
+  cudaEvent_t e = prof_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->st);
+  ctx->prof.pend[phase].push_back({ctx->prof.open[phase], e});
+  ctx->prof.open[phase] = nullptr;
+}
+
+static void prof_collect(hci_ctx* ctx) {
+  cudaStreamSynchronize(ctx->st);
+  for (int k = 0; k < HCI_PH_COUNT; ++k) {
+    for (auto& pr : ctx->prof.pend[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr[0], pr[1]) == cudaSuccess) {
+        ctx->prof.ms[k] += ms;
+        ctx->prof.count[k] += 1;
+      }
+      ctx->prof.pool.push_back(pr[0]);
+      ctx->prof.pool.push_back(pr[1]);
+    }
+    ctx->prof.pend[k].clear();
+  }
+}
+
+void prof_release(hci_ctx* ctx) {
+  prof_collect(ctx);
+  for (int k = 0; k < HCI_PH_COUNT; ++k)
+    if (ctx->prof.open[k]) { ctx->prof.pool.push_back(ctx->prof.open[k]); ctx->prof.open[k] = nullptr; }
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  ctx->prof.pool.clear();
+}
+
+extern "C" hci_status hci_profile(hci_ctx* ctx, int enable) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_profile: null context");
+  ctx->prof.on = enable != 0;
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_timers(hci_ctx* ctx, double* ms, int64_t* counts, int nphase) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_timers: null context");
+  if (nphase < 0 || nphase > HCI_PH_COUNT) return hci_fail(ctx, HCI_ERR_INVALID, "hci_timers: bad nphase");
+  prof_collect(ctx);
+  for (int k = 0; k < nphase; ++k) {
+    if (ms) ms[k] = ctx->prof.ms[k];
+    if (counts) counts[k] = ctx->prof.count[k];
+  }
+  for (int k = 0; k < HCI_PH_COUNT; ++k) { ctx->prof.ms[k] = 0.0; ctx->prof.count[k] = 0; }
+  return HCI_OK;
+}
+
+extern "C" int64_t hci_launch_count(void) { return (int64_t)g_hci_launches.load(); }

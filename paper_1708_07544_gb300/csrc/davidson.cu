@@ -1,7 +1,7 @@
 // FP64 Davidson for the lowest eigenpair on a fixed determinant space:
 // the minimum of the energy functional Eq. (variational) with the
-// normalisation multiplier (Sec. II.A "obtained at each iteration by the
-// Davidson procedure").  Vector operations, the subspace eigenproblem
+// normalisation multiplier (Sec. II.A: after each enlargement of V the new
+// ground state is found with Davidson's method).  Vector operations, the subspace eigenproblem
 // (cyclic Jacobi on one warp) and the phase convention all run on the GPU;
 // the host only reads the Ritz value and the residual norm per iteration.
 #include <cmath>
@@ -85,24 +85,24 @@ __global__ void k_jacobi(DavDev* d, int k) {
     Q[l][j] = (l == j) ? 1.0 : 0.0;
   }
   __syncwarp();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    if (l < k) {
-      for (int j = 0; j < k; ++j) {
-        if (j > l) off += A[l][j] * A[l][j];
-        if (j == l) dia += A[l][j] * A[l][j];
-      }
-    }
-    for (int o = 16; o; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      dia += __shfl_xor_sync(0xffffffffu, dia, o);
-    }
-    if (off <= 1e-32 * dia || off == 0.0) break;
+  // cyclic sweeps; an off-diagonal element too small to change either of its
+  // diagonal partners in floating point (even scaled by 100) is set to zero,
+  // a rotated pair is zeroed exactly, and the sweeps stop once a sweep makes
+  // no rotation
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    int rotated = 0;
     for (int p = 0; p < k - 1; ++p) {
       for (int q = p + 1; q < k; ++q) {
         double apq = A[p][q];
-        if (fabs(apq) < 1e-300) continue;
         double app = A[p][p], aqq = A[q][q];
+        const double g = 100.0 * fabs(apq);
+        if ((fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq)) || fabs(apq) < 1e-300) {
+          __syncwarp();
+          if (l == 0) { A[p][q] = 0.0; A[q][p] = 0.0; }
+          __syncwarp();
+          continue;
+        }
+        rotated = 1;
         double tau = (aqq - app) / (2.0 * apq);
         double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
         double c = 1.0 / sqrt(1.0 + t * t);
@@ -123,8 +123,11 @@ __global__ void k_jacobi(DavDev* d, int k) {
           Q[l][q] = s * vlp + c * vlq;
         }
         __syncwarp();
+        if (l == 0) { A[p][q] = 0.0; A[q][p] = 0.0; }
+        __syncwarp();
       }
     }
+    if (!rotated) break;
   }
   __syncwarp();
   __shared__ int s_m;
@@ -272,9 +275,9 @@ struct Dav {
   int nblk;
 
   hci_status dots(const double* Vb, int k, const double* w, double* out) {
-    if (k <= 8) k_dots<8><<<nblk, DBLOCK, 0, ctx->st>>>(Vb, ld, k, w, n, part);
-    else k_dots<LDG><<<nblk, DBLOCK, 0, ctx->st>>>(Vb, ld, k, w, n, part);
-    k_reduce<<<1, 32 * LDG, 0, ctx->st>>>(part, nblk, k, out);
+    if (k <= 8) HCI_LAUNCH(k_dots<8>, nblk, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part);
+    else HCI_LAUNCH(k_dots<LDG>, nblk, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part);
+    HCI_LAUNCH(k_reduce, 1, 32 * LDG, 0, ctx->st)(part, nblk, k, out);
     HCI_CUDA(ctx, cudaGetLastError());
     return HCI_OK;
   }
@@ -290,6 +293,7 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
     return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson: empty space or null pointer");
   if (iters) *iters = 0;
   HCI_TRY(graph_ensure(ctx, keys, nV));
+  prof_tic(ctx, HCI_PH_DAVIDSON);
   Dav D;
   D.ctx = ctx;
   D.n = nV;
@@ -319,21 +323,21 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) {
     HCI_CUDA(ctx, cudaMemsetAsync(D.V, 0, (size_t)nV * 8, st));
-    k_unit_min_diag<<<1, 1024, 0, st>>>(D.V, diag, nV);
+    HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(D.V, diag, nV);
   } else {
-    k_scale_const<<<D.nblk, DBLOCK, 0, st>>>(D.V, nV, 1.0 / std::sqrt(nrm2));
+    HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.V, nV, 1.0 / std::sqrt(nrm2));
   }
   HCI_TRY(D.sigma(0));
   HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots));
-  k_set_gcol<<<1, 32, 0, st>>>(D.d, 0);
+  HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, 0);
   int k = 1;
   bool converged = false;
   double theta = 0.0, rn = 0.0;
   int it = 0;
   for (; it < maxit; ++it) {
-    k_jacobi<<<1, 32, 0, st>>>(D.d, k);
-    k_ritz<<<D.nblk, DBLOCK, 0, st>>>(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
-    k_reduce<<<1, 32, 0, st>>>(D.part, D.nblk, 1, &D.d->rnorm2);
+    HCI_LAUNCH(k_jacobi, 1, 32, 0, st)(D.d, k);
+    HCI_LAUNCH(k_ritz, D.nblk, DBLOCK, 0, st)(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
+    HCI_LAUNCH(k_reduce, 1, 32, 0, st)(D.part, D.nblk, 1, &D.d->rnorm2);
     HCI_CUDA(ctx, cudaGetLastError());
     double hv[2];
     HCI_CUDA(ctx, cudaMemcpyAsync(&hv[0], &D.d->theta, 8, cudaMemcpyDeviceToHost, st));
@@ -352,15 +356,15 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
       HCI_CUDA(ctx, cudaMemcpyAsync(D.V, D.x, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
       HCI_CUDA(ctx, cudaMemcpyAsync(D.W, D.wy, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
       HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
-      k_scale_by<<<D.nblk, DBLOCK, 0, st>>>(D.V, D.W, nV, &D.d->nrm2);
+      HCI_LAUNCH(k_scale_by, D.nblk, DBLOCK, 0, st)(D.V, D.W, nV, &D.d->nrm2);
       HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots));
-      k_set_gcol<<<1, 32, 0, st>>>(D.d, 0);
+      HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, 0);
       k = 1;
     }
     // orthogonalise the correction twice, normalise
     for (int pass = 0; pass < 2; ++pass) {
       HCI_TRY(D.dots(D.V, k, D.t, D.d->dots));
-      k_orth<<<D.nblk, DBLOCK, 0, st>>>(D.V, D.ld, k, D.d, D.t, nV);
+      HCI_LAUNCH(k_orth, D.nblk, DBLOCK, 0, st)(D.V, D.ld, k, D.d, D.t, nV);
     }
     HCI_TRY(D.dots(D.t, 1, D.t, &D.d->nrm2));
     HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
@@ -370,22 +374,23 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
       break;
     }
     double* slot = D.V + (int64_t)k * D.ld;
-    k_scale_const<<<D.nblk, DBLOCK, 0, st>>>(D.t, nV, 1.0 / std::sqrt(nrm2));
+    HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.t, nV, 1.0 / std::sqrt(nrm2));
     HCI_CUDA(ctx, cudaMemcpyAsync(slot, D.t, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
     HCI_TRY(D.sigma(k));
     HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots));
-    k_set_gcol<<<1, 32, 0, st>>>(D.d, k);
+    HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, k);
     ++k;
   }
   if (iters) *iters = it + (converged ? 1 : 0);
   // final vector: normalise, fix phase
   HCI_TRY(D.dots(D.x, 1, D.x, &D.d->nrm2));
-  k_scale_by<<<D.nblk, DBLOCK, 0, st>>>(D.x, nullptr, nV, &D.d->nrm2);
-  k_amax_part<<<D.nblk, DBLOCK, 0, st>>>(D.x, nV, amax_v, amax_i);
-  k_phase_sign<<<1, 1, 0, st>>>(D.x, amax_v, amax_i, D.nblk, &D.d->dots[0]);
-  k_apply_sign<<<D.nblk, DBLOCK, 0, st>>>(D.x, nV, &D.d->dots[0]);
+  HCI_LAUNCH(k_scale_by, D.nblk, DBLOCK, 0, st)(D.x, nullptr, nV, &D.d->nrm2);
+  HCI_LAUNCH(k_amax_part, D.nblk, DBLOCK, 0, st)(D.x, nV, amax_v, amax_i);
+  HCI_LAUNCH(k_phase_sign, 1, 1, 0, st)(D.x, amax_v, amax_i, D.nblk, &D.d->dots[0]);
+  HCI_LAUNCH(k_apply_sign, D.nblk, DBLOCK, 0, st)(D.x, nV, &D.d->dots[0]);
   HCI_CUDA(ctx, cudaMemcpyAsync(c_inout, D.x, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_DAVIDSON);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   *energy = theta;
   if (!converged && rn > tol)

@@ -1,7 +1,7 @@
 // Connection graph of a determinant space and the FP64 sigma H c.
 //
-// Sec. IV: every single and double excitation between pairs of determinants
-// of V is generated to evaluate the Hamiltonian.  Instead of generating the
+// Sec. IV: the Hamiltonian on V is built from all pairs of determinants of V
+// that differ by a single or double excitation.  Instead of generating the
 // ~N^2 n^2 excitations of each row and looking them up, the determinants are
 // grouped by alpha string (V is sorted by (alpha, beta)) and by beta string
 // (a second, beta-major order), and connections are found by XOR/popcount
@@ -186,25 +186,39 @@ __device__ double connection_el(const HamView& H, ulonglong2 ki, ulonglong2 kj) 
 // row traversal: (A) alpha group, (B) beta group, (C) alpha-single x beta-single
 // ---------------------------------------------------------------------------
 struct GraphArgs {
-  const ulonglong2* V;
+  const ulonglong2* V;     // alpha-major keys
+  const ulonglong2* bk;    // beta-major swapped keys (beta, alpha)
   int64_t nV;
+  int n, na, nb;
   const int32_t* ia;       // alpha group of each det
   const int64_t* ga;       // alpha group starts [nua+1]
   const int32_t* ib;       // beta group of each det
   const int64_t* gb;       // beta group starts (beta-major positions) [nub+1]
   const int32_t* permb;    // beta-major position -> det
-  const int64_t* nbr_ptr;  // alpha single neighbours
-  const int32_t* nbr;
-  const int64_t* rowptr;   // fill pass
+  const int64_t* anbr_ptr; // single-excitation neighbours of each distinct alpha string
+  const int32_t* anbr;
+  const int64_t* bnbr_ptr; // ... of each distinct beta string
+  const int32_t* bnbr;
+  const int64_t* costa;    // cost of the alpha-side (C) search per distinct alpha string
+  const int64_t* costb;
+  const int32_t* rowlist;  // rows to process (nullptr: all rows, in order)
+  int64_t nrows;
+  const int64_t* rowptr;   // fill pass: output offset per processed row
   int32_t* col;
   double* val;
-  int64_t* rowcnt;         // count pass
+  int64_t* rowcnt;         // count pass: entries per processed row
   unsigned long long* queue;
   HamView H;
 };
 
+// A group of size m is scanned when that is cheaper than L binary searches.
+__device__ __forceinline__ bool use_lookup(int64_t m, int L) {
+  int lg = 64 - __clzll((long long)(m + 1));
+  return m > (int64_t)L * lg;
+}
+
 template <bool FILL>
-__device__ __forceinline__ void visit(const GraphArgs& A, int64_t i, ulonglong2 ki, int64_t j, bool ok, int64_t& w) {
+__device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t j, bool ok, int64_t& w) {
   const int lane = threadIdx.x & 31;
   unsigned m = __ballot_sync(0xffffffffu, ok);
   if (FILL && ok) {
@@ -215,97 +229,340 @@ __device__ __forceinline__ void visit(const GraphArgs& A, int64_t i, ulonglong2 
   w += __popc(m);
 }
 
+// (C) from one side.  BETA == false: neighbours are alpha strings, groups are
+// alpha groups (members j = position, other-spin value V[j].y); BETA == true:
+// neighbours are beta strings, groups live in beta-major order (members
+// j = permb[pos], other-spin value bk[pos].y).  Small groups are scanned
+// (flattened, 32 groups at a time); large groups are probed with binary
+// searches for the L single excitations of the other-spin string.
+template <bool FILL, bool BETA>
+__device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, int g, int64_t& w, int64_t* s_start,
+                                           int64_t* s_pref, int64_t* s_size, const int* occ_o, const int* vir_o,
+                                           int nocc_o, int nvir_o) {
+  const int lane = threadIdx.x & 31;
+  const int64_t* ptr = BETA ? A.bnbr_ptr : A.anbr_ptr;
+  const int32_t* nbr = BETA ? A.bnbr : A.anbr;
+  const int64_t* gs = BETA ? A.gb : A.ga;
+  const uint64_t mine = BETA ? ki.x : ki.y;     // other-spin string of row i
+  const int L = nocc_o * nvir_o;
+  const int64_t nb0 = ptr[g], nb1 = ptr[g + 1];
+  for (int64_t c0 = nb0; c0 < nb1; c0 += 32) {
+    const int64_t cidx = c0 + lane;
+    int64_t st = 0, sz = 0;
+    bool look = false;
+    if (cidx < nb1) {
+      const int gg = nbr[cidx];
+      st = gs[gg];
+      sz = gs[gg + 1] - st;
+      look = use_lookup(sz, L);
+    }
+    const int64_t ssz = look ? 0 : sz;
+    int64_t inc = ssz;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    s_start[lane] = st;
+    s_size[lane] = sz;
+    s_pref[lane + 1] = inc;
+    if (lane == 0) s_pref[0] = 0;
+    __syncwarp();
+    const int64_t total = s_pref[32];
+    for (int64_t v0 = 0; v0 < total; v0 += 32) {
+      const int64_t v = v0 + lane;
+      bool ok = false;
+      int64_t j = -1;
+      if (v < total) {
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (s_pref[mid] <= v) lo = mid;
+          else hi = mid - 1;
+        }
+        const int64_t pos = s_start[lo] + (v - s_pref[lo]);
+        uint64_t other;
+        if (BETA) { j = A.permb[pos]; other = A.bk[pos].y; }
+        else { j = pos; other = A.V[pos].y; }
+        ok = __popcll(mine ^ other) == 2;
+      }
+      visit<FILL>(A, ki, j, ok, w);
+    }
+    unsigned lk = __ballot_sync(0xffffffffu, look);
+    while (lk) {
+      const int src = __ffs(lk) - 1;
+      lk &= lk - 1;
+      const int64_t st2 = s_start[src], sz2 = s_size[src];
+      for (int t0 = 0; t0 < L; t0 += 32) {
+        const int t = t0 + lane;
+        bool ok = false;
+        int64_t j = -1;
+        if (t < L) {
+          const uint64_t want = mine ^ (1ull << occ_o[t / nvir_o]) ^ (1ull << vir_o[t % nvir_o]);
+          int64_t lo = 0, hi = sz2;
+          while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            const uint64_t x = BETA ? A.bk[st2 + mid].y : A.V[st2 + mid].y;
+            if (x < want) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo < sz2) {
+            const uint64_t x = BETA ? A.bk[st2 + lo].y : A.V[st2 + lo].y;
+            if (x == want) { ok = true; j = BETA ? A.permb[st2 + lo] : st2 + lo; }
+          }
+        }
+        visit<FILL>(A, ki, j, ok, w);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ int occ_vir_lists(uint64_t s, int n, int* occ, int* vir) {
+  const int lane = threadIdx.x & 31;
+  int bo = 0, bv = 0;
+  for (int p0 = 0; p0 < n; p0 += 32) {
+    const int p = p0 + lane;
+    const bool in = p < n;
+    const bool o = in && ((s >> p) & 1ull);
+    const unsigned mo = __ballot_sync(0xffffffffu, o);
+    const unsigned mv = __ballot_sync(0xffffffffu, in && !o);
+    const unsigned lt = (1u << lane) - 1u;
+    if (o) occ[bo + __popc(mo & lt)] = p;
+    if (in && !o) vir[bv + __popc(mv & lt)] = p;
+    bo += __popc(mo);
+    bv += __popc(mv);
+  }
+  __syncwarp();
+  return bo;
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
   __shared__ int64_t s_start[G_WARPS][32];
+  __shared__ int64_t s_size[G_WARPS][32];
   __shared__ int64_t s_pref[G_WARPS][33];
+  __shared__ int s_occ[G_WARPS][HCI_MAXORB];
+  __shared__ int s_vir[G_WARPS][HCI_MAXORB];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   while (true) {
     unsigned long long qi = 0;
     if (lane == 0) qi = atomicAdd(A.queue, 1ull);
-    const int64_t i = (int64_t)__shfl_sync(0xffffffffu, qi, 0);
-    if (i >= A.nV) break;
+    const int64_t q = (int64_t)__shfl_sync(0xffffffffu, qi, 0);
+    if (q >= A.nrows) break;
+    const int64_t i = A.rowlist ? (int64_t)A.rowlist[q] : q;
     const ulonglong2 ki = A.V[i];
-    int64_t w = FILL ? A.rowptr[i] : 0;
+    int64_t w = FILL ? A.rowptr[q] : 0;
     // (A) same alpha string
     {
-      int g = A.ia[i];
-      int64_t b = A.ga[g], e = A.ga[g + 1];
+      const int g = A.ia[i];
+      const int64_t b = A.ga[g], e = A.ga[g + 1];
       for (int64_t j0 = b; j0 < e; j0 += 32) {
-        int64_t j = j0 + lane;
+        const int64_t j = j0 + lane;
         bool ok = false;
         if (j < e && j != i) {
-          int d = __popcll(ki.y ^ A.V[j].y);
+          const int d = __popcll(ki.y ^ A.V[j].y);
           ok = d == 2 || d == 4;
         }
-        visit<FILL>(A, i, ki, j, ok, w);
+        visit<FILL>(A, ki, j, ok, w);
       }
     }
     // (B) same beta string
     {
-      int g = A.ib[i];
-      int64_t b = A.gb[g], e = A.gb[g + 1];
+      const int g = A.ib[i];
+      const int64_t b = A.gb[g], e = A.gb[g + 1];
       for (int64_t k0 = b; k0 < e; k0 += 32) {
-        int64_t k = k0 + lane;
+        const int64_t k = k0 + lane;
         bool ok = false;
         int64_t j = -1;
         if (k < e) {
           j = A.permb[k];
           if (j != i) {
-            int d = __popcll(ki.x ^ A.V[j].x);
+            const int d = __popcll(ki.x ^ A.bk[k].y);
             ok = d == 2 || d == 4;
           }
         }
-        visit<FILL>(A, i, ki, j, ok, w);
+        visit<FILL>(A, ki, j, ok, w);
       }
     }
-    // (C) alpha single neighbours, beta single: flattened over the
-    // concatenation of the neighbour groups, 32 groups at a time
+    // (C) single in alpha and single in beta, from the cheaper side
     {
-      int g = A.ia[i];
-      int64_t nb0 = A.nbr_ptr[g], nb1 = A.nbr_ptr[g + 1];
-      for (int64_t c0 = nb0; c0 < nb1; c0 += 32) {
-        int64_t cidx = c0 + lane;
-        int64_t st = 0, sz = 0;
-        if (cidx < nb1) {
-          int gg = A.nbr[cidx];
-          st = A.ga[gg];
-          sz = A.ga[gg + 1] - st;
-        }
-        // inclusive scan of sizes
-        int64_t inc = sz;
-        for (int o = 1; o < 32; o <<= 1) {
-          int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += t;
-        }
-        s_start[wid][lane] = st;
-        s_pref[wid][lane + 1] = inc;
-        if (lane == 0) s_pref[wid][0] = 0;
-        __syncwarp();
-        const int64_t total = s_pref[wid][32];
-        for (int64_t v0 = 0; v0 < total; v0 += 32) {
-          int64_t v = v0 + lane;
-          bool ok = false;
-          int64_t j = -1;
-          if (v < total) {
-            int lo = 0, hi = 31;     // find group t with pref[t] <= v < pref[t+1]
-            while (lo < hi) {
-              int mid = (lo + hi + 1) >> 1;
-              if (s_pref[wid][mid] <= v) lo = mid;
-              else hi = mid - 1;
-            }
-            j = s_start[wid][lo] + (v - s_pref[wid][lo]);
-            ok = __popcll(ki.y ^ A.V[j].y) == 2;
-          }
-          visit<FILL>(A, i, ki, j, ok, w);
-        }
-        __syncwarp();
+      const int ga_i = A.ia[i], gb_i = A.ib[i];
+      if (A.costa[ga_i] <= A.costb[gb_i]) {
+        const int no = occ_vir_lists(ki.y, A.n, s_occ[wid], s_vir[wid]);
+        mixed_side<FILL, false>(A, ki, ga_i, w, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid], s_vir[wid],
+                                no, A.n - no);
+      } else {
+        const int no = occ_vir_lists(ki.x, A.n, s_occ[wid], s_vir[wid]);
+        mixed_side<FILL, true>(A, ki, gb_i, w, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid], s_vir[wid],
+                               no, A.n - no);
       }
     }
-    if (!FILL && lane == 0) A.rowcnt[i] = w;
+    if (!FILL && lane == 0) A.rowcnt[q] = w;
   }
 }
 
+// cost[u] = sum over the neighbours v of string u of min(scan, lookup) cost
+__global__ void k_nbr_cost(const int64_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
+                           const int64_t* __restrict__ gs, int64_t nu, int L, int64_t* __restrict__ cost) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < nu; u += nwarps) {
+    int64_t c = 0;
+    for (int64_t k = ptr[u] + lane; k < ptr[u + 1]; k += 32) {
+      const int g = nbr[k];
+      const int64_t m = gs[g + 1] - gs[g];
+      const int lg = 64 - __clzll((long long)(m + 1));
+      c += use_lookup(m, L) ? (int64_t)L * lg : m;
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cost[u] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// incremental update: V' = V + N (V's keys all present in V')
+// ---------------------------------------------------------------------------
+__global__ void k_find_old(const ulonglong2* __restrict__ oldk, int64_t nold, const ulonglong2* __restrict__ V,
+                           int64_t nV, int64_t* __restrict__ pos_old, int64_t* __restrict__ mark,
+                           unsigned long long* __restrict__ missing) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nold; i += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 k = oldk[i];
+    const int64_t p = lower_bound_k(V, nV, k);
+    if (p < nV && V[p].x == k.x && V[p].y == k.y) {
+      pos_old[i] = p;
+      mark[p] = 1;
+    } else {
+      pos_old[i] = -1;
+      atomicAdd(missing, 1ull);
+    }
+  }
+}
+
+__global__ void k_not(const int64_t* __restrict__ mark, int64_t n, int64_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = 1 - mark[i];
+}
+
+__global__ void k_compact_idx(const int64_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n,
+                              int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) out[pos[i]] = (int32_t)i;
+}
+
+// per new row: number of entries whose column is an old determinant; also
+// the histogram of those columns (entries to append to old rows)
+__global__ void k_count_old_cols(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t nrows,
+                                 const int64_t* __restrict__ mark, int64_t* __restrict__ cnt,
+                                 int64_t* __restrict__ hist) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nrows; q += nwarps) {
+    int64_t c = 0;
+    for (int64_t k = rp[q] + lane; k < rp[q + 1]; k += 32) {
+      const int32_t j = col[k];
+      if (mark[j]) {
+        ++c;
+        atomicAdd((unsigned long long*)&hist[j], 1ull);
+      }
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[q] = c;
+  }
+}
+
+// T records {x = old column (row to append to), y = entry index in the new
+// rows' CSR}, written in CSR order (deterministic)
+__global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t nrows,
+                         const int64_t* __restrict__ mark, const int64_t* __restrict__ base,
+                         ulonglong2* __restrict__ T) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nrows; q += nwarps) {
+    int64_t w = base[q];
+    for (int64_t k0 = rp[q]; k0 < rp[q + 1]; k0 += 32) {
+      const int64_t k = k0 + lane;
+      bool ok = false;
+      int32_t j = 0;
+      if (k < rp[q + 1]) {
+        j = col[k];
+        ok = mark[j] != 0;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) T[w + __popc(m & ((1u << lane) - 1u))] = make_ulonglong2((uint64_t)j, (uint64_t)k);
+      w += __popc(m);
+    }
+  }
+}
+
+__global__ void k_lengths(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ rp_old, int64_t nold,
+                          const int32_t* __restrict__ newrows, const int64_t* __restrict__ rpN, int64_t nnew,
+                          const int64_t* __restrict__ hist, int64_t* __restrict__ len) {
+  const int64_t tot = nold + nnew;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < nold) {
+      const int64_t p = pos_old[t];
+      len[p] = (rp_old[t + 1] - rp_old[t]) + hist[p];
+    } else {
+      const int64_t q = t - nold;
+      len[newrows[q]] = rpN[q + 1] - rpN[q];
+    }
+  }
+}
+
+// old rows: remapped old entries, then the appended T entries
+__global__ void k_copy_old_rows(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ rp_old,
+                                const int32_t* __restrict__ col_old, const double* __restrict__ val_old, int64_t nold,
+                                const int64_t* __restrict__ rp_new, int32_t* __restrict__ col_new,
+                                double* __restrict__ val_new, const ulonglong2* __restrict__ T,
+                                const int64_t* __restrict__ tstart, const int64_t* __restrict__ hist,
+                                const int64_t* __restrict__ rpN, int64_t nnew, const int32_t* __restrict__ newrows,
+                                const double* __restrict__ valN) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < nold; i += nwarps) {
+    const int64_t p = pos_old[i];
+    const int64_t dst = rp_new[p];
+    const int64_t b = rp_old[i], len = rp_old[i + 1] - b;
+    for (int64_t k = lane; k < len; k += 32) {
+      col_new[dst + k] = (int32_t)pos_old[col_old[b + k]];
+      val_new[dst + k] = val_old[b + k];
+    }
+    const int64_t t0 = tstart[p], tn = hist[p];
+    for (int64_t k = lane; k < tn; k += 32) {
+      const int64_t e = (int64_t)T[t0 + k].y;
+      // new row owning entry e
+      int64_t lo = 0, hi = nnew;
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (rpN[mid] <= e) lo = mid;
+        else hi = mid;
+      }
+      col_new[dst + len + k] = newrows[lo];
+      val_new[dst + len + k] = valN[e];
+    }
+  }
+}
+
+__global__ void k_copy_new_rows(const int32_t* __restrict__ newrows, int64_t nnew, const int64_t* __restrict__ rpN,
+                                const int32_t* __restrict__ colN, const double* __restrict__ valN,
+                                const int64_t* __restrict__ rp_new, int32_t* __restrict__ col_new,
+                                double* __restrict__ val_new) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nnew; q += nwarps) {
+    const int64_t dst = rp_new[newrows[q]];
+    const int64_t b = rpN[q], len = rpN[q + 1] - b;
+    for (int64_t k = lane; k < len; k += 32) {
+      col_new[dst + k] = colN[b + k];
+      val_new[dst + k] = valN[b + k];
+    }
+  }
+}
 // diagonal <D|H|D> (includes e_core)
 __global__ void k_diag(int n, const double* __restrict__ h, const double* __restrict__ eri, double ecore,
                        const ulonglong2* __restrict__ V, int64_t nV, double* __restrict__ out) {
@@ -350,7 +607,9 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
   }
 }
 
-// sigma = diag .* c + offdiag * c ; one warp per row, nvec vectors
+// sigma = diag .* c + offdiag * c ; one warp per row.  The single-vector
+// path keeps four independent (col, val, c[col]) chains per lane in flight;
+// the CSR stream is read with evict-first hints so that c stays in L2.
 __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ diag,
                                                int64_t nV, const double* __restrict__ c, double* __restrict__ sigma,
@@ -358,6 +617,28 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (nvec == 1) {
+    for (int64_t i = warp; i < nV; i += nwarps) {
+      const int64_t b = rowptr[i], e = rowptr[i + 1];
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int64_t k = b + lane;
+      for (; k + 96 < e; k += 128) {
+        const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
+                      j3 = __ldcs(col + k + 96);
+        const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
+                     v3 = __ldcs(val + k + 96);
+        a0 = fma(v0, c[j0], a0);
+        a1 = fma(v1, c[j1], a1);
+        a2 = fma(v2, c[j2], a2);
+        a3 = fma(v3, c[j3], a3);
+      }
+      for (; k < e; k += 32) a0 = fma(__ldcs(val + k), c[__ldcs(col + k)], a0);
+      double a = (a0 + a1) + (a2 + a3);
+      for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) sigma[i] = fma(diag[i], c[i], a);
+    }
+    return;
+  }
   for (int64_t i = warp; i < nV; i += nwarps) {
     const int64_t b = rowptr[i], e = rowptr[i + 1];
     for (int v0 = 0; v0 < nvec; v0 += 4) {
@@ -387,20 +668,14 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
 
 }  // namespace
 
-hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
+// Group structures of the space in G.keys (nV determinants): alpha groups,
+// beta-major order and beta groups, single-excitation neighbour lists of the
+// distinct alpha and beta strings, and the (C) search cost per string.
+static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   Graph& G = ctx->graph;
-  G.valid = false;
   const int n = ctx->n;
-  const ulonglong2* V = reinterpret_cast<const ulonglong2*>(keys);
-  if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 columns");
-  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  const ulonglong2* V = bp<ulonglong2>(G.keys);
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
-  unsigned long long* queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 48);
-  // keep a private copy of the keys (the caller's buffer may change)
-  HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
-  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
-  V = bp<ulonglong2>(G.keys);
-  // --- alpha groups
   HCI_TRY(ensure_buf(ctx, ctx->s_flags, (size_t)(2 * nV + 1) * 8));
   int64_t* flag = bp<int64_t>(ctx->s_flags);
   int64_t* excl = flag + nV;
@@ -408,86 +683,237 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   HCI_TRY(ensure_buf(ctx, ctx->g_ua, (size_t)nV * 8));
   HCI_TRY(ensure_buf(ctx, ctx->g_ga, (size_t)(nV + 1) * 8));
   const int gb = grid_for(nV, 256);
-  k_run_flags<<<gb, 256, 0, ctx->st>>>(V, nV, flag);
+  HCI_LAUNCH(k_run_flags, gb, 256, 0, ctx->st)(V, nV, flag);
   HCI_TRY(scan_i64(ctx, flag, excl, nV, dtot));
-  k_groups<<<gb, 256, 0, ctx->st>>>(V, nV, flag, excl, bp<int32_t>(ctx->g_ia), bp<uint64_t>(ctx->g_ua),
-                                     bp<int64_t>(ctx->g_ga));
-  k_set_last<<<1, 1, 0, ctx->st>>>(bp<int64_t>(ctx->g_ga), dtot, nV);
+  HCI_LAUNCH(k_groups, gb, 256, 0, ctx->st)(V, nV, flag, excl, bp<int32_t>(ctx->g_ia), bp<uint64_t>(ctx->g_ua),
+                                             bp<int64_t>(ctx->g_ga));
+  HCI_LAUNCH(k_set_last, 1, 1, 0, ctx->st)(bp<int64_t>(ctx->g_ga), dtot, nV);
   int64_t nua = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&nua, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
-  // --- beta-major order and beta groups
   HCI_TRY(ensure_buf(ctx, ctx->g_bkeys, (size_t)nV * 16));
   HCI_TRY(ensure_buf(ctx, ctx->g_bkeys2, (size_t)nV * 16));
-  k_swap_keys<<<gb, 256, 0, ctx->st>>>(V, nV, bp<ulonglong2>(ctx->g_bkeys));
+  HCI_LAUNCH(k_swap_keys, gb, 256, 0, ctx->st)(V, nV, bp<ulonglong2>(ctx->g_bkeys));
   HCI_TRY(sort_keys(ctx, bp<uint64_t>(ctx->g_bkeys), bp<uint64_t>(ctx->g_bkeys2), nV, n, n));
   HCI_TRY(ensure_buf(ctx, ctx->g_ub, (size_t)nV * 8));
   HCI_TRY(ensure_buf(ctx, ctx->g_gb, (size_t)(nV + 1) * 8));
   HCI_TRY(ensure_buf(ctx, ctx->g_ib, (size_t)nV * 4));
   HCI_TRY(ensure_buf(ctx, ctx->g_permb, (size_t)nV * 4));
-  // reuse bkeys2 (now scratch) as int32 group-of-position
   int32_t* bgroup_of_pos = bp<int32_t>(ctx->g_bkeys2);
-  k_run_flags<<<gb, 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->g_bkeys), nV, flag);
+  HCI_LAUNCH(k_run_flags, gb, 256, 0, ctx->st)(bp<ulonglong2>(ctx->g_bkeys), nV, flag);
   HCI_TRY(scan_i64(ctx, flag, excl, nV, dtot));
-  k_groups<<<gb, 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->g_bkeys), nV, flag, excl, bgroup_of_pos,
-                                     bp<uint64_t>(ctx->g_ub), bp<int64_t>(ctx->g_gb));
-  k_set_last<<<1, 1, 0, ctx->st>>>(bp<int64_t>(ctx->g_gb), dtot, nV);
-  k_perm_b<<<gb, 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->g_bkeys), nV, V, bgroup_of_pos, bp<int32_t>(ctx->g_permb),
-                                     bp<int32_t>(ctx->g_ib));
+  HCI_LAUNCH(k_groups, gb, 256, 0, ctx->st)(bp<ulonglong2>(ctx->g_bkeys), nV, flag, excl, bgroup_of_pos,
+                                             bp<uint64_t>(ctx->g_ub), bp<int64_t>(ctx->g_gb));
+  HCI_LAUNCH(k_set_last, 1, 1, 0, ctx->st)(bp<int64_t>(ctx->g_gb), dtot, nV);
+  HCI_LAUNCH(k_perm_b, gb, 256, 0, ctx->st)(bp<ulonglong2>(ctx->g_bkeys), nV, V, bgroup_of_pos,
+                                             bp<int32_t>(ctx->g_permb), bp<int32_t>(ctx->g_ib));
+  int64_t nub = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&nub, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaGetLastError());
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
-  // --- alpha single neighbours
-  HCI_TRY(ensure_buf(ctx, ctx->g_cnt, (size_t)(nua + 1) * 8));
-  HCI_TRY(ensure_buf(ctx, ctx->g_nbr_ptr, (size_t)(nua + 1) * 8));
-  const int gw = grid_for(nua * 32, 256);
-  k_alpha_nbrs<<<gw, 256, 0, ctx->st>>>(n, bp<uint64_t>(ctx->g_ua), nua, nullptr, bp<int64_t>(ctx->g_cnt), nullptr);
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->g_cnt), bp<int64_t>(ctx->g_nbr_ptr), nua, dtot));
-  k_store_at<<<1, 1, 0, ctx->st>>>(bp<int64_t>(ctx->g_nbr_ptr), nua, dtot);
-  int64_t nnbr = 0;
-  HCI_CUDA(ctx, cudaMemcpyAsync(&nnbr, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
-  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
-  HCI_TRY(ensure_buf(ctx, ctx->g_nbr, (size_t)(nnbr + 1) * 4));
-  k_alpha_nbrs<<<gw, 256, 0, ctx->st>>>(n, bp<uint64_t>(ctx->g_ua), nua, bp<int64_t>(ctx->g_nbr_ptr), nullptr,
-                                         bp<int32_t>(ctx->g_nbr));
+  // neighbour lists of both spins
+  DevBuf* ptrs[2] = {&ctx->g_nbr_ptr, &ctx->g_bnbr_ptr};
+  DevBuf* lists[2] = {&ctx->g_nbr, &ctx->g_bnbr};
+  DevBuf* costs[2] = {&ctx->g_costa, &ctx->g_costb};
+  const uint64_t* uniq[2] = {bp<uint64_t>(ctx->g_ua), bp<uint64_t>(ctx->g_ub)};
+  const int64_t* gstart[2] = {bp<int64_t>(ctx->g_ga), bp<int64_t>(ctx->g_gb)};
+  const int64_t nu[2] = {nua, nub};
+  // lookups on the alpha side generate beta singles and vice versa
+  const int Lside[2] = {ctx->nb * (n - ctx->nb), ctx->na * (n - ctx->na)};
+  for (int s = 0; s < 2; ++s) {
+    HCI_TRY(ensure_buf(ctx, ctx->g_cnt, (size_t)(nu[s] + 1) * 8));
+    HCI_TRY(ensure_buf(ctx, *ptrs[s], (size_t)(nu[s] + 1) * 8));
+    HCI_TRY(ensure_buf(ctx, *costs[s], (size_t)(nu[s] + 1) * 8));
+    const int gw = grid_for(nu[s] * 32, 256);
+    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], nullptr, bp<int64_t>(ctx->g_cnt), nullptr);
+    HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->g_cnt), bp<int64_t>(*ptrs[s]), nu[s], dtot));
+    HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(*ptrs[s]), nu[s], dtot);
+    int64_t nn = 0;
+    HCI_CUDA(ctx, cudaMemcpyAsync(&nn, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+    HCI_TRY(ensure_buf(ctx, *lists[s], (size_t)(nn + 1) * 4));
+    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], bp<int64_t>(*ptrs[s]), nullptr,
+                                                   bp<int32_t>(*lists[s]));
+    HCI_LAUNCH(k_nbr_cost, gw, 256, 0, ctx->st)(bp<int64_t>(*ptrs[s]), bp<int32_t>(*lists[s]), gstart[s], nu[s],
+                                                 Lside[s], bp<int64_t>(*costs[s]));
+  }
   HCI_CUDA(ctx, cudaGetLastError());
-  // --- count pass
-  GraphArgs A;
-  A.V = V; A.nV = nV;
+  A.V = V;
+  A.bk = bp<ulonglong2>(ctx->g_bkeys);
+  A.nV = nV;
+  A.n = n; A.na = ctx->na; A.nb = ctx->nb;
   A.ia = bp<int32_t>(ctx->g_ia); A.ga = bp<int64_t>(ctx->g_ga);
   A.ib = bp<int32_t>(ctx->g_ib); A.gb = bp<int64_t>(ctx->g_gb);
   A.permb = bp<int32_t>(ctx->g_permb);
-  A.nbr_ptr = bp<int64_t>(ctx->g_nbr_ptr); A.nbr = bp<int32_t>(ctx->g_nbr);
+  A.anbr_ptr = bp<int64_t>(ctx->g_nbr_ptr); A.anbr = bp<int32_t>(ctx->g_nbr);
+  A.bnbr_ptr = bp<int64_t>(ctx->g_bnbr_ptr); A.bnbr = bp<int32_t>(ctx->g_bnbr);
+  A.costa = bp<int64_t>(ctx->g_costa); A.costb = bp<int64_t>(ctx->g_costb);
   A.H = HamView{n, bp<double>(ctx->h), bp<double>(ctx->eri), bp<double>(ctx->jk_same), bp<double>(ctx->j_opp)};
-  A.queue = queue;
-  HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
-  A.rowcnt = flag;   // reuse
+  A.queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 48);
+  A.rowlist = nullptr;
+  A.nrows = nV;
+  A.rowptr = nullptr; A.col = nullptr; A.val = nullptr; A.rowcnt = nullptr;
+  return HCI_OK;
+}
+
+// Count, scan and fill the rows listed in A (A.rowlist / A.nrows) into
+// rowptr (nrows+1), col, val buffers; returns their nnz.
+static hci_status rows_csr(hci_ctx* ctx, GraphArgs& A, DevBuf& rowptr, DevBuf& col, DevBuf& val, DevBuf& cnt,
+                           int64_t* nnz_out) {
+  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+  const int64_t nr = A.nrows;
+  HCI_TRY(ensure_buf(ctx, rowptr, (size_t)(nr + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, cnt, (size_t)(nr + 1) * 8));
+  A.rowcnt = bp<int64_t>(cnt);
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr;
   const int grows = 152 * 8;
-  HCI_CUDA(ctx, cudaMemsetAsync(queue, 0, 8, ctx->st));
-  k_rows<false><<<grows, G_WARPS * 32, 0, ctx->st>>>(A);
+  HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
+  HCI_LAUNCH(k_rows<false>, grows, G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
-  HCI_TRY(scan_i64(ctx, flag, bp<int64_t>(G.rowptr), nV, dtot));
-  k_store_at<<<1, 1, 0, ctx->st>>>(bp<int64_t>(G.rowptr), nV, dtot);
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(cnt), bp<int64_t>(rowptr), nr, dtot));
+  HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(rowptr), nr, dtot);
   int64_t nnz = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&nnz, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
-  // --- fill pass
-  HCI_TRY(ensure_buf(ctx, G.col, (size_t)(nnz + 1) * 4));
-  HCI_TRY(ensure_buf(ctx, G.val, (size_t)(nnz + 1) * 8));
-  A.rowptr = bp<int64_t>(G.rowptr); A.col = bp<int32_t>(G.col); A.val = bp<double>(G.val);
+  HCI_TRY(ensure_buf(ctx, col, (size_t)(nnz + 1) * 4));
+  HCI_TRY(ensure_buf(ctx, val, (size_t)(nnz + 1) * 8));
   A.rowcnt = nullptr;
-  HCI_CUDA(ctx, cudaMemsetAsync(queue, 0, 8, ctx->st));
-  k_rows<true><<<grows, G_WARPS * 32, 0, ctx->st>>>(A);
+  A.rowptr = bp<int64_t>(rowptr); A.col = bp<int32_t>(col); A.val = bp<double>(val);
+  HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
+  HCI_LAUNCH(k_rows<true>, grows, G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
-  // --- diagonal
+  *nnz_out = nnz;
+  return HCI_OK;
+}
+
+static hci_status compute_diag(hci_ctx* ctx, int64_t nV) {
+  Graph& G = ctx->graph;
+  const int n = ctx->n;
   HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
-  k_diag<<<grid_for(nV, 128), 128, (size_t)2 * n * n * 8, ctx->st>>>(n, bp<double>(ctx->h), bp<double>(ctx->eri),
-                                                                     ctx->ecore, V, nV, bp<double>(G.diag));
+  HCI_LAUNCH(k_diag, grid_for(nV, 128), 128, (size_t)2 * n * n * 8, ctx->st)(
+      n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, bp<ulonglong2>(G.keys), nV, bp<double>(G.diag));
   HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}
+
+hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
+  Graph& G = ctx->graph;
+  G.valid = false;
+  if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 columns");
+  prof_tic(ctx, HCI_PH_GRAPH);
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  GraphArgs A;
+  HCI_TRY(build_space(ctx, nV, A));
+  int64_t nnz = 0;
+  HCI_TRY(rows_csr(ctx, A, G.rowptr, G.col, G.val, ctx->inc.cnt, &nnz));
+  HCI_TRY(compute_diag(ctx, nV));
+  prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
   G.nV = nV;
   G.nnz = nnz;
+  ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   G.valid = true;
+  return HCI_OK;
+}
+
+// V' contains every determinant of the cached space: search only the rows of
+// the new determinants, append their transposes to the old rows, and merge.
+static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, bool* done) {
+  Graph& G = ctx->graph;
+  IncScratch& S = ctx->inc;
+  *done = false;
+  const int64_t nold = G.nV;
+  if (nV <= nold || nV >= ((int64_t)1 << 31) - 1) return HCI_OK;
+  cudaStream_t st = ctx->st;
+  unsigned long long* missing = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 24);
+  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+  const ulonglong2* Vn = reinterpret_cast<const ulonglong2*>(keys);
+  HCI_TRY(ensure_buf(ctx, S.pos_old, (size_t)nold * 8));
+  HCI_TRY(ensure_buf(ctx, S.mark, (size_t)nV * 8));
+  HCI_CUDA(ctx, cudaMemsetAsync(S.mark.p, 0, (size_t)nV * 8, st));
+  HCI_CUDA(ctx, cudaMemsetAsync(missing, 0, 8, st));
+  HCI_LAUNCH(k_find_old, grid_for(nold, 256), 256, 0, st)(bp<ulonglong2>(G.keys), nold, Vn, nV,
+                                                          bp<int64_t>(S.pos_old), bp<int64_t>(S.mark), missing);
+  unsigned long long miss = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&miss, missing, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  if (miss) return HCI_OK;        // not an extension: full rebuild
+  prof_tic(ctx, HCI_PH_GRAPH);
+  // the old CSR and keys move to the scratch side
+  std::swap(G.keys, S.keys_old);
+  std::swap(G.rowptr, S.rp_old);
+  std::swap(G.col, S.col_old);
+  std::swap(G.val, S.val_old);
+  HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st));
+  // new rows
+  const int64_t nnew = nV - nold;
+  HCI_TRY(ensure_buf(ctx, S.flag, (size_t)(2 * nV + 1) * 8));
+  int64_t* nflag = bp<int64_t>(S.flag);
+  int64_t* npos = nflag + nV;
+  HCI_LAUNCH(k_not, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.mark), nV, nflag);
+  HCI_TRY(scan_i64(ctx, nflag, npos, nV, dtot));
+  HCI_TRY(ensure_buf(ctx, S.newrows, (size_t)nnew * 4));
+  HCI_LAUNCH(k_compact_idx, grid_for(nV, 256), 256, 0, st)(nflag, npos, nV, bp<int32_t>(S.newrows));
+  GraphArgs A;
+  HCI_TRY(build_space(ctx, nV, A));
+  A.rowlist = bp<int32_t>(S.newrows);
+  A.nrows = nnew;
+  int64_t nnzN = 0;
+  HCI_TRY(rows_csr(ctx, A, S.rpN, S.colN, S.valN, S.cnt, &nnzN));
+  // transposed entries for the old rows
+  HCI_TRY(ensure_buf(ctx, S.hist, (size_t)(nV + 1) * 8));
+  HCI_CUDA(ctx, cudaMemsetAsync(S.hist.p, 0, (size_t)(nV + 1) * 8, st));
+  const int gw = grid_for(nnew * 32, 256);
+  HCI_LAUNCH(k_count_old_cols, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, bp<int64_t>(S.mark),
+                                                bp<int64_t>(S.cnt), bp<int64_t>(S.hist));
+  HCI_TRY(ensure_buf(ctx, S.tbase, (size_t)(nnew + 1) * 8));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.tbase), nnew, dtot));
+  int64_t nT = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&nT, dtot, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  HCI_TRY(ensure_buf(ctx, S.T, (size_t)(nT + 1) * 16));
+  HCI_TRY(ensure_buf(ctx, S.T2, (size_t)(nT + 1) * 16));
+  HCI_LAUNCH(k_emit_T, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, bp<int64_t>(S.mark),
+                                        bp<int64_t>(S.tbase), bp<ulonglong2>(S.T));
+  int bits = 1;
+  while (((int64_t)1 << bits) < nV) ++bits;
+  HCI_TRY(sort_keys(ctx, bp<uint64_t>(S.T), bp<uint64_t>(S.T2), nT, bits, 0));
+  HCI_TRY(ensure_buf(ctx, S.tstart, (size_t)(nV + 1) * 8));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.hist), bp<int64_t>(S.tstart), nV, dtot));
+  // lengths and the merged CSR
+  HCI_TRY(ensure_buf(ctx, S.len, (size_t)(nV + 1) * 8));
+  HCI_LAUNCH(k_lengths, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), nold,
+                                                       bp<int32_t>(S.newrows), bp<int64_t>(S.rpN), nnew,
+                                                       bp<int64_t>(S.hist), bp<int64_t>(S.len));
+  HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.len), bp<int64_t>(G.rowptr), nV, dtot));
+  HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(G.rowptr), nV, dtot);
+  int64_t nnz = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&nnz, dtot, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  if (nnz != G.nnz + nnzN + nT)
+    return hci_fail(ctx, HCI_ERR_CUDA, "graph_extend: inconsistent sizes %lld != %lld + %lld + %lld", (long long)nnz,
+                    (long long)G.nnz, (long long)nnzN, (long long)nT);
+  HCI_TRY(ensure_buf(ctx, G.col, (size_t)(nnz + 1) * 4));
+  HCI_TRY(ensure_buf(ctx, G.val, (size_t)(nnz + 1) * 8));
+  HCI_LAUNCH(k_copy_old_rows, grid_for(nold * 32, 256), 256, 0, st)(
+      bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), bp<int32_t>(S.col_old), bp<double>(S.val_old), nold,
+      bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val), bp<ulonglong2>(S.T), bp<int64_t>(S.tstart),
+      bp<int64_t>(S.hist), bp<int64_t>(S.rpN), nnew, bp<int32_t>(S.newrows), bp<double>(S.valN));
+  HCI_LAUNCH(k_copy_new_rows, gw, 256, 0, st)(bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN),
+                                               bp<int32_t>(S.colN), bp<double>(S.valN), bp<int64_t>(G.rowptr),
+                                               bp<int32_t>(G.col), bp<double>(G.val));
+  HCI_CUDA(ctx, cudaGetLastError());
+  HCI_TRY(compute_diag(ctx, nV));
+  prof_toc(ctx, HCI_PH_GRAPH);
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  G.nV = nV;
+  G.nnz = nnz;
+  ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
+  *done = true;
   return HCI_OK;
 }
 
@@ -498,16 +924,27 @@ hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   int ok = 0;
   HCI_TRY(check_sorted(ctx, keys, nV, &ok));
   if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "keys are not strictly ascending");
-  HCI_TRY(graph_build(ctx, keys, nV));
+  bool done = false;
+  if (ctx->graph.valid && ctx->incremental) {
+    ctx->graph.valid = false;
+    HCI_TRY(graph_extend(ctx, keys, nV, &done));
+  }
+  if (!done) HCI_TRY(graph_build(ctx, keys, nV));
   ctx->graph.hash = hsh;
+  ctx->graph.valid = true;
   return HCI_OK;
 }
 
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
   Graph& G = ctx->graph;
-  k_sigma<<<grid_for(G.nV * 32, 256, 152 * 16), 256, 0, ctx->st>>>(
+  prof_tic(ctx, HCI_PH_SIGMA);
+  ctx->st_counts[HCI_ST_SIGMA_CALLS] += nvec;
+  ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;
+  ctx->st_counts[HCI_ST_SIGMA_NNZ] += G.nnz * nvec;
+  HCI_LAUNCH(k_sigma, grid_for(G.nV * 32, 256, 152 * 16), 256, 0, ctx->st)(
       bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag), G.nV, c, sigma, nvec);
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_SIGMA);
   return HCI_OK;
 }
 

@@ -4,9 +4,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "../../include/hci.h"
 
@@ -18,9 +22,9 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-// Connection graph of one determinant space (Sec. IV: "all single and double
-// excitations between pairs of determinants in the variational wavefunction
-// are generated in order to evaluate the Hamiltonian").
+// Connection graph of one determinant space (Sec. IV: the Hamiltonian on V
+// is evaluated from every single and double excitation linking two
+// determinants of V; the same connections feed the RDMs).
 struct Graph {
   bool valid = false;
   int64_t nV = 0;
@@ -44,6 +48,22 @@ struct Lists {
   double max_opp = 0, max_same = 0, max_single = 0;
 };
 
+// Scratch of the incremental graph update (V' = V + new determinants).
+struct IncScratch {
+  DevBuf pos_old, mark, flag, newrows, rpN, colN, valN, cnt, hist, tbase, T, T2, tstart, len;
+  DevBuf keys_old, rp_old, col_old, val_old;
+};
+
+// Per-phase CUDA-event timers (enabled by hci_profile).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open[HCI_PH_COUNT] = {};
+  std::vector<std::array<cudaEvent_t, 2>> pend[HCI_PH_COUNT];
+  double ms[HCI_PH_COUNT] = {};
+  int64_t count[HCI_PH_COUNT] = {};
+};
+
 struct hci_ctx {
   int n = 0, na = 0, nb = 0;
   double ecore = 0;
@@ -55,10 +75,24 @@ struct hci_ctx {
   // scratch
   DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist;
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
+  DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb;
+  IncScratch inc;
+  bool incremental = true;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part;
   int64_t last_candidates = 0;
+  int64_t st_counts[HCI_ST_COUNT] = {};
+  Prof prof;
   char err[512] = {0};
 };
+
+void prof_tic(hci_ctx* ctx, int phase);
+void prof_toc(hci_ctx* ctx, int phase);
+void prof_release(hci_ctx* ctx);
+
+// Every kernel launch of the library goes through HCI_LAUNCH, which counts it.
+extern std::atomic<long long> g_hci_launches;
+inline void hci_count_launch() { g_hci_launches.fetch_add(1, std::memory_order_relaxed); }
+#define HCI_LAUNCH(k, ...) hci_count_launch(), k<<<__VA_ARGS__>>>
 
 // ----------------------------------------------------------------------------
 // error helpers

@@ -196,9 +196,9 @@ hci_status scan_i64(hci_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, in
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   HCI_TRY(ensure_buf(ctx, ctx->s_scan, (size_t)nb * sizeof(int64_t)));
   int64_t* bsum = bp<int64_t>(ctx->s_scan);
-  k_scan_reduce<<<(unsigned)nb, SCAN_BLOCK, 0, ctx->st>>>(in, n, bsum);
-  k_scan_sums<<<1, 1024, 0, ctx->st>>>(bsum, nb, total_dev);
-  k_scan_final<<<(unsigned)nb, SCAN_BLOCK, 0, ctx->st>>>(in, out, n, bsum);
+  HCI_LAUNCH(k_scan_reduce, (unsigned)nb, SCAN_BLOCK, 0, ctx->st)(in, n, bsum);
+  HCI_LAUNCH(k_scan_sums, 1, 1024, 0, ctx->st)(bsum, nb, total_dev);
+  HCI_LAUNCH(k_scan_final, (unsigned)nb, SCAN_BLOCK, 0, ctx->st)(in, out, n, bsum);
   HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
 }
@@ -215,9 +215,9 @@ hci_status sort_keys(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, int64_t n, int
   for (int word = 0; word < 2; ++word) {
     int bits = word == 0 ? bits_b : bits_a;
     for (int shift = 0; shift < bits; shift += 8) {
-      k_rs_hist<<<(unsigned)ntiles, RS_BLOCK, 0, ctx->st>>>(a, n, word, shift, hist, ntiles);
+      HCI_LAUNCH(k_rs_hist, (unsigned)ntiles, RS_BLOCK, 0, ctx->st)(a, n, word, shift, hist, ntiles);
       HCI_TRY(scan_i64(ctx, hist, offs, ntiles * 256, nullptr));
-      k_rs_scatter<<<(unsigned)ntiles, RS_BLOCK, 0, ctx->st>>>(a, b, n, word, shift, offs, ntiles);
+      HCI_LAUNCH(k_rs_scatter, (unsigned)ntiles, RS_BLOCK, 0, ctx->st)(a, b, n, word, shift, offs, ntiles);
       ulonglong2* t = a; a = b; b = t;
       ++passes;
     }
@@ -233,7 +233,7 @@ hci_status hash_keys(hci_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t* ha
   unsigned long long* d = bp<unsigned long long>(ctx->s_counter);
   HCI_CUDA(ctx, cudaMemsetAsync(d, 0, 16, ctx->st));
   if (n > 0)
-    k_hash<<<grid_for(n, 256, 152 * 8), 256, 0, ctx->st>>>(reinterpret_cast<const ulonglong2*>(keys), n, d);
+    HCI_LAUNCH(k_hash, grid_for(n, 256, 152 * 8), 256, 0, ctx->st)(reinterpret_cast<const ulonglong2*>(keys), n, d);
   unsigned long long hv[2];
   HCI_CUDA(ctx, cudaMemcpyAsync(hv, d, 16, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
@@ -246,7 +246,7 @@ hci_status check_sorted(hci_ctx* ctx, const uint64_t* keys, int64_t n, int* ok_h
   int* d = reinterpret_cast<int*>(bp<char>(ctx->s_counter) + 32);
   HCI_CUDA(ctx, cudaMemsetAsync(d, 0, sizeof(int), ctx->st));
   if (n > 1)
-    k_check_sorted<<<grid_for(n, 256, 152 * 8), 256, 0, ctx->st>>>(reinterpret_cast<const ulonglong2*>(keys), n, d);
+    HCI_LAUNCH(k_check_sorted, grid_for(n, 256, 152 * 8), 256, 0, ctx->st)(reinterpret_cast<const ulonglong2*>(keys), n, d);
   int bad = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&bad, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));

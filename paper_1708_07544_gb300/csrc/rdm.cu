@@ -1,6 +1,6 @@
 // Spin-summed variational 1- and 2-RDMs accumulated over the connections of
-// V (Sec. IV: "looping over such connections and accumulating the
-// contributions"; Gamma^{c,c} of Eq. vdedk2).
+// V (Sec. IV: the variational RDMs reuse the single/double connections of
+// the Hamiltonian build; Gamma^{c,c} of Eq. vdedk2).
 //
 //   rdm1[p,q]     = sum_s  <a+_ps a_qs>
 //   rdm2[p,q,r,s] = sum_st <a+_ps a+_rt a_st a_qs>
@@ -162,6 +162,7 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   HCI_TRY(graph_ensure(ctx, keys, nV));
   const int n = ctx->n;
   cudaStream_t st = ctx->st;
+  prof_tic(ctx, HCI_PH_RDM);
   const size_t n2 = (size_t)n * n, n4 = n2 * n2;
   HCI_CUDA(ctx, cudaMemsetAsync(rdm1, 0, n2 * 8, st));
   HCI_CUDA(ctx, cudaMemsetAsync(rdm2, 0, n4 * 8, st));
@@ -171,14 +172,15 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   const ulonglong2* V = bp<ulonglong2>(ctx->graph.keys);
   const size_t smem = (size_t)4 * n2 * 8;
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_occ_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 64 * 64 * 8));
-  k_occ_corr<<<grid_for(nV, 256, 152 * 2), 256, smem, st>>>(n, V, nV, c, M);
-  k_diag_rdm<<<grid_for((int64_t)n2, 256), 256, 0, st>>>(n, M, rdm1, rdm2);
+  HCI_LAUNCH(k_occ_corr, grid_for(nV, 256, 152 * 2), 256, smem, st)(n, V, nV, c, M);
+  HCI_LAUNCH(k_diag_rdm, grid_for((int64_t)n2, 256), 256, 0, st)(n, M, rdm1, rdm2);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 56);
   HCI_CUDA(ctx, cudaMemsetAsync(queue, 0, 8, st));
-  k_rdm_offdiag<<<152 * 8, R_WARPS * 32, 0, st>>>(n, V, nV, c, bp<int64_t>(ctx->graph.rowptr),
+  HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, V, nV, c, bp<int64_t>(ctx->graph.rowptr),
                                                    bp<int32_t>(ctx->graph.col), rdm1, rdm2, queue);
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_RDM);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   return HCI_OK;
 }

@@ -175,14 +175,14 @@ inline unsigned blocks(int64_t work, int b = 256) { return (unsigned)((work + b 
 
 hci_status mm(cudaStream_t st, int m, const double* A, int tA, const double* B, int tB, double* C, double alpha,
               double beta) {
-  k_mm<<<blocks((int64_t)m * m), 256, 0, st>>>(m, A, tA, B, tB, C, alpha, beta);
+  HCI_LAUNCH(k_mm, blocks((int64_t)m * m), 256, 0, st)(m, A, tA, B, tB, C, alpha, beta);
   return HCI_OK;
 }
 
 // E = exp(A) for an m x m matrix; w1, w2, w3 scratch of m*m
 hci_status expm_dev(cudaStream_t st, int m, const double* A, double* E, double* w1, double* w2, double* w3,
                     double* dscal) {
-  k_norm1<<<1, 256, 0, st>>>(m, A, dscal);
+  HCI_LAUNCH(k_norm1, 1, 256, 0, st)(m, A, dscal);
   double nrm = 0.0;
   if (cudaMemcpyAsync(&nrm, dscal, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HCI_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HCI_ERR_CUDA;
@@ -190,13 +190,13 @@ hci_status expm_dev(cudaStream_t st, int m, const double* A, double* E, double* 
   int s = 0;
   while (nrm / std::ldexp(1.0, s) > 0.5) ++s;
   const double sc = std::ldexp(1.0, -s);
-  k_scale_copy<<<blocks((int64_t)m * m), 256, 0, st>>>((int64_t)m * m, A, sc, w1);   // X
+  HCI_LAUNCH(k_scale_copy, blocks((int64_t)m * m), 256, 0, st)((int64_t)m * m, A, sc, w1);   // X
   // Horner: E = I + X/18; E = I + X E / k for k = 17..1
   const int deg = 18;
-  k_eye_plus<<<blocks((int64_t)m * m), 256, 0, st>>>(m, w1, 1.0 / deg, E);
+  HCI_LAUNCH(k_eye_plus, blocks((int64_t)m * m), 256, 0, st)(m, w1, 1.0 / deg, E);
   for (int k = deg - 1; k >= 1; --k) {
     mm(st, m, w1, 0, E, 0, w2, 1.0, 0.0);
-    k_horner<<<blocks((int64_t)m * m), 256, 0, st>>>(m, w2, E, 1.0 / k);
+    HCI_LAUNCH(k_horner, blocks((int64_t)m * m), 256, 0, st)(m, w2, E, 1.0 / k);
   }
   for (int i = 0; i < s; ++i) {
     mm(st, m, E, 0, E, 0, w3, 1.0, 0.0);
@@ -208,7 +208,7 @@ hci_status expm_dev(cudaStream_t st, int m, const double* A, double* E, double* 
 void qtrans(cudaStream_t st, int n, const double* in, const double* M, double* out) {
   const int64_t N3 = (int64_t)n * n * n;
   size_t smem = (size_t)(n * n + n * QT_J) * 8;
-  k_qtrans<<<blocks(N3, QT_J), 256, smem, st>>>(n, in, M, out);
+  HCI_LAUNCH(k_qtrans, blocks(N3, QT_J), 256, smem, st)(n, in, M, out);
 }
 
 }  // namespace
@@ -262,14 +262,14 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
   cudaFuncSetAttribute(k_gemm_nt_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * NT_CH * 8);
   hci_status s = expm_dev(st, n, kappa, U, w1, b1, b2, ds);
   if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_backward: matrix exponential failed");
-  k_eye<<<blocks((int64_t)n2), 256, 0, st>>>(n, I);
+  HCI_LAUNCH(k_eye, blocks((int64_t)n2), 256, 0, st)(n, I);
   // U^T as a matrix for the back-transforms: M[a][p] = U[p][a]
   mm(st, n, U, 1, I, 0, Ut, 1.0, 0.0);
   if (dh) {
     mm(st, n, rdm1, 0, U, 1, w1, 1.0, 0.0);     // g1 U^T
     mm(st, n, U, 0, w1, 0, dh, 1.0, 0.0);       // U g1 U^T
   }
-  k_scale_copy<<<blocks((int64_t)n4), 256, 0, st>>>((int64_t)n4, rdm2, 0.5, D);
+  HCI_LAUNCH(k_scale_copy, blocks((int64_t)n4), 256, 0, st)((int64_t)n4, rdm2, 0.5, D);
   if (deri) {
     qtrans(st, n, D, Ut, t4);
     qtrans(st, n, t4, Ut, deri);
@@ -292,13 +292,13 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
     const int nparts = (int)((K + NT_CH - 1) / NT_CH);
     double* part = S.get((size_t)nparts * n2);
     if (!part) return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed");
-    k_gemm_nt_part<<<nparts, 256, (size_t)2 * n * NT_CH * 8, st>>>(n, K, eri, D, part);
-    k_sum_parts<<<blocks((int64_t)n2), 256, 0, st>>>((int)n2, nparts, part, 4.0, gU);
+    HCI_LAUNCH(k_gemm_nt_part, nparts, 256, (size_t)2 * n * NT_CH * 8, st)(n, K, eri, D, part);
+    HCI_LAUNCH(k_sum_parts, blocks((int64_t)n2), 256, 0, st)((int)n2, nparts, part, 4.0, gU);
     // dkappa = L_exp(kappa^T, gU)
-    k_frechet_block<<<blocks((int64_t)m2 * m2), 256, 0, st>>>(n, kappa, gU, b1);
+    HCI_LAUNCH(k_frechet_block, blocks((int64_t)m2 * m2), 256, 0, st)(n, kappa, gU, b1);
     s = expm_dev(st, m2, b1, b2, b3, b4, b5, ds);
     if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_backward: Frechet exponential failed");
-    k_upper_right<<<blocks((int64_t)n2), 256, 0, st>>>(n, b2, dkappa);
+    HCI_LAUNCH(k_upper_right, blocks((int64_t)n2), 256, 0, st)(n, b2, dkappa);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));

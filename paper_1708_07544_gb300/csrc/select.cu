@@ -287,13 +287,15 @@ __global__ void k_merge_new(const ulonglong2* __restrict__ V, int64_t nV, const 
 }  // namespace
 
 static hci_status run_walk(hci_ctx* ctx, WalkArgs& A, int64_t* total) {
+  prof_tic(ctx, HCI_PH_WALK);
   HCI_CUDA(ctx, cudaMemsetAsync(A.counter, 0, 16, ctx->st));
   const int grid = 152 * 8;
-  k_walk_doubles<<<grid, SEL_WARPS * 32, 0, ctx->st>>>(A);
+  HCI_LAUNCH(k_walk_doubles, grid, SEL_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   HCI_CUDA(ctx, cudaMemsetAsync(A.counter + 1, 0, 8, ctx->st));
-  k_singles<<<grid, SEL_WARPS * 32, 0, ctx->st>>>(A);
+  HCI_LAUNCH(k_singles, grid, SEL_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_WALK);
   unsigned long long cnt = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&cnt, A.counter, 8, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
@@ -343,17 +345,22 @@ extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys
     if (m2 != m) return hci_fail(ctx, HCI_ERR_CUDA, "hci_select: candidate count changed between runs");
   }
   ctx->last_candidates = m;
+  ctx->st_counts[HCI_ST_SELECT_CALLS] += 1;
+  ctx->st_counts[HCI_ST_SELECT_SOURCES] += nV;
+  ctx->st_counts[HCI_ST_CANDIDATES] += m;
   if (m == 0) return HCI_OK;
+  prof_tic(ctx, HCI_PH_DEDUP);
   HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)m * 16));
   HCI_TRY(sort_keys(ctx, bp<uint64_t>(ctx->s_cand), bp<uint64_t>(ctx->s_cand2), m, ctx->n, ctx->n));
   HCI_TRY(ensure_buf(ctx, ctx->s_flags, (size_t)(2 * m + 1) * 8));
   int64_t* flag = bp<int64_t>(ctx->s_flags);
   int64_t* pos = flag + m;
   int64_t* total = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 16);
-  k_flag_new<<<grid_for(m, 256), 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->s_cand), m,
+  HCI_LAUNCH(k_flag_new, grid_for(m, 256), 256, 0, ctx->st)(bp<ulonglong2>(ctx->s_cand), m,
                                                     reinterpret_cast<const ulonglong2*>(keys), nV, flag);
   HCI_CUDA(ctx, cudaGetLastError());
   HCI_TRY(scan_i64(ctx, flag, pos, m, total));
+  prof_toc(ctx, HCI_PH_DEDUP);
   int64_t cnt = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&cnt, total, 8, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
@@ -361,7 +368,7 @@ extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys
   if (cnt > cap)
     return hci_fail(ctx, HCI_ERR_CAPACITY, "hci_select: %lld new determinants exceed cap %lld", (long long)cnt,
                     (long long)cap);
-  k_compact<<<grid_for(m, 256), 256, 0, ctx->st>>>(bp<ulonglong2>(ctx->s_cand), m, flag, pos,
+  HCI_LAUNCH(k_compact, grid_for(m, 256), 256, 0, ctx->st)(bp<ulonglong2>(ctx->s_cand), m, flag, pos,
                                                    reinterpret_cast<ulonglong2*>(new_keys), cap);
   HCI_CUDA(ctx, cudaGetLastError());
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
@@ -376,10 +383,12 @@ extern "C" hci_status hci_merge(hci_ctx* ctx, const uint64_t* keys, const double
   const ulonglong2* V = reinterpret_cast<const ulonglong2*>(keys);
   const ulonglong2* N = reinterpret_cast<const ulonglong2*>(new_keys);
   ulonglong2* O = reinterpret_cast<ulonglong2*>(out_keys);
+  prof_tic(ctx, HCI_PH_MERGE);
   if (nV > 0)
-    k_merge_old<<<grid_for(nV, 256), 256, 0, ctx->st>>>(V, c, nV, N, n_new, O, out_c);
+    HCI_LAUNCH(k_merge_old, grid_for(nV, 256), 256, 0, ctx->st)(V, c, nV, N, n_new, O, out_c);
   if (n_new > 0)
-    k_merge_new<<<grid_for(n_new, 256), 256, 0, ctx->st>>>(V, nV, N, n_new, O, out_c);
+    HCI_LAUNCH(k_merge_new, grid_for(n_new, 256), 256, 0, ctx->st)(V, nV, N, n_new, O, out_c);
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_MERGE);
   return HCI_OK;
 }

@@ -34,7 +34,7 @@ extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double 
   int64_t nV = 1;
   hci_status s;
   if ((s = ensure_buf(ctx, kb[0], 16)) != HCI_OK || (s = ensure_buf(ctx, cb[0], 8)) != HCI_OK) { cleanup(); return s; }
-  k_aufbau<<<1, 1, 0, st>>>(ctx->na, ctx->nb, bp<ulonglong2>(kb[0]), bp<double>(cb[0]));
+  HCI_LAUNCH(k_aufbau, 1, 1, 0, st)(ctx->na, ctx->nb, bp<ulonglong2>(kb[0]), bp<double>(cb[0]));
   double e = 0.0;
   int dav_it = 0;
   s = hci_davidson(ctx, bp<uint64_t>(kb[0]), 1, bp<double>(cb[0]), &e, dav_tol, dav_maxit, &dav_it);

@@ -57,6 +57,12 @@ class HCISolver:
     def stats(self):
         return _abi.hci_stats(self.ctx)
 
+    def profile(self, enable=True):
+        _abi.hci_profile(self.ctx, enable)
+
+    def timers(self):
+        return _abi.hci_timers(self.ctx)
+
 
 class HCIEnergy(torch.autograd.Function):
     """E(h, eri, kappa) = variational HCI energy of the rotated integrals.

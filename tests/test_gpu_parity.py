@@ -254,3 +254,49 @@ def test_capacity_error_reports_required_size(pkg):
         st = L.hci_select(s.ctx, 1e-4, bad.data_ptr(), torch.ones(2, dtype=torch.float64).cuda().data_ptr(), 2,
                           out.data_ptr(), 4, ctypes.byref(n))
         assert st == _abi.HCI_ERR_INVALID
+
+
+@pytest.mark.parametrize("name,make,nv", [CASES[1], CASES[2]])
+def test_incremental_graph_matches_oracle(pkg, name, make, nv):
+    """A space that grows by merges reuses the cached graph (new rows only,
+    transposes appended to old rows); the product must equal the oracle's
+    H c on every space of the chain, and a space that is not a superset
+    falls back to a full rebuild."""
+    inst = make()
+    allk = hi.random_det_keys(inst.norb, inst.nalpha, inst.nbeta, nv, seed=nv + 21)
+    rng = np.random.default_rng(nv)
+    order = rng.permutation(len(allk))
+    sizes = [len(allk) // 5, len(allk) // 2, len(allk) - 3, len(allk)]
+    with solver(pkg, inst) as s:
+        builds0 = s.stats()["graph_builds"]
+        for m in sizes:
+            sub = allk[np.sort(order[:m])]
+            c = hi.random_vector(len(sub), seed=m)
+            got = s.sigma(dev_keys(sub), torch.tensor(c).cuda()).cpu().numpy()
+            H = oracle.hamiltonian(inst, sub)
+            want = H @ c
+            assert np.abs(got - want).max() < 1e-11 * max(1.0, np.abs(want).max()), m
+            assert s.stats()["graph_nnz"] == H.nnz - len(sub)
+        assert s.stats()["graph_builds"] - builds0 == len(sizes)
+        # shrink: not an extension
+        sub = allk[np.sort(order[: len(allk) // 3])]
+        c = hi.random_vector(len(sub), seed=5)
+        got = s.sigma(dev_keys(sub), torch.tensor(c).cuda()).cpu().numpy()
+        assert np.abs(got - oracle.hamiltonian(inst, sub) @ c).max() < 1e-11 * max(1.0, np.abs(got).max())
+
+
+def test_incremental_solve_matches_fresh_contexts(pkg, poly8_ref):
+    """Davidson on each space of an HCI run with one context (incremental
+    graphs) equals the oracle's eigenvalue on that space."""
+    inst, r4, _ = poly8_ref
+    keys = oracle.aufbau(4, 4)
+    c = np.array([1.0])
+    with solver(pkg, inst) as s:
+        for _ in range(4):
+            new, _, _ = oracle.select(inst, keys, c, 1e-4)
+            if len(new) == 0:
+                break
+            keys, c = oracle.merge(keys, c, new)
+            e, cg, _ = s.davidson(dev_keys(keys), torch.tensor(c).cuda(), tol=1e-10)
+            e_ref, c = oracle.ground_state(inst, keys)
+            assert abs(e - e_ref) < E_TOL
