@@ -157,6 +157,24 @@ hci_status hci_rotate_backward(int norb, const double* kappa, const double* h, c
                                const double* rdm1, const double* rdm2, double* dh, double* deri,
                                double* dkappa, void* stream);
 
+/* hci_rotate without any device allocation (the paper has no counterpart:
+ * this is a deployment variant).  For callers that cannot allocate device
+ * memory when they need the rotation -- code inside another framework's
+ * memory pool that forbids foreign allocations, or a host thread that must
+ * not call cudaMalloc/cudaFree because those may synchronise the device.
+ * Same arguments, outputs and results as hci_rotate; the caller still
+ * provides every input and output buffer.  Scratch (one norb^4
+ * intermediate and the exp(kappa) work matrices) lives in a static device
+ * array of about 8 MiB that every GPU loading this library holds until the
+ * process exits; norb above 32 is rejected with HCI_ERR_INVALID.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it, so make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Synchronises the stream. */
+hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, const double* eri, double* U,
+                              double* h_out, double* eri_out, void* stream);
+
 /* Work counters of this context (instrumentation; the paper reports only
  * wall times per HCISCF iteration, Sec. V).  out[k] for k < nout:
  *   HCI_ST_GRAPH_NNZ        off-diagonal connections of the cached graph

@@ -26,7 +26,7 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
-           "hci_stats", "hci_profile", "hci_timers", "hci_launch_count"]
+           "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
          "select_sources", "candidates", "graph_builds"]
@@ -68,6 +68,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
+    L.hci_rotate_noalloc.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_stats.argtypes = [V, V, I]
     L.hci_profile.argtypes = [V, I]
     L.hci_timers.argtypes = [V, V, V, I]

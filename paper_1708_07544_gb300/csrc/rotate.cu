@@ -15,6 +15,7 @@
 // FP64 on CUDA cores: double-precision tensor throughput on this part is no
 // higher than the FP64 pipe, and the contraction is a small share of a solve.
 #include <cmath>
+#include <mutex>
 
 #include "hci_internal.cuh"
 
@@ -304,5 +305,91 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));
+  return HCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free rotation.
+//
+// Some callers cannot allocate device memory at the time they need the
+// rotation: code running inside another framework's memory pool that forbids
+// foreign allocations, or a host thread that must not perform a
+// cudaMalloc/cudaFree (each may synchronise the device).  For them
+// hci_rotate_noalloc computes exactly what hci_rotate computes, with its
+// scratch (the n^4 intermediate of the quarter transforms and the work
+// matrices of exp(kappa)) in the file-scope device array below instead of
+// stream-ordered allocations.  The array is part of this library's module:
+// every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAXORB = 32;
+constexpr size_t NOALLOC_T4 = (size_t)NOALLOC_MAXORB * NOALLOC_MAXORB * NOALLOC_MAXORB * NOALLOC_MAXORB;
+constexpr size_t NOALLOC_M = (size_t)NOALLOC_MAXORB * NOALLOC_MAXORB;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_T4 + 3 * NOALLOC_M + 32;   // 8.02 MiB
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+constexpr int NOALLOC_MAXDEV = 64;
+static double* g_noalloc_ptr[NOALLOC_MAXDEV] = {};
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+hci_status noalloc_scratch(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= NOALLOC_MAXDEV)
+    return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate_noalloc: device %d outside [0,%d)", dev, NOALLOC_MAXDEV);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = reinterpret_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return HCI_OK;
+}
+
+}  // namespace
+
+extern "C" hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, const double* eri, double* U,
+                                         double* h_out, double* eri_out, void* stream) {
+  const int n = norb;
+  if (n < 1 || n > NOALLOC_MAXORB)
+    return hci_fail(nullptr, HCI_ERR_INVALID,
+                    "hci_rotate_noalloc: norb=%d outside [1,%d] (the static scratch holds one %d^4 intermediate)", n,
+                    NOALLOC_MAXORB, NOALLOC_MAXORB);
+  if (!kappa || !h || !eri || !U || !h_out || !eri_out)
+    return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate_noalloc: null pointer");
+  double* base = nullptr;
+  hci_status s = noalloc_scratch(&base);
+  if (s != HCI_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  // every scratch element read below is written first in the same call, so
+  // nothing has to be cleared; calls that overlap on the GPU share the array
+  // and race
+  double* t4 = base;
+  double* w1 = base + NOALLOC_T4;
+  double* w2 = w1 + NOALLOC_M;
+  double* w3 = w2 + NOALLOC_M;
+  double* ds = w3 + NOALLOC_M;
+  s = expm_dev(st, n, kappa, U, w1, w2, w3, ds);
+  if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_noalloc: matrix exponential failed");
+  mm(st, n, h, 0, U, 0, w1, 1.0, 0.0);          // h U
+  mm(st, n, U, 1, w1, 0, h_out, 1.0, 0.0);      // U^T h U
+  qtrans(st, n, eri, U, t4);
+  qtrans(st, n, t4, U, eri_out);
+  qtrans(st, n, eri_out, U, t4);
+  qtrans(st, n, t4, U, eri_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: %s", cudaGetErrorString(e));
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: %s", cudaGetErrorString(e));
   return HCI_OK;
 }
