@@ -185,25 +185,33 @@ hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, co
  *   HCI_ST_SELECT_CALLS     selection steps so far
  *   HCI_ST_SELECT_SOURCES   source determinants offered to them
  *   HCI_ST_CANDIDATES       candidates emitted by them in total
- *   HCI_ST_GRAPH_BUILDS     connection graphs built */
+ *   HCI_ST_GRAPH_BUILDS     connection graphs built
+ *   HCI_ST_WALK_ENTRIES     list entries examined by the heat-bath walks
+ *   HCI_ST_SINGLES_EXACT    single excitations evaluated exactly */
 enum {
   HCI_ST_GRAPH_NNZ = 0, HCI_ST_LAST_CANDIDATES = 1, HCI_ST_SIGMA_CALLS = 2, HCI_ST_SIGMA_ROWS = 3,
   HCI_ST_SIGMA_NNZ = 4, HCI_ST_SELECT_CALLS = 5, HCI_ST_SELECT_SOURCES = 6, HCI_ST_CANDIDATES = 7,
-  HCI_ST_GRAPH_BUILDS = 8, HCI_ST_COUNT = 9
+  HCI_ST_GRAPH_BUILDS = 8, HCI_ST_WALK_ENTRIES = 9, HCI_ST_SINGLES_EXACT = 10, HCI_ST_COUNT = 11
 };
 hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout);
 
 /* Phases timed by hci_profile / hci_timers. */
 enum {
   HCI_PH_LISTS = 0,     /* heat-bath list build */
-  HCI_PH_WALK = 1,      /* heat-bath walk + singles (candidate generation) */
+  HCI_PH_WALK = 1,      /* heat-bath walk over the double-excitation lists */
   HCI_PH_DEDUP = 2,     /* radix sort, set difference against V, compaction */
   HCI_PH_MERGE = 3,     /* sorted union V + C */
   HCI_PH_GRAPH = 4,     /* connection graph + diagonal of a new space */
   HCI_PH_SIGMA = 5,     /* the sigma kernel alone (one entry per H c product) */
   HCI_PH_DAVIDSON = 6,  /* hci_davidson excluding the graph build */
   HCI_PH_RDM = 7,       /* hci_rdm12 excluding the graph build */
-  HCI_PH_COUNT = 8
+  HCI_PH_SINGLES = 8,   /* single excitations of the selection */
+  HCI_PH_GRAPH_SPACE = 9,  /* string groups, beta-major order, neighbour lists */
+  HCI_PH_GRAPH_ROWS = 10,  /* row search and element evaluation */
+  HCI_PH_GRAPH_MERGE = 11, /* incremental update: transposes and CSR merge */
+  HCI_PH_RDM_DIAG = 12,    /* diagonal part of the RDMs */
+  HCI_PH_HDIAG = 13,       /* diagonal Hamiltonian elements */
+  HCI_PH_COUNT = 14
 };
 
 /* Enable (1) or disable (0) per-phase CUDA-event timing on the context

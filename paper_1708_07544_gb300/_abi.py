@@ -27,9 +27,10 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc"]
-PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm"]
+PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
+          "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
-         "select_sources", "candidates", "graph_builds"]
+         "select_sources", "candidates", "graph_builds", "walk_entries", "singles_exact"]
 
 
 class HCIError(RuntimeError):

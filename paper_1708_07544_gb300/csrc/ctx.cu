@@ -146,6 +146,27 @@ __global__ void k_build_lists(int n, const double* __restrict__ eri, int same, i
   }
 }
 
+// f_ref[s][p][r] = h_pr + sum_{k occ in spin s of R} ((pr|kk) - (pk|kr))
+//                       + sum_{k occ in the other spin of R} (pr|kk),  R = aufbau
+__global__ void k_fref(int n, int na, int nb, const double* __restrict__ h, const double* __restrict__ jk_same,
+                       const double* __restrict__ j_opp, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * n * n) return;
+  const int s = t / (n * n), p = (t / n) % n, r = t % n;
+  const int ns = s == 0 ? na : nb, no = s == 0 ? nb : na;
+  double v = h[p * n + r];
+  for (int k = 0; k < n; ++k) {
+    if (k < ns) v += jk_same[((int64_t)p * n + r) * n + k];
+    if (k < no) v += j_opp[((int64_t)p * n + r) * n + k];
+  }
+  out[t] = v;
+}
+
+__global__ void k_gather_first(const double* __restrict__ mag, int nlists, int L, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nlists) out[t] = mag[(int64_t)t * L];
+}
+
 __global__ void k_max_first(const double* __restrict__ mag, int nlists, int L, double* out) {
   double m = 0.0;
   for (int i = threadIdx.x; i < nlists; i += blockDim.x) m = fmax(m, mag[(int64_t)i * L]);
@@ -234,13 +255,14 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
   if (!ctx) return HCI_OK;
   cudaStream_t st = ctx->st;
   DevBuf* bufs[] = {&ctx->h, &ctx->eri, &ctx->jk_same, &ctx->j_opp, &ctx->lists.opp_mag, &ctx->lists.opp_tgt,
+                    &ctx->lists.list_max, &ctx->lists.f_ref, &ctx->s_items,
                     &ctx->lists.same_mag, &ctx->lists.same_tgt, &ctx->lists.single_bound,
                     &ctx->graph.rowptr, &ctx->graph.col, &ctx->graph.val, &ctx->graph.diag, &ctx->graph.keys,
                     &ctx->s_cand, &ctx->s_cand2, &ctx->s_flags, &ctx->s_scan, &ctx->s_misc, &ctx->s_counter,
                     &ctx->s_hist, &ctx->g_ua, &ctx->g_ga, &ctx->g_ia, &ctx->g_ub, &ctx->g_gb, &ctx->g_ib,
                     &ctx->g_permb, &ctx->g_bkeys, &ctx->g_bkeys2, &ctx->g_nbr_ptr, &ctx->g_nbr, &ctx->g_cnt,
                     &ctx->d_vb, &ctx->d_wb, &ctx->d_diag, &ctx->d_small, &ctx->d_part,
-                    &ctx->g_bnbr_ptr, &ctx->g_bnbr, &ctx->g_costa, &ctx->g_costb,
+                    &ctx->g_bnbr_ptr, &ctx->g_bnbr, &ctx->g_costa, &ctx->g_costb, &ctx->s_walkstat,
                     &ctx->inc.pos_old, &ctx->inc.mark, &ctx->inc.flag, &ctx->inc.newrows, &ctx->inc.rpN,
                     &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.cnt, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T,
                     &ctx->inc.T2, &ctx->inc.tstart, &ctx->inc.len, &ctx->inc.keys_old, &ctx->inc.rp_old,
@@ -285,6 +307,16 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
                                                          bp<double>(L.same_mag), bp<uint16_t>(L.same_tgt));
     HCI_CUDA(ctx, cudaGetLastError());
   }
+  HCI_TRY(ensure_buf(ctx, L.f_ref, (size_t)2 * n * n * 8));
+  HCI_LAUNCH(k_fref, (2 * n * n + 255) / 256, 256, 0, ctx->st)(n, ctx->na, ctx->nb, bp<double>(ctx->h),
+                                                              bp<double>(ctx->jk_same), bp<double>(ctx->j_opp),
+                                                              bp<double>(L.f_ref));
+  HCI_TRY(ensure_buf(ctx, L.list_max, (size_t)(n * n + L.npair_same + 1) * 8));
+  HCI_LAUNCH(k_gather_first, (n * n + 255) / 256, 256, 0, ctx->st)(bp<double>(L.opp_mag), n * n, L.len_opp,
+                                                                  bp<double>(L.list_max));
+  if (L.npair_same > 0)
+    HCI_LAUNCH(k_gather_first, (L.npair_same + 255) / 256, 256, 0, ctx->st)(
+        bp<double>(L.same_mag), L.npair_same, L.len_same, bp<double>(L.list_max) + n * n);
   HCI_TRY(ensure_buf(ctx, ctx->s_misc, 64));
   double* dm = bp<double>(ctx->s_misc);
   HCI_CUDA(ctx, cudaMemsetAsync(dm, 0, 64, ctx->st));

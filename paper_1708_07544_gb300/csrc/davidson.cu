@@ -75,72 +75,99 @@ __global__ void k_set_gcol(DavDev* d, int col) {
   }
 }
 
-// lowest eigenpair of the k x k subspace matrix by cyclic Jacobi (one warp)
+// Lowest eigenpair of the k x k subspace matrix by parallel-order Jacobi on
+// one warp: in each round the indices are paired by a round-robin schedule
+// and all disjoint pairs rotate at once (their rotations commute), so a
+// sweep is k-1 rounds of parallel row and column updates.  An off-diagonal
+// element too small to change either diagonal partner in floating point
+// (even scaled by 100) is zeroed; the sweeps stop when a sweep rotates none.
 __global__ void k_jacobi(DavDev* d, int k) {
   __shared__ double A[32][33];
   __shared__ double Q[32][33];
+  __shared__ double rc[16], rs[16];
+  __shared__ int rp[16], rq[16];
   const int l = threadIdx.x;
   for (int j = 0; j < 32; ++j) {
     A[l][j] = (l < k && j < k) ? d->G[l * LDG + j] : 0.0;
     Q[l][j] = (l == j) ? 1.0 : 0.0;
   }
   __syncwarp();
-  // cyclic sweeps; an off-diagonal element too small to change either of its
-  // diagonal partners in floating point (even scaled by 100) is set to zero,
-  // a rotated pair is zeroed exactly, and the sweeps stop once a sweep makes
-  // no rotation
-  for (int sweep = 0; sweep < 50; ++sweep) {
+  const int m = (k + 1) & ~1;          // even number of players (index k is a dummy when k is odd)
+  const int npairs = m / 2;
+  for (int sweep = 0; sweep < 50 && k > 1; ++sweep) {
     int rotated = 0;
-    for (int p = 0; p < k - 1; ++p) {
-      for (int q = p + 1; q < k; ++q) {
-        double apq = A[p][q];
-        double app = A[p][p], aqq = A[q][q];
-        const double g = 100.0 * fabs(apq);
-        if ((fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq)) || fabs(apq) < 1e-300) {
-          __syncwarp();
-          if (l == 0) { A[p][q] = 0.0; A[q][p] = 0.0; }
-          __syncwarp();
-          continue;
+    for (int r = 0; r < m - 1; ++r) {
+      // lane t < npairs: pair t of round r
+      if (l < npairs) {
+        int a, b;
+        if (l == 0) { a = r; b = m - 1; }
+        else { a = (r + l) % (m - 1); b = (r - l + (m - 1)) % (m - 1); }
+        int p = a < b ? a : b, q = a < b ? b : a;
+        double c = 1.0, sn = 0.0;
+        int active = 0;
+        if (q < k) {
+          const double apq = A[p][q], app = A[p][p], aqq = A[q][q];
+          const double g = 100.0 * fabs(apq);
+          if (!((fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq)) || fabs(apq) < 1e-300)) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+            active = 1;
+          }
         }
-        rotated = 1;
-        double tau = (aqq - app) / (2.0 * apq);
-        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        double c = 1.0 / sqrt(1.0 + t * t);
-        double s = t * c;
-        __syncwarp();
-        if (l < k) {
-          double alp = A[l][p], alq = A[l][q];
-          A[l][p] = c * alp - s * alq;
-          A[l][q] = s * alp + c * alq;
-        }
-        __syncwarp();
-        if (l < k) {
-          double apl = A[p][l], aql = A[q][l];
-          A[p][l] = c * apl - s * aql;
-          A[q][l] = s * apl + c * aql;
-          double vlp = Q[l][p], vlq = Q[l][q];
-          Q[l][p] = c * vlp - s * vlq;
-          Q[l][q] = s * vlp + c * vlq;
-        }
-        __syncwarp();
-        if (l == 0) { A[p][q] = 0.0; A[q][p] = 0.0; }
-        __syncwarp();
+        rp[l] = p; rq[l] = q; rc[l] = c; rs[l] = active ? sn : 0.0;
+        if (!active && q < k) { A[p][q] = 0.0; A[q][p] = 0.0; }
+        rotated |= active;
       }
+      __syncwarp();
+      // columns: A <- A J, Q <- Q J (lane = row)
+      if (l < k) {
+        for (int t = 0; t < npairs; ++t) {
+          const double s2 = rs[t];
+          if (s2 == 0.0) continue;
+          const int p = rp[t], q = rq[t];
+          const double c2 = rc[t];
+          const double alp = A[l][p], alq = A[l][q];
+          A[l][p] = c2 * alp - s2 * alq;
+          A[l][q] = s2 * alp + c2 * alq;
+          const double vlp = Q[l][p], vlq = Q[l][q];
+          Q[l][p] = c2 * vlp - s2 * vlq;
+          Q[l][q] = s2 * vlp + c2 * vlq;
+        }
+      }
+      __syncwarp();
+      // rows: A <- J^T A (lane = column)
+      if (l < k) {
+        for (int t = 0; t < npairs; ++t) {
+          const double s2 = rs[t];
+          if (s2 == 0.0) continue;
+          const int p = rp[t], q = rq[t];
+          const double c2 = rc[t];
+          const double apl = A[p][l], aql = A[q][l];
+          A[p][l] = c2 * apl - s2 * aql;
+          A[q][l] = s2 * apl + c2 * aql;
+        }
+      }
+      __syncwarp();
+      if (l < npairs && rs[l] != 0.0) { A[rp[l]][rq[l]] = 0.0; A[rq[l]][rp[l]] = 0.0; }
+      __syncwarp();
     }
+    rotated = __any_sync(0xffffffffu, rotated);
     if (!rotated) break;
   }
   __syncwarp();
   __shared__ int s_m;
   if (l == 0) {
-    int m = 0;
+    int mm = 0;
     for (int j = 1; j < k; ++j)
-      if (A[j][j] < A[m][m]) m = j;
-    s_m = m;
-    d->theta = A[m][m];
+      if (A[j][j] < A[mm][mm]) mm = j;
+    s_m = mm;
+    d->theta = A[mm][mm];
   }
   __syncwarp();
-  int m = s_m;
-  if (l < LDG) d->y[l] = (l < k) ? Q[l][m] : 0.0;
+  const int mi = s_m;
+  if (l < LDG) d->y[l] = (l < k) ? Q[l][mi] : 0.0;
 }
 
 // x = V y, wy = W y, r = wy - theta x, t = r / (theta - diag) (guarded),

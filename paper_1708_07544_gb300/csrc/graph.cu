@@ -607,18 +607,32 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
   }
 }
 
-// sigma = diag .* c + offdiag * c ; one warp per row.  The single-vector
-// path keeps four independent (col, val, c[col]) chains per lane in flight;
-// the CSR stream is read with evict-first hints so that c stays in L2.
-__global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+// sigma = diag .* c + offdiag * c ; one warp per row.  In the single-vector
+// path each warp owns a contiguous range of rows holding an equal share of
+// the connections and keeps four independent (col, val, c[col]) chains per
+// lane in flight; the CSR stream is read with evict-first hints so that c
+// stays in L2.
+__global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ diag,
                                                int64_t nV, const double* __restrict__ c, double* __restrict__ sigma,
-                                               int nvec) {
+                                               int nvec_unused) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  if (nvec == 1) {
-    for (int64_t i = warp; i < nV; i += nwarps) {
+  {
+    // contiguous row ranges holding an equal share of the connections
+    const int64_t tot = rowptr[nV];
+    const int64_t chunk = (tot + nwarps - 1) / nwarps;
+    int64_t r0, r1;
+    {
+      int64_t lo = 0, hi = nV, x = warp * chunk;
+      while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (rowptr[mid] < x) lo = mid + 1; else hi = mid; }
+      r0 = lo;
+      lo = r0; hi = nV; x = (warp + 1) * chunk;
+      while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (rowptr[mid] < x) lo = mid + 1; else hi = mid; }
+      r1 = warp == nwarps - 1 ? nV : lo;
+    }
+    for (int64_t i = r0; i < r1; ++i) {
       const int64_t b = rowptr[i], e = rowptr[i + 1];
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       int64_t k = b + lane;
@@ -637,8 +651,17 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
       for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       if (lane == 0) sigma[i] = fma(diag[i], c[i], a);
     }
-    return;
   }
+}
+
+// several vectors at once (one pass over the connections per 4 vectors)
+__global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                               const double* __restrict__ val, const double* __restrict__ diag,
+                                               int64_t nV, const double* __restrict__ c, double* __restrict__ sigma,
+                                               int nvec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < nV; i += nwarps) {
     const int64_t b = rowptr[i], e = rowptr[i + 1];
     for (int v0 = 0; v0 < nvec; v0 += 4) {
@@ -673,6 +696,7 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
 // distinct alpha and beta strings, and the (C) search cost per string.
 static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   Graph& G = ctx->graph;
+  prof_tic(ctx, HCI_PH_GRAPH_SPACE);
   const int n = ctx->n;
   const ulonglong2* V = bp<ulonglong2>(G.keys);
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
@@ -710,6 +734,8 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   HCI_CUDA(ctx, cudaMemcpyAsync(&nub, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaGetLastError());
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  G.nua = nua;
+  G.nub = nub;
   // neighbour lists of both spins
   DevBuf* ptrs[2] = {&ctx->g_nbr_ptr, &ctx->g_bnbr_ptr};
   DevBuf* lists[2] = {&ctx->g_nbr, &ctx->g_bnbr};
@@ -752,6 +778,7 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   A.rowlist = nullptr;
   A.nrows = nV;
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr; A.rowcnt = nullptr;
+  prof_toc(ctx, HCI_PH_GRAPH_SPACE);
   return HCI_OK;
 }
 
@@ -761,6 +788,7 @@ static hci_status rows_csr(hci_ctx* ctx, GraphArgs& A, DevBuf& rowptr, DevBuf& c
                            int64_t* nnz_out) {
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
   const int64_t nr = A.nrows;
+  prof_tic(ctx, HCI_PH_GRAPH_ROWS);
   HCI_TRY(ensure_buf(ctx, rowptr, (size_t)(nr + 1) * 8));
   HCI_TRY(ensure_buf(ctx, cnt, (size_t)(nr + 1) * 8));
   A.rowcnt = bp<int64_t>(cnt);
@@ -781,6 +809,7 @@ static hci_status rows_csr(hci_ctx* ctx, GraphArgs& A, DevBuf& rowptr, DevBuf& c
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
   HCI_LAUNCH(k_rows<true>, grows, G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_GRAPH_ROWS);
   *nnz_out = nnz;
   return HCI_OK;
 }
@@ -788,11 +817,13 @@ static hci_status rows_csr(hci_ctx* ctx, GraphArgs& A, DevBuf& rowptr, DevBuf& c
 static hci_status compute_diag(hci_ctx* ctx, int64_t nV) {
   Graph& G = ctx->graph;
   const int n = ctx->n;
+  prof_tic(ctx, HCI_PH_HDIAG);
   HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
   HCI_LAUNCH(k_diag, grid_for(nV, 128), 128, (size_t)2 * n * n * 8, ctx->st)(
       n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, bp<ulonglong2>(G.keys), nV, bp<double>(G.diag));
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_HDIAG);
   return HCI_OK;
 }
 
@@ -864,6 +895,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   int64_t nnzN = 0;
   HCI_TRY(rows_csr(ctx, A, S.rpN, S.colN, S.valN, S.cnt, &nnzN));
   // transposed entries for the old rows
+  prof_tic(ctx, HCI_PH_GRAPH_MERGE);
   HCI_TRY(ensure_buf(ctx, S.hist, (size_t)(nV + 1) * 8));
   HCI_CUDA(ctx, cudaMemsetAsync(S.hist.p, 0, (size_t)(nV + 1) * 8, st));
   const int gw = grid_for(nnew * 32, 256);
@@ -907,6 +939,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
                                                bp<int32_t>(S.colN), bp<double>(S.valN), bp<int64_t>(G.rowptr),
                                                bp<int32_t>(G.col), bp<double>(G.val));
   HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_GRAPH_MERGE);
   HCI_TRY(compute_diag(ctx, nV));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
@@ -941,8 +974,12 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
   ctx->st_counts[HCI_ST_SIGMA_CALLS] += nvec;
   ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;
   ctx->st_counts[HCI_ST_SIGMA_NNZ] += G.nnz * nvec;
-  HCI_LAUNCH(k_sigma, grid_for(G.nV * 32, 256, 152 * 16), 256, 0, ctx->st)(
-      bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag), G.nV, c, sigma, nvec);
+  if (nvec == 1)
+    HCI_LAUNCH(k_sigma1, 152 * 6, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val),
+                                                   bp<double>(G.diag), G.nV, c, sigma, 1);
+  else
+    HCI_LAUNCH(k_sigma, grid_for(G.nV * 32, 256, 152 * 16), 256, 0, ctx->st)(
+        bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag), G.nV, c, sigma, nvec);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_SIGMA);
   return HCI_OK;

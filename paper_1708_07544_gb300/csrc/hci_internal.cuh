@@ -30,6 +30,7 @@ struct Graph {
   int64_t nV = 0;
   uint64_t hash = 0;
   int64_t nnz = 0;           // off-diagonal entries (both orientations stored)
+  int64_t nua = 0, nub = 0;  // distinct alpha / beta strings of the space
   DevBuf rowptr;             // int64 [nV+1]
   DevBuf col;                // int32 [nnz]
   DevBuf val;                // double [nnz]
@@ -45,6 +46,8 @@ struct Lists {
   DevBuf opp_mag, opp_tgt;           // [n*n][len_opp] double / uint16 (r | s<<8)
   DevBuf same_mag, same_tgt;         // [npair_same][len_same]
   DevBuf single_bound;               // [n*n] upper bound of |H| for single p->r
+  DevBuf list_max;                   // [n*n + npair_same] first (largest) magnitude of each list
+  DevBuf f_ref;                      // [2][n][n] single-excitation rows of the aufbau determinant
   double max_opp = 0, max_same = 0, max_single = 0;
 };
 
@@ -73,7 +76,7 @@ struct hci_ctx {
   Lists lists;
   Graph graph;
   // scratch
-  DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist;
+  DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items;
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb;
   IncScratch inc;

@@ -101,36 +101,77 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
   }
 }
 
-// M[s*n+p][t*n+q] += sum_i c_i^2 n_sp n_tq  (block-private in shared memory)
-__global__ void k_occ_corr(int n, const ulonglong2* __restrict__ V, int64_t nV, const double* __restrict__ c,
-                           double* __restrict__ M) {
+// M[s*n+p][t*n+q] = sum_i c_i^2 n_sp(i) n_tq(i), folded over the string
+// groups of the cached graph.  One warp per alpha group g with weight
+// W_g = sum_{i in g} c_i^2: the alpha-alpha block gets W_g for every pair of
+// orbitals occupied in alpha_g, the alpha-beta block gets v_g[q] =
+// sum_{i in g} c_i^2 n_q(beta_i) for every occupied p of alpha_g.  The
+// beta-beta block is folded over the beta groups the same way.  Block
+// partials live in shared memory and are added to M once per block.
+__global__ void k_occ_groups(int n, const ulonglong2* __restrict__ V, const double* __restrict__ c,
+                             const int64_t* __restrict__ ga, int64_t nua, const ulonglong2* __restrict__ bk,
+                             const int32_t* __restrict__ permb, const int64_t* __restrict__ gb, int64_t nub,
+                             double* __restrict__ M) {
   extern __shared__ double sm[];
   const int m = 2 * n;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) sm[t] = 0.0;
+  double* Ms = sm;                          // m*m
+  double* vq = sm + m * m;                  // [warps][64]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* v = vq + wid * HCI_MAXORB;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ms[t] = 0.0;
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nV; i += (int64_t)gridDim.x * blockDim.x) {
-    const double w = c[i] * c[i];
-    if (w == 0.0) continue;
-    const ulonglong2 k = V[i];
-    for (int s = 0; s < 2; ++s) {
-      uint64_t x = s == 0 ? k.x : k.y;
-      while (x) {
-        const int p = __ffsll((long long)x) - 1;
-        x &= x - 1;
-        for (int t = 0; t < 2; ++t) {
-          uint64_t y = t == 0 ? k.x : k.y;
-          while (y) {
-            const int q = __ffsll((long long)y) - 1;
-            y &= y - 1;
-            atomicAdd(&sm[(s * n + p) * m + t * n + q], w);
-          }
+  const int64_t gw = (int64_t)blockIdx.x * nw + wid, nwarps = (int64_t)gridDim.x * nw;
+  for (int64_t g = gw; g < nua; g += nwarps) {
+    // v[q] = sum_{i in g} c_i^2 n_q(beta_i): lane q % 32 keeps v[q] in a
+    // register, each 32-member chunk is reduced across the warp per orbital
+    double v0 = 0.0, v1 = 0.0, W = 0.0;
+    const int64_t b = ga[g], e = ga[g + 1];
+    for (int64_t i0 = b; i0 < e; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const double w = i < e ? c[i] * c[i] : 0.0;
+      const uint64_t y = i < e ? V[i].y : 0ull;
+      W += w;
+      for (int q = 0; q < n; ++q) {
+        double t = ((y >> q) & 1ull) ? w : 0.0;
+        if (__any_sync(0xffffffffu, t != 0.0)) {
+          for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == (q & 31)) { if (q < 32) v0 += t; else v1 += t; }
         }
       }
+    }
+    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+    v[lane] = v0;
+    v[lane + 32] = v1;
+    __syncwarp();
+    const uint64_t a = V[b].x;
+    for (int t = lane; t < n * n; t += 32) {
+      const int p = t / n, q = t % n;
+      if (!((a >> p) & 1ull)) continue;
+      if ((a >> q) & 1ull) atomicAdd(&Ms[p * m + q], W);
+      if (v[q] != 0.0) {
+        atomicAdd(&Ms[p * m + n + q], v[q]);
+        atomicAdd(&Ms[(n + q) * m + p], v[q]);
+      }
+    }
+    __syncwarp();
+  }
+  for (int64_t g = gw; g < nub; g += nwarps) {
+    double W = 0.0;
+    const int64_t b = gb[g], e = gb[g + 1];
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const double cv = c[permb[k]];
+      W += cv * cv;
+    }
+    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+    const uint64_t bb = bk[b].x;
+    for (int t = lane; t < n * n; t += 32) {
+      const int p = t / n, q = t % n;
+      if (((bb >> p) & 1ull) && ((bb >> q) & 1ull)) atomicAdd(&Ms[(n + p) * m + n + q], W);
     }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < m * m; t += blockDim.x)
-    if (sm[t] != 0.0) atomicAdd(&M[t], sm[t]);
+    if (Ms[t] != 0.0) atomicAdd(&M[t], Ms[t]);
 }
 
 // diagonal contributions from M
@@ -169,11 +210,16 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   HCI_TRY(ensure_buf(ctx, ctx->s_misc, (size_t)4 * n2 * 8 + 64));
   double* M = bp<double>(ctx->s_misc);
   HCI_CUDA(ctx, cudaMemsetAsync(M, 0, 4 * n2 * 8, st));
+  prof_tic(ctx, HCI_PH_RDM_DIAG);
   const ulonglong2* V = bp<ulonglong2>(ctx->graph.keys);
-  const size_t smem = (size_t)4 * n2 * 8;
-  HCI_CUDA(ctx, cudaFuncSetAttribute(k_occ_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 64 * 64 * 8));
-  HCI_LAUNCH(k_occ_corr, grid_for(nV, 256, 152 * 2), 256, smem, st)(n, V, nV, c, M);
+  const size_t smem = (size_t)4 * n2 * 8 + 8 * HCI_MAXORB * 8;
+  HCI_CUDA(ctx, cudaFuncSetAttribute(k_occ_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     4 * 64 * 64 * 8 + 8 * HCI_MAXORB * 8));
+  HCI_LAUNCH(k_occ_groups, 152, 256, smem, st)(n, V, c, bp<int64_t>(ctx->g_ga), ctx->graph.nua,
+                                               bp<ulonglong2>(ctx->g_bkeys), bp<int32_t>(ctx->g_permb),
+                                               bp<int64_t>(ctx->g_gb), ctx->graph.nub, M);
   HCI_LAUNCH(k_diag_rdm, grid_for((int64_t)n2, 256), 256, 0, st)(n, M, rdm1, rdm2);
+  prof_toc(ctx, HCI_PH_RDM_DIAG);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 56);
   HCI_CUDA(ctx, cudaMemsetAsync(queue, 0, 8, st));

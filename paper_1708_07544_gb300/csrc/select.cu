@@ -7,6 +7,7 @@
 namespace {
 
 constexpr int SEL_WARPS = 8;          // warps per CTA in the walk kernels
+constexpr int WALK_CHUNK = 256;       // list entries per walk work item
 
 struct WalkArgs {
   int n, na, nb;
@@ -22,6 +23,7 @@ struct WalkArgs {
   const uint16_t* same_tgt;
   int Ls;
   double max_dbl;        // largest magnitude in any list
+  const double* list_max; // [n*n] opposite-spin then [n(n-1)/2] same-spin list maxima
   const double* h;
   const double* jk_same;
   const double* j_opp;
@@ -30,6 +32,12 @@ struct WalkArgs {
   ulonglong2* out;
   int64_t cap;
   unsigned long long* counter;     // [0] candidates, [1] next det (work queue)
+  unsigned long long* walkstat;    // [0] list entries walked, [1] exact singles
+  int4* items;                     // walk work items {det, code, start, end}
+  int64_t item_cap;
+  unsigned long long* nitems;
+  const double* f_ref;             // [2][n][n] single-excitation rows of the aufbau determinant
+  uint64_t ref_a, ref_b;
 };
 
 __device__ __forceinline__ void tri_decode_dev(int t, int& lo, int& hi) {
@@ -79,16 +87,35 @@ __device__ __forceinline__ int prefix_len(const double* __restrict__ mag, int le
   return lo;
 }
 
-// Doubles: one warp per determinant (dynamic queue).  For every occupied
-// pair the list prefix with |v||c_i| > eps1 is walked by the whole warp and
-// every target whose orbitals are empty is emitted.
-__global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_doubles(WalkArgs A) {
+// Doubles, planning pass: one warp per determinant (dynamic queue).  For
+// every occupied pair the length L of the list prefix with |v||c_i| > eps1
+// is found by binary search, and the prefix is cut into work items of at
+// most WALK_CHUNK entries, so that a determinant with a large coefficient
+// (whose prefixes cover most of the lists) is spread over many warps.
+__global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_plan(WalkArgs A) {
+  // shared: list maxima (n*n + n(n-1)/2 doubles), then the triangular
+  // decode table t -> (lo, hi) of occupied-pair indices (bytes)
+  extern __shared__ double s_dyn[];
   __shared__ int s_occ[SEL_WARPS][2][HCI_MAXORB];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nmax = A.n * A.n + A.n * (A.n - 1) / 2;
+  double* s_max = s_dyn;
+  unsigned char* s_tlo = reinterpret_cast<unsigned char*>(s_dyn + nmax);
+  const int ntri = HCI_MAXORB * (HCI_MAXORB - 1) / 2;
+  unsigned char* s_thi = s_tlo + ntri;
+  for (int t = threadIdx.x; t < nmax; t += blockDim.x) s_max[t] = A.list_max[t];
+  for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+    int lo, hi;
+    tri_decode_dev(t, lo, hi);
+    s_tlo[t] = (unsigned char)lo;
+    s_thi[t] = (unsigned char)hi;
+  }
+  __syncthreads();
   int* occA = s_occ[w][0];
   int* occB = s_occ[w][1];
   const int Paa = A.na * (A.na - 1) / 2, Pbb = A.nb * (A.nb - 1) / 2, Pab = A.na * A.nb;
   const int P = Paa + Pbb + Pab;
+  const int nn = A.n * A.n;
   while (true) {
     unsigned long long i = 0;
     if (lane == 0) i = atomicAdd(&A.counter[1], 1ull);
@@ -102,71 +129,126 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_doubles(WalkArgs A) {
     for (int base = 0; base < P; base += 32) {
       int t = base + lane;
       int kind = -1, p = 0, q = 0, L = 0;
-      const double* mag = nullptr;
       int listid = 0;
       if (t < P) {
         int len;
+        double first;
+        const double* mag;
         if (t < Paa) {
-          int lo, hi;
-          tri_decode_dev(t, lo, hi);
-          p = occA[lo]; q = occA[hi]; kind = 0;
+          p = occA[s_tlo[t]]; q = occA[s_thi[t]]; kind = 0;
           listid = q * (q - 1) / 2 + p;
+          first = s_max[nn + listid];
           mag = A.same_mag + (int64_t)listid * A.Ls; len = A.Ls;
         } else if (t < Paa + Pbb) {
-          int lo, hi;
-          tri_decode_dev(t - Paa, lo, hi);
-          p = occB[lo]; q = occB[hi]; kind = 1;
+          p = occB[s_tlo[t - Paa]]; q = occB[s_thi[t - Paa]]; kind = 1;
           listid = q * (q - 1) / 2 + p;
+          first = s_max[nn + listid];
           mag = A.same_mag + (int64_t)listid * A.Ls; len = A.Ls;
         } else {
           int u = t - Paa - Pbb;
           p = occA[u / A.nb]; q = occB[u % A.nb]; kind = 2;
           listid = p * A.n + q;
+          first = s_max[listid];
           mag = A.opp_mag + (int64_t)listid * A.Lo; len = A.Lo;
         }
         if (A.accept_all) L = len;
-        else if (mag[0] * absc > A.eps1) L = prefix_len(mag, len, absc, A.eps1);
+        else if (first * absc > A.eps1) L = prefix_len(mag, len, absc, A.eps1);
       }
-      unsigned act = __ballot_sync(0xffffffffu, L > 0);
-      while (act) {
-        int src = __ffs(act) - 1;
-        act &= act - 1;
-        int sk = __shfl_sync(0xffffffffu, kind, src);
-        int sl = __shfl_sync(0xffffffffu, listid, src);
-        int sp = __shfl_sync(0xffffffffu, p, src);
-        int sq = __shfl_sync(0xffffffffu, q, src);
-        int sL = __shfl_sync(0xffffffffu, L, src);
-        const uint16_t* tg = sk == 2 ? A.opp_tgt + (int64_t)sl * A.Lo : A.same_tgt + (int64_t)sl * A.Ls;
-        for (int k0 = 0; k0 < sL; k0 += 32) {
-          int e = k0 + lane;
-          bool emit = false;
-          ulonglong2 key = k;
-          if (e < sL) {
-            uint16_t tt = tg[e];
-            int r = tt & 0xff, s = tt >> 8;
-            if (sk == 0) {
-              if (!((k.x >> r) & 1ull) && !((k.x >> s) & 1ull)) {
-                emit = true;
-                key.x = k.x ^ (1ull << sp) ^ (1ull << sq) ^ (1ull << r) ^ (1ull << s);
-              }
-            } else if (sk == 1) {
-              if (!((k.y >> r) & 1ull) && !((k.y >> s) & 1ull)) {
-                emit = true;
-                key.y = k.y ^ (1ull << sp) ^ (1ull << sq) ^ (1ull << r) ^ (1ull << s);
-              }
-            } else {
-              if (!((k.x >> r) & 1ull) && !((k.y >> s) & 1ull)) {
-                emit = true;
-                key.x = k.x ^ (1ull << sp) ^ (1ull << r);
-                key.y = k.y ^ (1ull << sq) ^ (1ull << s);
-              }
-            }
-          }
-          warp_emit(emit, key, A);
+      {
+        unsigned long long tot = (unsigned long long)L;
+        for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0 && tot) atomicAdd(&A.walkstat[0], tot);
+      }
+      // work items of at most WALK_CHUNK entries (det, kind|p|q|list, start, end)
+      int nit = L > 0 ? (L + WALK_CHUNK - 1) / WALK_CHUNK : 0;
+      int incl = nit;
+      for (int o = 1; o < 32; o <<= 1) {
+        int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t2;
+      }
+      const int tot_it = __shfl_sync(0xffffffffu, incl, 31);
+      if (tot_it > 0) {
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(A.nitems, (unsigned long long)tot_it);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const int code = kind | (p << 2) | (q << 8) | (listid << 14);
+        for (int j = 0; j < nit; ++j) {
+          const unsigned long long idx = base + (incl - nit) + j;
+          if ((int64_t)idx < A.item_cap)
+            A.items[idx] = make_int4((int)i, code, j * WALK_CHUNK, min(L, (j + 1) * WALK_CHUNK));
         }
       }
     }
   }
+}
+
+// Walk the planned list ranges: one warp per work item; every target whose
+// orbitals are empty in the source determinant is emitted.
+__global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_exec(WalkArgs A, int64_t nitems) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = warp; it < nitems; it += nwarps) {
+    const int4 w = A.items[it];
+    const ulonglong2 k = A.keys[w.x];
+    const int sk = w.y & 3, sp = (w.y >> 2) & 63, sq = (w.y >> 8) & 63, sl = w.y >> 14;
+    const uint16_t* tg = sk == 2 ? A.opp_tgt + (int64_t)sl * A.Lo : A.same_tgt + (int64_t)sl * A.Ls;
+    for (int k0 = w.z; k0 < w.w; k0 += 32) {
+      const int e = k0 + lane;
+      bool emit = false;
+      ulonglong2 key = k;
+      if (e < w.w) {
+        const uint16_t tt = tg[e];
+        const int r = tt & 0xff, s2 = tt >> 8;
+        if (sk == 0) {
+          if (!((k.x >> r) & 1ull) && !((k.x >> s2) & 1ull)) {
+            emit = true;
+            key.x = k.x ^ (1ull << sp) ^ (1ull << sq) ^ (1ull << r) ^ (1ull << s2);
+          }
+        } else if (sk == 1) {
+          if (!((k.y >> r) & 1ull) && !((k.y >> s2) & 1ull)) {
+            emit = true;
+            key.y = k.y ^ (1ull << sp) ^ (1ull << sq) ^ (1ull << r) ^ (1ull << s2);
+          }
+        } else {
+          if (!((k.x >> r) & 1ull) && !((k.y >> s2) & 1ull)) {
+            emit = true;
+            key.x = k.x ^ (1ull << sp) ^ (1ull << r);
+            key.y = k.y ^ (1ull << sq) ^ (1ull << s2);
+          }
+        }
+      }
+      warp_emit(emit, key, A);
+    }
+  }
+}
+
+// Bound on |H_ai| of the single p->r (spin S) of a determinant D from the
+// aufbau reference R: H = F_R + sum over the orbitals where D and R differ of
+// +-(pr|kk)-(pk|kr) (same spin) or +-(pr|kk) (other spin), so |H| is at most
+// |F_R| plus the absolute values of those few terms; the margin covers the
+// rounding of both sums (at most 2n+1 terms bounded by the loose bound B).
+__device__ __forceinline__ double single_tight(const WalkArgs& A, int spin, int p, int r, uint64_t s, uint64_t o,
+                                               double B) {
+  const int n = A.n;
+  const uint64_t ds = s ^ (spin == 0 ? A.ref_a : A.ref_b);
+  const uint64_t dot = o ^ (spin == 0 ? A.ref_b : A.ref_a);
+  const double* js = A.jk_same + ((int64_t)p * n + r) * n;
+  const double* jo = A.j_opp + ((int64_t)p * n + r) * n;
+  double t = fabs(A.f_ref[((int64_t)spin * n + p) * n + r]);
+  uint64_t x = ds;
+  while (x) {
+    const int k = __ffsll((long long)x) - 1;
+    x &= x - 1;
+    t += fabs(js[k]);
+  }
+  x = dot;
+  while (x) {
+    const int k = __ffsll((long long)x) - 1;
+    x &= x - 1;
+    t += fabs(jo[k]);
+  }
+  return (t + 1e-13 * B) * (1.0 + 1e-12);
 }
 
 // Singles: one warp per determinant; each lane screens (p->r) with the
@@ -174,8 +256,12 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_doubles(WalkArgs A) {
 // summation order as the textbook rule (k ascending, same spin then
 // opposite spin per k).
 __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ double s_bound[];          // n*n single-excitation bounds
+  __shared__ int s_ov[SEL_WARPS][2][2][HCI_MAXORB];   // [warp][spin][occ/vir][]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = A.n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) s_bound[t] = A.single_bound[t];
+  __syncthreads();
   const int Pa = A.na * (n - A.na), Pb = A.nb * (n - A.nb);
   const int P = Pa + Pb;
   while (true) {
@@ -186,6 +272,23 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
     const double absc = fabs(A.c[i]);
     if (!A.accept_all && !(A.max_single * absc > A.eps1)) continue;
     const ulonglong2 k = A.keys[i];
+    for (int sp = 0; sp < 2; ++sp) {
+      const uint64_t x = sp == 0 ? k.x : k.y;
+      int bo = 0, bv = 0;
+      for (int p0 = 0; p0 < n; p0 += 32) {
+        const int pp = p0 + lane;
+        const bool in = pp < n;
+        const bool o = in && ((x >> pp) & 1ull);
+        const unsigned mo = __ballot_sync(0xffffffffu, o);
+        const unsigned mv = __ballot_sync(0xffffffffu, in && !o);
+        const unsigned lt = (1u << lane) - 1u;
+        if (o) s_ov[w][sp][0][bo + __popc(mo & lt)] = pp;
+        if (in && !o) s_ov[w][sp][1][bv + __popc(mv & lt)] = pp;
+        bo += __popc(mo);
+        bv += __popc(mv);
+      }
+    }
+    __syncwarp();
     for (int base = 0; base < P; base += 32) {
       int t = base + lane;
       bool emit = false;
@@ -197,16 +300,11 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
         uint64_t o = spin == 0 ? k.y : k.x;
         int nocc = spin == 0 ? A.na : A.nb;
         int nvirt = n - nocc;
-        int oi = u / nvirt, vi = u % nvirt;
-        // oi-th occupied and vi-th empty orbital of s
-        int p = -1, r = -1, co = 0, cv = 0;
-        for (int x = 0; x < n; ++x) {
-          if ((s >> x) & 1ull) { if (co == oi) p = x; ++co; }
-          else { if (cv == vi) r = x; ++cv; }
-        }
+        const int p = s_ov[w][spin][0][u / nvirt], r = s_ov[w][spin][1][u % nvirt];
         if (A.accept_all) {
           emit = true;
-        } else if (A.single_bound[p * n + r] * absc > A.eps1) {
+        } else if (s_bound[p * n + r] * absc > A.eps1 && single_tight(A, spin, p, r, s, o, s_bound[p * n + r]) * absc > A.eps1) {
+          atomicAdd(&A.walkstat[1], 1ull);
           double v = A.h[p * n + r];
           const double* js = A.jk_same + ((int64_t)p * n + r) * n;
           const double* jo = A.j_opp + ((int64_t)p * n + r) * n;
@@ -287,18 +385,46 @@ __global__ void k_merge_new(const ulonglong2* __restrict__ V, int64_t nV, const 
 }  // namespace
 
 static hci_status run_walk(hci_ctx* ctx, WalkArgs& A, int64_t* total) {
+  HCI_TRY(ensure_buf(ctx, ctx->s_walkstat, 64));
+  A.walkstat = bp<unsigned long long>(ctx->s_walkstat);
+  A.nitems = A.walkstat + 2;
+  HCI_CUDA(ctx, cudaMemsetAsync(A.walkstat, 0, 16, ctx->st));
   prof_tic(ctx, HCI_PH_WALK);
   HCI_CUDA(ctx, cudaMemsetAsync(A.counter, 0, 16, ctx->st));
   const int grid = 152 * 8;
-  HCI_LAUNCH(k_walk_doubles, grid, SEL_WARPS * 32, 0, ctx->st)(A);
-  HCI_CUDA(ctx, cudaGetLastError());
-  HCI_CUDA(ctx, cudaMemsetAsync(A.counter + 1, 0, 8, ctx->st));
-  HCI_LAUNCH(k_singles, grid, SEL_WARPS * 32, 0, ctx->st)(A);
+  const size_t smw = (size_t)(A.n * A.n + A.n * (A.n - 1) / 2) * 8 + HCI_MAXORB * (HCI_MAXORB - 1);
+  HCI_CUDA(ctx, cudaFuncSetAttribute(k_walk_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    HCI_TRY(ensure_buf(ctx, ctx->s_items, (size_t)(ctx->s_items.bytes > 0 ? ctx->s_items.bytes : (1 << 20) * 16)));
+    A.items = bp<int4>(ctx->s_items);
+    A.item_cap = (int64_t)(ctx->s_items.bytes / 16);
+    HCI_CUDA(ctx, cudaMemsetAsync(A.counter + 1, 0, 8, ctx->st));
+    HCI_CUDA(ctx, cudaMemsetAsync(A.nitems, 0, 8, ctx->st));
+    HCI_LAUNCH(k_walk_plan, grid, SEL_WARPS * 32, smw, ctx->st)(A);
+    HCI_CUDA(ctx, cudaGetLastError());
+    unsigned long long ni = 0;
+    HCI_CUDA(ctx, cudaMemcpyAsync(&ni, A.nitems, 8, cudaMemcpyDeviceToHost, ctx->st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+    if ((int64_t)ni <= A.item_cap) {
+      if (ni > 0) HCI_LAUNCH(k_walk_exec, grid, SEL_WARPS * 32, 0, ctx->st)(A, (int64_t)ni);
+      break;
+    }
+    HCI_TRY(ensure_buf(ctx, ctx->s_items, (size_t)(ni + ni / 8 + 1024) * 16));
+  }
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_WALK);
-  unsigned long long cnt = 0;
+  prof_tic(ctx, HCI_PH_SINGLES);
+  HCI_CUDA(ctx, cudaMemsetAsync(A.counter + 1, 0, 8, ctx->st));
+  HCI_CUDA(ctx, cudaFuncSetAttribute(k_singles, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  HCI_LAUNCH(k_singles, grid, SEL_WARPS * 32, (size_t)A.n * A.n * 8, ctx->st)(A);
+  HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_SINGLES);
+  unsigned long long cnt = 0, ws[2] = {0, 0};
   HCI_CUDA(ctx, cudaMemcpyAsync(&cnt, A.counter, 8, cudaMemcpyDeviceToHost, ctx->st));
+  HCI_CUDA(ctx, cudaMemcpyAsync(ws, A.walkstat, 16, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  ctx->st_counts[HCI_ST_WALK_ENTRIES] += (int64_t)ws[0];
+  ctx->st_counts[HCI_ST_SINGLES_EXACT] += (int64_t)ws[1];
   *total = (int64_t)cnt;
   return HCI_OK;
 }
@@ -326,6 +452,10 @@ extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys
   A.max_dbl = L.max_opp > L.max_same ? L.max_opp : L.max_same;
   A.h = bp<double>(ctx->h); A.jk_same = bp<double>(ctx->jk_same); A.j_opp = bp<double>(ctx->j_opp);
   A.single_bound = bp<double>(L.single_bound); A.max_single = L.max_single;
+  A.list_max = bp<double>(L.list_max);
+  A.f_ref = bp<double>(L.f_ref);
+  A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
+  A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   A.counter = bp<unsigned long long>(ctx->s_counter);
   // candidate buffer: grow and rerun when the first guess overflows
