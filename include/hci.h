@@ -28,7 +28,10 @@
  * synchronise that stream before returning.  The context owns only its
  * internal workspaces (integral tables, heat-bath lists, the connection
  * graph of the last space, scratch), allocated with cudaMallocAsync on the
- * context stream and released by hci_destroy.  A context is not thread-safe.
+ * context stream and released by hci_destroy to the device's default memory
+ * pool, whose release threshold hci_create raises so that freed workspace
+ * stays mapped for the next context (cudaMemPoolTrimTo returns it to the
+ * system).  A context is not thread-safe.
  *
  * Errors: every call returns an hci_status.  On failure hci_last_error()
  * holds a one-line message.  HCI_ERR_CAPACITY reports, through the

@@ -215,6 +215,18 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
   if (!h || !eri) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_create: null integrals");
   hci_ctx* ctx = new (std::nothrow) hci_ctx();
   if (!ctx) return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_create: host allocation failed");
+  {
+    // Workspaces come from the device's default stream-ordered pool; keep
+    // freed memory in the pool (instead of unmapping it at every
+    // synchronisation) so that a solve per orbital iteration reuses it.
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
   ctx->n = norb;
   ctx->na = nalpha;
   ctx->nb = nbeta;
@@ -263,10 +275,12 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->g_permb, &ctx->g_bkeys, &ctx->g_bkeys2, &ctx->g_nbr_ptr, &ctx->g_nbr, &ctx->g_cnt,
                     &ctx->d_vb, &ctx->d_wb, &ctx->d_diag, &ctx->d_small, &ctx->d_part,
                     &ctx->g_bnbr_ptr, &ctx->g_bnbr, &ctx->g_costa, &ctx->g_costb, &ctx->s_walkstat,
+                    &ctx->g_htab, &ctx->g_hval,
                     &ctx->inc.pos_old, &ctx->inc.mark, &ctx->inc.flag, &ctx->inc.newrows, &ctx->inc.rpN,
                     &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.cnt, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T,
                     &ctx->inc.T2, &ctx->inc.tstart, &ctx->inc.len, &ctx->inc.keys_old, &ctx->inc.rp_old,
-                    &ctx->inc.col_old, &ctx->inc.val_old};
+                    &ctx->inc.col_old, &ctx->inc.val_old, &ctx->inc.len_old, &ctx->inc.cap_old,
+                    &ctx->inc.diag_old, &ctx->graph.rowstart, &ctx->graph.rowlen, &ctx->graph.rowcap};
   for (DevBuf* b : bufs) free_buf(st, *b);
   prof_release(ctx);
   cudaStreamSynchronize(st);

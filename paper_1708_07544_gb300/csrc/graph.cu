@@ -89,10 +89,50 @@ __global__ void k_perm_b(const ulonglong2* __restrict__ bkeys, int64_t n, const 
   }
 }
 
-// single-excitation neighbours (within the distinct alpha strings) of each
-// distinct alpha string; count pass (out == nullptr) or fill pass
+// Open-addressing hash set of the distinct strings (value = group index),
+// linear probing; table size is a power of two >= 2 x entries, so probing
+// always ends at an empty slot.
+constexpr uint64_t HASH_EMPTY = ~0ull;
+
+__device__ __forceinline__ uint64_t hash_str(uint64_t x) {
+  x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33;
+  return x;
+}
+
+__global__ void k_hash_insert(const uint64_t* __restrict__ u, int64_t nu, unsigned long long* __restrict__ tab,
+                              int32_t* __restrict__ val, uint64_t mask) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nu; g += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = u[g];
+    uint64_t h = hash_str(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      const unsigned long long prev = atomicCAS(&tab[h], (unsigned long long)HASH_EMPTY, (unsigned long long)key);
+      if (prev == HASH_EMPTY || prev == key) {
+        val[h] = (int32_t)g;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+  }
+}
+
+__device__ __forceinline__ int32_t hash_find(const unsigned long long* __restrict__ tab, const int32_t* __restrict__ val,
+                                             uint64_t mask, uint64_t key) {
+  uint64_t h = hash_str(key) & mask;
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    const unsigned long long t = tab[h];
+    if (t == key) return val[h];
+    if (t == HASH_EMPTY) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// single-excitation neighbours (within the distinct strings) of each
+// distinct string; count pass (out == nullptr) or fill pass
 __global__ void k_alpha_nbrs(int n, const uint64_t* __restrict__ ua, int64_t nua, const int64_t* __restrict__ ptr,
-                             int64_t* __restrict__ cnt, int32_t* __restrict__ out) {
+                             int64_t* __restrict__ cnt, int32_t* __restrict__ out,
+                             const unsigned long long* __restrict__ tab, const int32_t* __restrict__ tval,
+                             uint64_t mask) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -104,17 +144,16 @@ __global__ void k_alpha_nbrs(int n, const uint64_t* __restrict__ ua, int64_t nua
     for (int b0 = 0; b0 < npairs; b0 += 32) {
       int t = b0 + lane;
       bool hit = false;
-      int64_t idx = -1;
+      int32_t idx = -1;
       if (t < npairs) {
         int p = t / n, r = t % n;
         if (((s >> p) & 1ull) && !((s >> r) & 1ull)) {
-          uint64_t x = s ^ (1ull << p) ^ (1ull << r);
-          int64_t pos = lower_bound_u(ua, nua, x);
-          if (pos < nua && ua[pos] == x) { hit = true; idx = pos; }
+          idx = hash_find(tab, tval, mask, s ^ (1ull << p) ^ (1ull << r));
+          hit = idx >= 0;
         }
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (out && hit) out[w + c + __popc(m & ((1u << lane) - 1u))] = (int32_t)idx;
+      if (out && hit) out[w + c + __popc(m & ((1u << lane) - 1u))] = idx;
       c += __popc(m);
     }
     if (!out && lane == 0) cnt[g] = c;
@@ -497,75 +536,119 @@ __global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restri
   }
 }
 
-__global__ void k_lengths(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ rp_old, int64_t nold,
-                          const int32_t* __restrict__ newrows, const int64_t* __restrict__ rpN, int64_t nnew,
-                          const int64_t* __restrict__ hist, int64_t* __restrict__ len) {
+// ---------------------------------------------------------------------------
+// row pool: each row owns [rowstart, rowstart + rowcap) of the col/val
+// pools; rowlen <= rowcap entries are live.  Slack lets later updates append
+// in place; rows that outgrow it move to the end of the pool.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t slack_cap(int64_t len) { return len + len / 8 + 8; }
+
+__global__ void k_caps(const int64_t* __restrict__ len, int64_t n, int64_t* __restrict__ cap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    cap[i] = slack_cap(len[i]);
+}
+
+// Plan of V' = V + N: new length of every row, its capacity, whether it stays
+// (start2 = old start) or needs a new range of `need` entries (start2 = -1).
+__global__ void k_plan_rows(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ start_old,
+                            const int64_t* __restrict__ len_old, const int64_t* __restrict__ cap_old, int64_t nold,
+                            const int32_t* __restrict__ newrows, const int64_t* __restrict__ rpN, int64_t nnew,
+                            const int64_t* __restrict__ hist, int repack, int64_t* __restrict__ start2,
+                            int64_t* __restrict__ len2, int64_t* __restrict__ cap2, int64_t* __restrict__ need) {
   const int64_t tot = nold + nnew;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     if (t < nold) {
       const int64_t p = pos_old[t];
-      len[p] = (rp_old[t + 1] - rp_old[t]) + hist[p];
+      const int64_t L = len_old[t] + hist[p];
+      len2[p] = L;
+      if (!repack && L <= cap_old[t]) {
+        start2[p] = start_old[t];
+        cap2[p] = cap_old[t];
+        need[p] = 0;
+      } else {
+        start2[p] = -1;
+        cap2[p] = slack_cap(L);
+        need[p] = cap2[p];
+      }
     } else {
       const int64_t q = t - nold;
-      len[newrows[q]] = rpN[q + 1] - rpN[q];
+      const int64_t p = newrows[q];
+      const int64_t L = rpN[q + 1] - rpN[q];
+      len2[p] = L;
+      start2[p] = -1;
+      cap2[p] = slack_cap(L);
+      need[p] = cap2[p];
     }
   }
 }
 
-// old rows: remapped old entries, then the appended T entries
-__global__ void k_copy_old_rows(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ rp_old,
-                                const int32_t* __restrict__ col_old, const double* __restrict__ val_old, int64_t nold,
-                                const int64_t* __restrict__ rp_new, int32_t* __restrict__ col_new,
-                                double* __restrict__ val_new, const ulonglong2* __restrict__ T,
-                                const int64_t* __restrict__ tstart, const int64_t* __restrict__ hist,
-                                const int64_t* __restrict__ rpN, int64_t nnew, const int32_t* __restrict__ newrows,
-                                const double* __restrict__ valN) {
+__global__ void k_assign_starts(int64_t* __restrict__ start2, const int64_t* __restrict__ rel, int64_t n, int64_t base) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (start2[i] < 0) start2[i] = base + rel[i];
+}
+
+// old rows: columns remapped to V' positions (in place when the row stays),
+// then the appended transposes of the new rows' entries
+__global__ void k_move_old_rows(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ start_old,
+                                const int64_t* __restrict__ len_old, int64_t nold, const int32_t* col_src,
+                                const double* val_src, const int64_t* __restrict__ start2, int32_t* col_dst,
+                                double* val_dst, const ulonglong2* __restrict__ T, const int64_t* __restrict__ tstart,
+                                const int64_t* __restrict__ hist, const int64_t* __restrict__ rpN, int64_t nnew,
+                                const int32_t* __restrict__ newrows, const double* __restrict__ valN) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < nold; i += nwarps) {
     const int64_t p = pos_old[i];
-    const int64_t dst = rp_new[p];
-    const int64_t b = rp_old[i], len = rp_old[i + 1] - b;
+    const int64_t src = start_old[i], dst = start2[p], len = len_old[i];
+    const bool moved = (dst != src) || (col_dst != col_src);
     for (int64_t k = lane; k < len; k += 32) {
-      col_new[dst + k] = (int32_t)pos_old[col_old[b + k]];
-      val_new[dst + k] = val_old[b + k];
+      const int32_t j = col_src[src + k];
+      col_dst[dst + k] = (int32_t)pos_old[j];
+      if (moved) val_dst[dst + k] = val_src[src + k];
     }
     const int64_t t0 = tstart[p], tn = hist[p];
     for (int64_t k = lane; k < tn; k += 32) {
       const int64_t e = (int64_t)T[t0 + k].y;
-      // new row owning entry e
       int64_t lo = 0, hi = nnew;
       while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
         if (rpN[mid] <= e) lo = mid;
         else hi = mid;
       }
-      col_new[dst + len + k] = newrows[lo];
-      val_new[dst + len + k] = valN[e];
+      col_dst[dst + len + k] = newrows[lo];
+      val_dst[dst + len + k] = valN[e];
     }
   }
 }
 
-__global__ void k_copy_new_rows(const int32_t* __restrict__ newrows, int64_t nnew, const int64_t* __restrict__ rpN,
-                                const int32_t* __restrict__ colN, const double* __restrict__ valN,
-                                const int64_t* __restrict__ rp_new, int32_t* __restrict__ col_new,
-                                double* __restrict__ val_new) {
+__global__ void k_place_new_rows(const int32_t* __restrict__ newrows, int64_t nnew, const int64_t* __restrict__ rpN,
+                                 const int32_t* __restrict__ colN, const double* __restrict__ valN,
+                                 const int64_t* __restrict__ start2, int32_t* __restrict__ col_dst,
+                                 double* __restrict__ val_dst) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = warp; q < nnew; q += nwarps) {
-    const int64_t dst = rp_new[newrows[q]];
+    const int64_t dst = start2[newrows[q]];
     const int64_t b = rpN[q], len = rpN[q + 1] - b;
     for (int64_t k = lane; k < len; k += 32) {
-      col_new[dst + k] = colN[b + k];
-      val_new[dst + k] = valN[b + k];
+      col_dst[dst + k] = colN[b + k];
+      val_dst[dst + k] = valN[b + k];
     }
   }
 }
+
+__global__ void k_move_diag(const int64_t* __restrict__ pos_old, const double* __restrict__ dold, int64_t nold,
+                            double* __restrict__ dnew) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nold; i += (int64_t)gridDim.x * blockDim.x)
+    dnew[pos_old[i]] = dold[i];
+}
+
 // diagonal <D|H|D> (includes e_core)
 __global__ void k_diag(int n, const double* __restrict__ h, const double* __restrict__ eri, double ecore,
-                       const ulonglong2* __restrict__ V, int64_t nV, double* __restrict__ out) {
+                       const ulonglong2* __restrict__ V, int64_t nV, double* __restrict__ out,
+                       const int32_t* __restrict__ rowlist) {
   extern __shared__ double sm[];
   double* J = sm;            // (kk|ll)
   double* K = sm + n * n;    // (kl|lk)
@@ -575,7 +658,8 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
     K[t] = eri[(((int64_t)k * n + l) * n + l) * n + k];
   }
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nV; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nV; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rowlist ? (int64_t)rowlist[t] : t;
     ulonglong2 key = V[i];
     double e1 = 0.0, e2 = 0.0;
     for (int s = 0; s < 2; ++s) {
@@ -612,7 +696,8 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
 // the connections and keeps four independent (col, val, c[col]) chains per
 // lane in flight; the CSR stream is read with evict-first hints so that c
 // stays in L2.
-__global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ rowptr,
+                                                  const int64_t* __restrict__ rowstart, const int32_t* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ diag,
                                                int64_t nV, const double* __restrict__ c, double* __restrict__ sigma,
                                                int nvec_unused) {
@@ -633,7 +718,7 @@ __global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ r
       r1 = warp == nwarps - 1 ? nV : lo;
     }
     for (int64_t i = r0; i < r1; ++i) {
-      const int64_t b = rowptr[i], e = rowptr[i + 1];
+      const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       int64_t k = b + lane;
       for (; k + 96 < e; k += 128) {
@@ -655,7 +740,8 @@ __global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ r
 }
 
 // several vectors at once (one pass over the connections per 4 vectors)
-__global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowptr,
+                                               const int64_t* __restrict__ rowstart, const int32_t* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ diag,
                                                int64_t nV, const double* __restrict__ c, double* __restrict__ sigma,
                                                int nvec) {
@@ -663,7 +749,7 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < nV; i += nwarps) {
-    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
     for (int v0 = 0; v0 < nvec; v0 += 4) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       const int nv = nvec - v0 < 4 ? nvec - v0 : 4;
@@ -746,11 +832,20 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   // lookups on the alpha side generate beta singles and vice versa
   const int Lside[2] = {ctx->nb * (n - ctx->nb), ctx->na * (n - ctx->na)};
   for (int s = 0; s < 2; ++s) {
+    uint64_t tsize = 64;
+    while (tsize < (uint64_t)(2 * nu[s] + 2)) tsize <<= 1;
+    HCI_TRY(ensure_buf(ctx, ctx->g_htab, (size_t)tsize * 8));
+    HCI_TRY(ensure_buf(ctx, ctx->g_hval, (size_t)tsize * 4));
+    HCI_CUDA(ctx, cudaMemsetAsync(ctx->g_htab.p, 0xFF, (size_t)tsize * 8, ctx->st));
+    HCI_LAUNCH(k_hash_insert, grid_for(nu[s], 256), 256, 0, ctx->st)(uniq[s], nu[s], bp<unsigned long long>(ctx->g_htab),
+                                                                      bp<int32_t>(ctx->g_hval), tsize - 1);
     HCI_TRY(ensure_buf(ctx, ctx->g_cnt, (size_t)(nu[s] + 1) * 8));
     HCI_TRY(ensure_buf(ctx, *ptrs[s], (size_t)(nu[s] + 1) * 8));
     HCI_TRY(ensure_buf(ctx, *costs[s], (size_t)(nu[s] + 1) * 8));
     const int gw = grid_for(nu[s] * 32, 256);
-    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], nullptr, bp<int64_t>(ctx->g_cnt), nullptr);
+    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], nullptr, bp<int64_t>(ctx->g_cnt), nullptr,
+                                                   bp<unsigned long long>(ctx->g_htab), bp<int32_t>(ctx->g_hval),
+                                                   tsize - 1);
     HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->g_cnt), bp<int64_t>(*ptrs[s]), nu[s], dtot));
     HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(*ptrs[s]), nu[s], dtot);
     int64_t nn = 0;
@@ -758,7 +853,8 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
     HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
     HCI_TRY(ensure_buf(ctx, *lists[s], (size_t)(nn + 1) * 4));
     HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], bp<int64_t>(*ptrs[s]), nullptr,
-                                                   bp<int32_t>(*lists[s]));
+                                                   bp<int32_t>(*lists[s]), bp<unsigned long long>(ctx->g_htab),
+                                                   bp<int32_t>(ctx->g_hval), tsize - 1);
     HCI_LAUNCH(k_nbr_cost, gw, 256, 0, ctx->st)(bp<int64_t>(*ptrs[s]), bp<int32_t>(*lists[s]), gstart[s], nu[s],
                                                  Lside[s], bp<int64_t>(*costs[s]));
   }
@@ -782,46 +878,43 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   return HCI_OK;
 }
 
-// Count, scan and fill the rows listed in A (A.rowlist / A.nrows) into
-// rowptr (nrows+1), col, val buffers; returns their nnz.
-static hci_status rows_csr(hci_ctx* ctx, GraphArgs& A, DevBuf& rowptr, DevBuf& col, DevBuf& val, DevBuf& cnt,
-                           int64_t* nnz_out) {
-  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
-  const int64_t nr = A.nrows;
-  prof_tic(ctx, HCI_PH_GRAPH_ROWS);
-  HCI_TRY(ensure_buf(ctx, rowptr, (size_t)(nr + 1) * 8));
-  HCI_TRY(ensure_buf(ctx, cnt, (size_t)(nr + 1) * 8));
+// Count the entries of the rows listed in A (A.rowlist / A.nrows) into cnt.
+static hci_status rows_count(hci_ctx* ctx, GraphArgs& A, DevBuf& cnt) {
+  HCI_TRY(ensure_buf(ctx, cnt, (size_t)(A.nrows + 1) * 8));
   A.rowcnt = bp<int64_t>(cnt);
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr;
-  const int grows = 152 * 8;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<false>, grows, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_LAUNCH(k_rows<false>, 152 * 8, G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(cnt), bp<int64_t>(rowptr), nr, dtot));
-  HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(rowptr), nr, dtot);
-  int64_t nnz = 0;
-  HCI_CUDA(ctx, cudaMemcpyAsync(&nnz, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
-  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
-  HCI_TRY(ensure_buf(ctx, col, (size_t)(nnz + 1) * 4));
-  HCI_TRY(ensure_buf(ctx, val, (size_t)(nnz + 1) * 8));
   A.rowcnt = nullptr;
-  A.rowptr = bp<int64_t>(rowptr); A.col = bp<int32_t>(col); A.val = bp<double>(val);
-  HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<true>, grows, G_WARPS * 32, 0, ctx->st)(A);
-  HCI_CUDA(ctx, cudaGetLastError());
-  prof_toc(ctx, HCI_PH_GRAPH_ROWS);
-  *nnz_out = nnz;
   return HCI_OK;
 }
 
-static hci_status compute_diag(hci_ctx* ctx, int64_t nV) {
+// Fill the listed rows, row q starting at offs[q] of col/val.
+static hci_status rows_fill(hci_ctx* ctx, GraphArgs& A, const int64_t* offs, int32_t* col, double* val) {
+  A.rowptr = offs; A.col = col; A.val = val;
+  HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
+  HCI_LAUNCH(k_rows<true>, 152 * 8, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}
+
+static int64_t read_i64(hci_ctx* ctx, const int64_t* d, hci_status* st) {
+  int64_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, d, 8, cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  *st = e == cudaSuccess ? HCI_OK : hci_fail(ctx, HCI_ERR_CUDA, "graph: %s", cudaGetErrorString(e));
+  return v;
+}
+
+static hci_status compute_diag(hci_ctx* ctx, int64_t nrows, const int32_t* rowlist, double* out) {
   Graph& G = ctx->graph;
   const int n = ctx->n;
   prof_tic(ctx, HCI_PH_HDIAG);
-  HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
-  HCI_LAUNCH(k_diag, grid_for(nV, 128), 128, (size_t)2 * n * n * 8, ctx->st)(
-      n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, bp<ulonglong2>(G.keys), nV, bp<double>(G.diag));
+  if (nrows > 0)
+    HCI_LAUNCH(k_diag, grid_for(nrows, 128), 128, (size_t)2 * n * n * 8, ctx->st)(
+        n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, bp<ulonglong2>(G.keys), nrows, out, rowlist);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_HDIAG);
   return HCI_OK;
@@ -829,28 +922,55 @@ static hci_status compute_diag(hci_ctx* ctx, int64_t nV) {
 
 hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   Graph& G = ctx->graph;
+  IncScratch& S = ctx->inc;
   G.valid = false;
   if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 columns");
   prof_tic(ctx, HCI_PH_GRAPH);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
   HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
   HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
   GraphArgs A;
   HCI_TRY(build_space(ctx, nV, A));
-  int64_t nnz = 0;
-  HCI_TRY(rows_csr(ctx, A, G.rowptr, G.col, G.val, ctx->inc.cnt, &nnz));
-  HCI_TRY(compute_diag(ctx, nV));
+  prof_tic(ctx, HCI_PH_GRAPH_ROWS);
+  HCI_TRY(ensure_buf(ctx, G.rowlen, (size_t)(nV + 1) * 8));
+  HCI_TRY(rows_count(ctx, A, G.rowlen));
+  // capacities with slack, starts = their prefix sums, pool with headroom
+  HCI_TRY(ensure_buf(ctx, G.rowcap, (size_t)(nV + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, G.rowstart, (size_t)(nV + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
+  HCI_LAUNCH(k_caps, grid_for(nV, 256), 256, 0, ctx->st)(bp<int64_t>(G.rowlen), nV, bp<int64_t>(G.rowcap));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(G.rowcap), bp<int64_t>(G.rowstart), nV, dtot));
+  hci_status st = HCI_OK;
+  const int64_t used = read_i64(ctx, dtot, &st);
+  HCI_TRY(st);
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(G.rowlen), bp<int64_t>(G.rowptr), nV, dtot));
+  HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(G.rowptr), nV, dtot);
+  const int64_t nnz = read_i64(ctx, dtot, &st);
+  HCI_TRY(st);
+  const int64_t cap = used + used / 4 + 1024;
+  HCI_TRY(ensure_buf(ctx, G.col, (size_t)cap * 4));
+  HCI_TRY(ensure_buf(ctx, G.val, (size_t)cap * 8));
+  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val)));
+  prof_toc(ctx, HCI_PH_GRAPH_ROWS);
+  HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
+  HCI_TRY(compute_diag(ctx, nV, nullptr, bp<double>(G.diag)));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
   G.nV = nV;
   G.nnz = nnz;
+  G.pool_used = used;
+  G.pool_cap = (int64_t)(G.col.bytes / 4) < (int64_t)(G.val.bytes / 8) ? (int64_t)(G.col.bytes / 4)
+                                                                        : (int64_t)(G.val.bytes / 8);
+  (void)S;
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   G.valid = true;
   return HCI_OK;
 }
 
 // V' contains every determinant of the cached space: search only the rows of
-// the new determinants, append their transposes to the old rows, and merge.
+// the new determinants, append their transposes to the old rows (in place
+// where the row's slack allows), remap the old columns to V' positions.
 static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, bool* done) {
   Graph& G = ctx->graph;
   IncScratch& S = ctx->inc;
@@ -872,11 +992,13 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   if (miss) return HCI_OK;        // not an extension: full rebuild
   prof_tic(ctx, HCI_PH_GRAPH);
-  // the old CSR and keys move to the scratch side
+  hci_status hs = HCI_OK;
+  // the old row arrays, keys and diagonal move to the scratch side
   std::swap(G.keys, S.keys_old);
-  std::swap(G.rowptr, S.rp_old);
-  std::swap(G.col, S.col_old);
-  std::swap(G.val, S.val_old);
+  std::swap(G.rowstart, S.rp_old);
+  std::swap(G.rowlen, S.len_old);
+  std::swap(G.rowcap, S.cap_old);
+  std::swap(G.diag, S.diag_old);
   HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
   HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st));
   // new rows
@@ -892,9 +1014,18 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(build_space(ctx, nV, A));
   A.rowlist = bp<int32_t>(S.newrows);
   A.nrows = nnew;
-  int64_t nnzN = 0;
-  HCI_TRY(rows_csr(ctx, A, S.rpN, S.colN, S.valN, S.cnt, &nnzN));
-  // transposed entries for the old rows
+  prof_tic(ctx, HCI_PH_GRAPH_ROWS);
+  HCI_TRY(rows_count(ctx, A, S.cnt));
+  HCI_TRY(ensure_buf(ctx, S.rpN, (size_t)(nnew + 1) * 8));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.rpN), nnew, dtot));
+  HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(S.rpN), nnew, dtot);
+  const int64_t nnzN = read_i64(ctx, dtot, &hs);
+  HCI_TRY(hs);
+  HCI_TRY(ensure_buf(ctx, S.colN, (size_t)(nnzN + 1) * 4));
+  HCI_TRY(ensure_buf(ctx, S.valN, (size_t)(nnzN + 1) * 8));
+  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(S.rpN), bp<int32_t>(S.colN), bp<double>(S.valN)));
+  prof_toc(ctx, HCI_PH_GRAPH_ROWS);
+  // transposed entries for the old rows, sorted by the row they go to
   prof_tic(ctx, HCI_PH_GRAPH_MERGE);
   HCI_TRY(ensure_buf(ctx, S.hist, (size_t)(nV + 1) * 8));
   HCI_CUDA(ctx, cudaMemsetAsync(S.hist.p, 0, (size_t)(nV + 1) * 8, st));
@@ -903,9 +1034,8 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
                                                 bp<int64_t>(S.cnt), bp<int64_t>(S.hist));
   HCI_TRY(ensure_buf(ctx, S.tbase, (size_t)(nnew + 1) * 8));
   HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.tbase), nnew, dtot));
-  int64_t nT = 0;
-  HCI_CUDA(ctx, cudaMemcpyAsync(&nT, dtot, 8, cudaMemcpyDeviceToHost, st));
-  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  const int64_t nT = read_i64(ctx, dtot, &hs);
+  HCI_TRY(hs);
   HCI_TRY(ensure_buf(ctx, S.T, (size_t)(nT + 1) * 16));
   HCI_TRY(ensure_buf(ctx, S.T2, (size_t)(nT + 1) * 16));
   HCI_LAUNCH(k_emit_T, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, bp<int64_t>(S.mark),
@@ -915,32 +1045,70 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(sort_keys(ctx, bp<uint64_t>(S.T), bp<uint64_t>(S.T2), nT, bits, 0));
   HCI_TRY(ensure_buf(ctx, S.tstart, (size_t)(nV + 1) * 8));
   HCI_TRY(scan_i64(ctx, bp<int64_t>(S.hist), bp<int64_t>(S.tstart), nV, dtot));
-  // lengths and the merged CSR
-  HCI_TRY(ensure_buf(ctx, S.len, (size_t)(nV + 1) * 8));
-  HCI_LAUNCH(k_lengths, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), nold,
-                                                       bp<int32_t>(S.newrows), bp<int64_t>(S.rpN), nnew,
-                                                       bp<int64_t>(S.hist), bp<int64_t>(S.len));
+  // plan the rows of V' in the pool: stay in place or take a new range
+  HCI_TRY(ensure_buf(ctx, G.rowstart, (size_t)(nV + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, G.rowlen, (size_t)(nV + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, G.rowcap, (size_t)(nV + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, S.len, (size_t)(2 * nV + 2) * 8));
+  int64_t* need = bp<int64_t>(S.len);
+  int64_t* rel = need + nV + 1;
+  int64_t total = 0;
+  int repack = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    HCI_LAUNCH(k_plan_rows, grid_for(nV, 256), 256, 0, st)(
+        bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), bp<int64_t>(S.cap_old), nold,
+        bp<int32_t>(S.newrows), bp<int64_t>(S.rpN), nnew, bp<int64_t>(S.hist), repack, bp<int64_t>(G.rowstart),
+        bp<int64_t>(G.rowlen), bp<int64_t>(G.rowcap), need);
+    HCI_TRY(scan_i64(ctx, need, rel, nV, dtot));
+    total = read_i64(ctx, dtot, &hs);
+    HCI_TRY(hs);
+    if (repack || G.pool_used + total <= G.pool_cap) break;
+    repack = 1;
+  }
+  int32_t* col_dst = bp<int32_t>(G.col);
+  double* val_dst = bp<double>(G.val);
+  int64_t base = G.pool_used;
+  if (repack) {
+    // every row moves to a fresh pool sized with headroom
+    const int64_t cap = total + total / 4 + 1024;
+    HCI_TRY(ensure_buf(ctx, S.col_old, (size_t)cap * 4));
+    HCI_TRY(ensure_buf(ctx, S.val_old, (size_t)cap * 8));
+    col_dst = bp<int32_t>(S.col_old);
+    val_dst = bp<double>(S.val_old);
+    base = 0;
+  }
+  HCI_LAUNCH(k_assign_starts, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(G.rowstart), rel, nV, base);
+  HCI_LAUNCH(k_move_old_rows, grid_for(nold * 32, 256), 256, 0, st)(
+      bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), nold, bp<int32_t>(G.col),
+      bp<double>(G.val), bp<int64_t>(G.rowstart), col_dst, val_dst, bp<ulonglong2>(S.T), bp<int64_t>(S.tstart),
+      bp<int64_t>(S.hist), bp<int64_t>(S.rpN), nnew, bp<int32_t>(S.newrows), bp<double>(S.valN));
+  HCI_LAUNCH(k_place_new_rows, gw, 256, 0, st)(bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), bp<int32_t>(S.colN),
+                                                bp<double>(S.valN), bp<int64_t>(G.rowstart), col_dst, val_dst);
+  HCI_CUDA(ctx, cudaGetLastError());
+  if (repack) {
+    std::swap(G.col, S.col_old);
+    std::swap(G.val, S.val_old);
+    G.pool_cap = (int64_t)(G.col.bytes / 4) < (int64_t)(G.val.bytes / 8) ? (int64_t)(G.col.bytes / 4)
+                                                                          : (int64_t)(G.val.bytes / 8);
+    G.pool_used = total;
+  } else {
+    G.pool_used += total;
+  }
+  // logical prefix of the row lengths
   HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.len), bp<int64_t>(G.rowptr), nV, dtot));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(G.rowlen), bp<int64_t>(G.rowptr), nV, dtot));
   HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(G.rowptr), nV, dtot);
-  int64_t nnz = 0;
-  HCI_CUDA(ctx, cudaMemcpyAsync(&nnz, dtot, 8, cudaMemcpyDeviceToHost, st));
-  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  const int64_t nnz = read_i64(ctx, dtot, &hs);
+  HCI_TRY(hs);
+  prof_toc(ctx, HCI_PH_GRAPH_MERGE);
   if (nnz != G.nnz + nnzN + nT)
     return hci_fail(ctx, HCI_ERR_CUDA, "graph_extend: inconsistent sizes %lld != %lld + %lld + %lld", (long long)nnz,
                     (long long)G.nnz, (long long)nnzN, (long long)nT);
-  HCI_TRY(ensure_buf(ctx, G.col, (size_t)(nnz + 1) * 4));
-  HCI_TRY(ensure_buf(ctx, G.val, (size_t)(nnz + 1) * 8));
-  HCI_LAUNCH(k_copy_old_rows, grid_for(nold * 32, 256), 256, 0, st)(
-      bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), bp<int32_t>(S.col_old), bp<double>(S.val_old), nold,
-      bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val), bp<ulonglong2>(S.T), bp<int64_t>(S.tstart),
-      bp<int64_t>(S.hist), bp<int64_t>(S.rpN), nnew, bp<int32_t>(S.newrows), bp<double>(S.valN));
-  HCI_LAUNCH(k_copy_new_rows, gw, 256, 0, st)(bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN),
-                                               bp<int32_t>(S.colN), bp<double>(S.valN), bp<int64_t>(G.rowptr),
-                                               bp<int32_t>(G.col), bp<double>(G.val));
-  HCI_CUDA(ctx, cudaGetLastError());
-  prof_toc(ctx, HCI_PH_GRAPH_MERGE);
-  HCI_TRY(compute_diag(ctx, nV));
+  // diagonal: old values move, new rows are computed
+  HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
+  HCI_LAUNCH(k_move_diag, grid_for(nold, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<double>(S.diag_old), nold,
+                                                           bp<double>(G.diag));
+  HCI_TRY(compute_diag(ctx, nnew, bp<int32_t>(S.newrows), bp<double>(G.diag)));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   G.nV = nV;
@@ -975,11 +1143,13 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
   ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;
   ctx->st_counts[HCI_ST_SIGMA_NNZ] += G.nnz * nvec;
   if (nvec == 1)
-    HCI_LAUNCH(k_sigma1, 152 * 6, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val),
-                                                   bp<double>(G.diag), G.nV, c, sigma, 1);
+    HCI_LAUNCH(k_sigma1, 152 * 6, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart),
+                                                   bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag), G.nV,
+                                                   c, sigma, 1);
   else
     HCI_LAUNCH(k_sigma, grid_for(G.nV * 32, 256, 152 * 16), 256, 0, ctx->st)(
-        bp<int64_t>(G.rowptr), bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag), G.nV, c, sigma, nvec);
+        bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag),
+        G.nV, c, sigma, nvec);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_SIGMA);
   return HCI_OK;

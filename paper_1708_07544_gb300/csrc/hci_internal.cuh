@@ -31,9 +31,13 @@ struct Graph {
   uint64_t hash = 0;
   int64_t nnz = 0;           // off-diagonal entries (both orientations stored)
   int64_t nua = 0, nub = 0;  // distinct alpha / beta strings of the space
-  DevBuf rowptr;             // int64 [nV+1]
-  DevBuf col;                // int32 [nnz]
-  DevBuf val;                // double [nnz]
+  DevBuf rowptr;             // int64 [nV+1] prefix sums of the row lengths (logical CSR)
+  DevBuf rowstart;           // int64 [nV] first pool slot of each row
+  DevBuf rowlen;             // int64 [nV] live entries of each row
+  DevBuf rowcap;             // int64 [nV] slots owned by each row (>= rowlen)
+  DevBuf col;                // int32 pool of columns
+  DevBuf val;                // double pool of values
+  int64_t pool_used = 0, pool_cap = 0;
   DevBuf diag;               // double [nV]
   DevBuf keys;               // copy of the space's keys [nV][2]
 };
@@ -54,7 +58,7 @@ struct Lists {
 // Scratch of the incremental graph update (V' = V + new determinants).
 struct IncScratch {
   DevBuf pos_old, mark, flag, newrows, rpN, colN, valN, cnt, hist, tbase, T, T2, tstart, len;
-  DevBuf keys_old, rp_old, col_old, val_old;
+  DevBuf keys_old, rp_old, col_old, val_old, len_old, cap_old, diag_old;
 };
 
 // Per-phase CUDA-event timers (enabled by hci_profile).
@@ -78,7 +82,7 @@ struct hci_ctx {
   // scratch
   DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items;
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
-  DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb;
+  DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval;
   IncScratch inc;
   bool incremental = true;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part;

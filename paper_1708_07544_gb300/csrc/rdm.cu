@@ -29,6 +29,7 @@ __device__ __forceinline__ void add2(double* r2, int n, int p, int q, int r, int
 __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulonglong2* __restrict__ V, int64_t nV,
                                                               const double* __restrict__ c,
                                                               const int64_t* __restrict__ rowptr,
+                                                              const int64_t* __restrict__ rowstart,
                                                               const int32_t* __restrict__ col, double* __restrict__ r1,
                                                               double* __restrict__ r2,
                                                               unsigned long long* __restrict__ queue) {
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
     if (i >= nV) break;
     const double ci = c[i];
     const ulonglong2 ki = V[i];
-    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
     for (int64_t k = b + lane; k < e; k += 32) {
       const int64_t j = col[k];
       const ulonglong2 kj = V[j];
@@ -224,6 +225,7 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 56);
   HCI_CUDA(ctx, cudaMemsetAsync(queue, 0, 8, st));
   HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, V, nV, c, bp<int64_t>(ctx->graph.rowptr),
+                                                         bp<int64_t>(ctx->graph.rowstart),
                                                    bp<int32_t>(ctx->graph.col), rdm1, rdm2, queue);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);
