@@ -602,10 +602,24 @@ __global__ void k_move_old_rows(const int64_t* __restrict__ pos_old, const int64
     const int64_t p = pos_old[i];
     const int64_t src = start_old[i], dst = start2[p], len = len_old[i];
     const bool moved = (dst != src) || (col_dst != col_src);
-    for (int64_t k = lane; k < len; k += 32) {
+    // four independent load -> gather -> store chains per lane
+    int64_t k = lane;
+    for (; k + 96 < len; k += 128) {
+      const int32_t j0 = col_src[src + k], j1 = col_src[src + k + 32], j2 = col_src[src + k + 64],
+                    j3 = col_src[src + k + 96];
+      const int64_t p0 = pos_old[j0], p1 = pos_old[j1], p2 = pos_old[j2], p3 = pos_old[j3];
+      if (moved) {
+        const double v0 = val_src[src + k], v1 = val_src[src + k + 32], v2 = val_src[src + k + 64],
+                     v3 = val_src[src + k + 96];
+        val_dst[dst + k] = v0; val_dst[dst + k + 32] = v1; val_dst[dst + k + 64] = v2; val_dst[dst + k + 96] = v3;
+      }
+      col_dst[dst + k] = (int32_t)p0; col_dst[dst + k + 32] = (int32_t)p1;
+      col_dst[dst + k + 64] = (int32_t)p2; col_dst[dst + k + 96] = (int32_t)p3;
+    }
+    for (; k < len; k += 32) {
       const int32_t j = col_src[src + k];
-      col_dst[dst + k] = (int32_t)pos_old[j];
       if (moved) val_dst[dst + k] = val_src[src + k];
+      col_dst[dst + k] = (int32_t)pos_old[j];
     }
     const int64_t t0 = tstart[p], tn = hist[p];
     for (int64_t k = lane; k < tn; k += 32) {
