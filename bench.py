@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of one CPU sample")
     ap.add_argument("--sigma-reps", type=int, default=20)
+    ap.add_argument("--fwd-bwd-reps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -119,6 +120,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of one sigma launch per (connection, row), from the ncu
+# capture of k_sigma1 on the pentacene (22e,22o) space (profiles/); traffic
+# grows in proportion to the connections, so it is scaled to the launch.
+# None while the kernel differs from the captured one.
+SIGMA_TRAFFIC_PER_CONN = 12.39
+
+
+def traffic_per_launch(nnz, nV):
+    if SIGMA_TRAFFIC_PER_CONN is None:
+        return None
+    return int(SIGMA_TRAFFIC_PER_CONN * (nnz + nV))
+
+
 def max_over_ranks(value, world, device=None):
     """Largest value over the ranks of the default process group."""
     import torch
@@ -134,6 +148,13 @@ def aggregate_seconds(ms_per_step_max, world):
     """Replicas: every rank solves one instance per step, so the whole job
     completes `world` solves per (max-over-ranks) step time."""
     return ms_per_step_max / 1e3 / world
+
+
+# FP64 rate of the part: 152 SMs x 2 DFMA per clock x 2 flop at the maximum
+# SM clock (2.07 GHz) = 1.26 TFLOP/s, consistent with the nominal 1.25
+# TFLOP/s; the sigma kernel's ncu capture shows one FP64 warp instruction
+# per 16 cycles per SM at full pipe utilisation.
+FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def measured_peaks():
@@ -272,9 +293,36 @@ def gpu_arm(args):
     sig_ms = tm["sigma"][0] / max(tm["sigma"][1], 1)
     nnz = st["graph_nnz"]
     nV = int(keys.shape[0])
-    sig_bytes = 12 * nnz + 32 * nV + 8
+    sig_bytes = 12 * nnz + 40 * nV + 8
+    sig_flops = 2 * (nnz + nV)
     peak, peak_kind = measured_peaks()
     achieved = sig_bytes / (sig_ms * 1e-3) / 1e9
+    achieved_tf = sig_flops / (sig_ms * 1e-3) / 1e12
+
+    # forward vs forward + backward through the autograd Function (the
+    # backward recomputes c by Davidson on the saved space, then the RDMs and
+    # the rotation adjoint)
+    fb = {}
+    if args.fwd_bwd_reps > 0:
+        t_f, t_fb = [], []
+        for _ in range(args.fwd_bwd_reps):
+            kk = k_d.clone().requires_grad_(True)
+            e0f = torch.cuda.Event(enable_timing=True)
+            e1f = torch.cuda.Event(enable_timing=True)
+            e2f = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0f.record()
+            E = pkg.HCIEnergy.apply(h_d, eri_d, kk, inst.nalpha, inst.nbeta, inst.e_core, eps1, 30, DAV_TOL)
+            e1f.record()
+            E.backward()
+            e2f.record()
+            torch.cuda.synchronize()
+            t_f.append(e0f.elapsed_time(e1f))
+            t_fb.append(e0f.elapsed_time(e2f))
+        fwd = statistics.median(t_f) / 1e3
+        fwdbwd = statistics.median(t_fb) / 1e3
+        fb = {"fwd_s": round(fwd, 4), "fwd_bwd_s": round(fwdbwd, 4), "ratio": round(fwdbwd / fwd, 4),
+              "reps": args.fwd_bwd_reps}
 
     phases = {}
     for r in recs:
@@ -309,10 +357,14 @@ def gpu_arm(args):
             "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
             "phase_counts": {k: v[1] for k, v in phases.items()},
             "work": work,
-            "roofline": {"kernel": "k_sigma (CSR FP64 H c)", "bound": "hbm", "achieved": round(achieved, 1),
-                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_kind": peak_kind, "bytes_per_launch": sig_bytes,
-                         "launch_ms": round(sig_ms, 4)},
+            "roofline": {"kernel": "k_sigma1 (pooled-CSR FP64 H c)", "bound": "alu", "achieved": round(achieved_tf, 4),
+                         "peak": round(FP64_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_TFLOPS, 4),
+                         "traffic": traffic_per_launch(nnz, nV), "peak_kind": "derived FP64 (152 SM x 2 DFMA/clk x 2.07 GHz)",
+                         "flops_per_launch": sig_flops, "launch_ms": round(sig_ms, 4)},
+            "roofline_hbm": {"kernel": "k_sigma1", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                             "bytes_per_launch": sig_bytes},
+            "fwd_bwd": fb,
             "e2e": {"value": round(aggregate_seconds(e2e_step, world), 6), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

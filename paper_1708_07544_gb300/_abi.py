@@ -186,7 +186,7 @@ def hci_rdm12(ctx, keys, c, norb):
     return r1, r2
 
 
-def hci_solve(ctx, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 20, device="cuda"):
+def hci_solve(ctx, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24, device="cuda"):
     """Whole variational stage; returns (keys, c, E, iterations)."""
     L = load()
     nv = ctypes.c_int64(0)

@@ -50,7 +50,7 @@ class HCISolver:
     def rdm12(self, keys, c):
         return _abi.hci_rdm12(self.ctx, keys, c, self.norb)
 
-    def solve(self, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 20):
+    def solve(self, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24):
         keys, c, e, it = _abi.hci_solve(self.ctx, eps1, max_iter, dav_tol, dav_maxit, cap)
         return {"keys": keys, "c": c, "E": e, "iters": it}
 
