@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of one CPU sample")
     ap.add_argument("--sigma-reps", type=int, default=20)
     ap.add_argument("--fwd-bwd-reps", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=1, help="also time the 64-instance batched solve")
     return ap.parse_args()
 
 
@@ -332,6 +333,31 @@ def gpu_arm(args):
             a[1] += cnt / len(recs)
     work = recs[-1]["stats"]
 
+    # batching: 64 uneven DF active spaces (norb 10-24) solved concurrently,
+    # stream count picked by the autotuner, against one-at-a-time solves
+    batch = {}
+    if args.batch:
+        from paper_1708_07544_gb300 import tune
+
+        binst = hi.df_batch(64)
+        lst = [(i.norb, i.nalpha, i.nbeta, torch.tensor(i.h, device=dev), torch.tensor(i.eri, device=dev),
+                i.e_core) for i in binst]
+        best, tuned = tune.tune_nstreams(lst, 1e-4, want_rdm=True)
+        reps = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            en, nv, _, _ = _abi.hci_solve_batch(lst, 1e-4, dav_tol=DAV_TOL, nstreams=best, want_rdm=True)
+            torch.cuda.synchronize()
+            reps.append(time.perf_counter() - t0)
+        seq = tuned.get(1)
+        batch = {"instances": len(lst), "total_dets": int(nv.sum()), "max_dets": int(nv.max()),
+                 "nstreams": best, "batched_s": round(statistics.median(reps), 4),
+                 "sequential_s": round(seq, 4) if seq else None,
+                 "speedup": round(seq / statistics.median(reps), 3) if seq else None,
+                 "tuning_s": {str(k): round(v, 4) for k, v in tuned.items()},
+                 "includes": "solve + 1/2-RDM per instance"}
+
     out = None
     if rank == 0:
         value = aggregate_seconds(ms_step, world)
@@ -365,6 +391,7 @@ def gpu_arm(args):
                              "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                              "bytes_per_launch": sig_bytes},
             "fwd_bwd": fb,
+            "batch": batch,
             "e2e": {"value": round(aggregate_seconds(e2e_step, world), 6), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

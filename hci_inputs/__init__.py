@@ -238,12 +238,21 @@ def df_12o(seed: int = 1708) -> Instance:
     return df_instance(12, 48, seed, name="df_12o_12e")
 
 
-def df_batch(count: int = 64, seed0: int = 7544):
+# Scale of the batch factors relative to sqrt(0.5/naux): at 1.0 every
+# instance with norb >= 18 needs a connection graph of 1e11+ bytes at
+# eps1 = 1e-4; the frozen 0.2 keeps the largest (24e,24o) instances at
+# 4.5e4-7e4 determinants (1.0e6 over the 64 instances).
+DF_BATCH_SCALE_FACTOR = 0.2
+
+
+def df_batch(count: int = 64, seed0: int = 7544, scale_factor: float | None = None):
     """Uneven batch: norb_k = 10 + (k mod 15), nelec = norb, naux = 4 norb."""
+    f = DF_BATCH_SCALE_FACTOR if scale_factor is None else scale_factor
     out = []
     for k in range(count):
         n = 10 + (k % 15)
-        out.append(df_instance(n, 4 * n, seed0 + k, name=f"df_batch_{k}_{n}o"))
+        s = f * math.sqrt(0.5 / (4 * n))
+        out.append(df_instance(n, 4 * n, seed0 + k, scale=s, name=f"df_batch_{k}_{n}o"))
     return out
 
 

@@ -138,6 +138,22 @@ hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, in
                      uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV, double* energy,
                      int* iters);
 
+/* Many independent active spaces of uneven size (BASELINE batching
+ * workload; the paper solves one space per orbital iteration, Sec. III): each
+ * instance k gets its own context and stream, `nstreams` host threads take
+ * instances from a shared queue, so uneven instances overlap on the GPU.
+ * Arrays of length count: norb, nalpha, nbeta, h[k] / eri[k] (device
+ * pointers as in hci_create), e_core (may be NULL = 0).  Outputs (host):
+ * energies[k], nV[k] (size of the converged space), status[k] (may be
+ * NULL).  rdm1 / rdm2 may be NULL, else arrays of device pointers receiving
+ * each instance's RDMs (hci_rdm12 layout; a NULL entry skips that instance).
+ * Returns the first failure (its instance named in hci_last_error(NULL));
+ * the other instances still run.  Synchronises. */
+hci_status hci_solve_batch(int count, const int* norb, const int* nalpha, const int* nbeta,
+                           const double* const* h, const double* const* eri, const double* e_core, double eps1,
+                           int max_iter, double dav_tol, int dav_maxit, int nstreams, double* energies,
+                           int64_t* nV, double* const* rdm1, double* const* rdm2, int* status);
+
 /* Active-active orbital rotation (Sec. III.A: the integrals depend on the
  * orbital parameters kappa; Sec. III.B): U = exp(kappa) for an n x n real
  * kappa (antisymmetric for an orthogonal U), h' = U^T h U,

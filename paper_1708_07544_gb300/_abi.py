@@ -26,7 +26,8 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
-           "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc"]
+           "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
+           "hci_solve_batch"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -70,6 +71,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
     L.hci_rotate_noalloc.argtypes = [I, V, V, V, V, V, V, V]
+    L.hci_solve_batch.argtypes = [I, V, V, V, V, V, V, D, I, D, I, I, V, V, V, V, V]
     L.hci_stats.argtypes = [V, V, I]
     L.hci_profile.argtypes = [V, I]
     L.hci_timers.argtypes = [V, V, V, I]
@@ -256,3 +258,39 @@ def hci_timers(ctx):
 
 def hci_launch_count():
     return int(load().hci_launch_count())
+
+
+def hci_solve_batch(instances, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, nstreams=8, want_rdm=False,
+                    device="cuda"):
+    """Solve many active spaces concurrently.  instances: list of
+    (norb, nalpha, nbeta, h, eri, e_core) with h, eri CUDA float64 tensors.
+    Returns (energies, nV, rdm1 list or None, rdm2 list or None)."""
+    import numpy as np
+
+    L = load()
+    cnt = len(instances)
+    norb = np.array([int(x[0]) for x in instances], dtype=np.int32)
+    na = np.array([int(x[1]) for x in instances], dtype=np.int32)
+    nb = np.array([int(x[2]) for x in instances], dtype=np.int32)
+    hs = [x[3].to(torch.float64).contiguous() for x in instances]
+    es = [x[4].to(torch.float64).contiguous() for x in instances]
+    hp = np.array([_ptr(t) for t in hs], dtype=np.uint64)
+    ep = np.array([_ptr(t) for t in es], dtype=np.uint64)
+    ec = np.array([float(x[5]) for x in instances], dtype=np.float64)
+    en = np.zeros(cnt)
+    nv = np.zeros(cnt, dtype=np.int64)
+    stat = np.zeros(cnt, dtype=np.int32)
+    r1 = r2 = None
+    r1p = r2p = None
+    if want_rdm:
+        r1 = [torch.empty((int(n), int(n)), dtype=torch.float64, device=device) for n in norb]
+        r2 = [torch.empty((int(n),) * 4, dtype=torch.float64, device=device) for n in norb]
+        r1p = np.array([t.data_ptr() for t in r1], dtype=np.uint64)
+        r2p = np.array([t.data_ptr() for t in r2], dtype=np.uint64)
+    torch.cuda.synchronize()
+    st = L.hci_solve_batch(cnt, norb.ctypes.data, na.ctypes.data, nb.ctypes.data, hp.ctypes.data, ep.ctypes.data,
+                           ec.ctypes.data, float(eps1), int(max_iter), float(dav_tol), int(dav_maxit), int(nstreams),
+                           en.ctypes.data, nv.ctypes.data, r1p.ctypes.data if want_rdm else None,
+                           r2p.ctypes.data if want_rdm else None, stat.ctypes.data)
+    _check(st, None)
+    return en, nv, r1, r2

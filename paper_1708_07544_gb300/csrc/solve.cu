@@ -3,6 +3,13 @@
 //   C^mu = selection(V^mu, c^mu, eps1); stop if empty;
 //   V^{mu+1} = V^mu + C^mu (sorted merge, c padded with zeros);
 //   c^{mu+1}, E^{mu+1} = Davidson on V^{mu+1} warm-started from the padded c.
+// hci_solve_batch runs many such solves concurrently, one context and one
+// stream per in-flight instance, driven by a pool of host threads.
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 #include "hci_internal.cuh"
 
 namespace {
@@ -14,17 +21,12 @@ __global__ void k_aufbau(int na, int nb, ulonglong2* keys, double* c) {
 }
 }  // namespace
 
-extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit,
-                                uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out, double* energy,
-                                int* iters) {
-  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_solve: null context");
-  if (!nV_out || !energy) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve: null output scalar");
-  if (max_iter < 0 || dav_maxit < 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve: bad iteration limits");
-  *nV_out = 0;
-  if (iters) *iters = 0;
+// The whole loop; on success the final space and vector are left in
+// keys_res / c_res (owned by the caller, released with free_buf).
+static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit, DevBuf& keys_res,
+                             DevBuf& c_res, int64_t* nV_out, double* energy, int* iters) {
   cudaStream_t st = ctx->st;
   HCI_TRY(hci_build_lists(ctx));
-  // two ping-pong spaces and a buffer for the new determinants
   DevBuf kb[2], cb[2], nk;
   auto cleanup = [&]() {
     for (int i = 0; i < 2; ++i) { free_buf(st, kb[i]); free_buf(st, cb[i]); }
@@ -53,7 +55,8 @@ extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double 
     if (nn == 0) break;
     const int nxt = cur ^ 1;
     const int64_t nV2 = nV + nn;
-    if ((s = ensure_buf(ctx, kb[nxt], (size_t)nV2 * 16)) != HCI_OK || (s = ensure_buf(ctx, cb[nxt], (size_t)nV2 * 8)) != HCI_OK) {
+    if ((s = ensure_buf(ctx, kb[nxt], (size_t)nV2 * 16)) != HCI_OK ||
+        (s = ensure_buf(ctx, cb[nxt], (size_t)nV2 * 8)) != HCI_OK) {
       cleanup();
       return s;
     }
@@ -68,14 +71,105 @@ extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double 
   if (iters) *iters = mu;
   *nV_out = nV;
   *energy = e;
+  std::swap(keys_res, kb[cur]);
+  std::swap(c_res, cb[cur]);
+  cleanup();
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit,
+                                uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out, double* energy,
+                                int* iters) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_solve: null context");
+  if (!nV_out || !energy) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve: null output scalar");
+  if (max_iter < 0 || dav_maxit < 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve: bad iteration limits");
+  *nV_out = 0;
+  if (iters) *iters = 0;
+  cudaStream_t st = ctx->st;
+  DevBuf kr, cr;
+  int64_t nV = 0;
+  double e = 0.0;
+  hci_status s = solve_core(ctx, eps1, max_iter, dav_tol, dav_maxit, kr, cr, &nV, &e, iters);
+  if (s != HCI_OK) return s;
+  *nV_out = nV;
+  *energy = e;
   if (nV > cap) {
-    cleanup();
+    free_buf(st, kr);
+    free_buf(st, cr);
     return hci_fail(ctx, HCI_ERR_CAPACITY, "hci_solve: %lld determinants exceed cap %lld", (long long)nV,
                     (long long)cap);
   }
-  if (keys_out) HCI_CUDA(ctx, cudaMemcpyAsync(keys_out, kb[cur].p, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st));
-  if (c_out) HCI_CUDA(ctx, cudaMemcpyAsync(c_out, cb[cur].p, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
-  HCI_CUDA(ctx, cudaStreamSynchronize(st));
-  cleanup();
+  cudaError_t ce = cudaSuccess;
+  if (keys_out) ce = cudaMemcpyAsync(keys_out, kr.p, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st);
+  if (ce == cudaSuccess && c_out) ce = cudaMemcpyAsync(c_out, cr.p, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  free_buf(st, kr);
+  free_buf(st, cr);
+  if (ce != cudaSuccess) return hci_fail(ctx, HCI_ERR_CUDA, "hci_solve: %s", cudaGetErrorString(ce));
+  return HCI_OK;
+}
+
+static std::mutex g_batch_mu;
+static char g_batch_err[512] = {0};
+
+extern "C" hci_status hci_solve_batch(int count, const int* norb, const int* nalpha, const int* nbeta,
+                                      const double* const* h, const double* const* eri, const double* e_core,
+                                      double eps1, int max_iter, double dav_tol, int dav_maxit, int nstreams,
+                                      double* energies, int64_t* nV, double* const* rdm1, double* const* rdm2,
+                                      int* status) {
+  if (count < 0 || nstreams < 1) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_solve_batch: bad count or nstreams");
+  if (count == 0) return HCI_OK;
+  if (!norb || !nalpha || !nbeta || !h || !eri || !energies || !nV)
+    return hci_fail(nullptr, HCI_ERR_INVALID, "hci_solve_batch: null argument array");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_solve_batch: %s", cudaGetErrorString(ce));
+  std::atomic<int> next{0};
+  std::atomic<int> first_err{HCI_OK};
+  g_batch_err[0] = 0;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      int z = HCI_OK;
+      first_err.compare_exchange_strong(z, HCI_ERR_CUDA);
+      return;
+    }
+    for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
+      hci_ctx* ctx = nullptr;
+      hci_status s = hci_create(&ctx, norb[k], nalpha[k], nbeta[k], h[k], eri[k], e_core ? e_core[k] : 0.0, st);
+      DevBuf kr, cr;
+      int64_t n = 0;
+      double e = 0.0;
+      int it = 0;
+      if (s == HCI_OK) s = solve_core(ctx, eps1, max_iter, dav_tol, dav_maxit, kr, cr, &n, &e, &it);
+      if (s == HCI_OK && rdm1 && rdm2 && rdm1[k] && rdm2[k])
+        s = hci_rdm12(ctx, bp<uint64_t>(kr), n, bp<double>(cr), rdm1[k], rdm2[k]);
+      energies[k] = e;
+      nV[k] = n;
+      if (status) status[k] = s;
+      if (s != HCI_OK) {
+        int z = HCI_OK;
+        if (first_err.compare_exchange_strong(z, s)) {
+          std::lock_guard<std::mutex> lock(g_batch_mu);
+          snprintf(g_batch_err, sizeof g_batch_err, "instance %d: %s", k, hci_last_error(ctx));
+        }
+      }
+      if (ctx) {
+        free_buf(st, kr);
+        free_buf(st, cr);
+        hci_destroy(ctx);
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  };
+  const int nt = nstreams < count ? nstreams : count;
+  std::vector<std::thread> pool;
+  pool.reserve((size_t)nt);
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  const int err = first_err.load();
+  if (err != HCI_OK) return hci_fail(nullptr, err, "hci_solve_batch: %s", g_batch_err);
   return HCI_OK;
 }
