@@ -263,7 +263,6 @@ __device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t
   if (FILL && ok) {
     int64_t pos = w + __popc(m & ((1u << lane) - 1u));
     A.col[pos] = (int32_t)j;
-    A.val[pos] = connection_el(A.H, ki, A.V[j]);
   }
   w += __popc(m);
 }
@@ -437,6 +436,37 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
       }
     }
     if (!FILL && lane == 0) A.rowcnt[q] = w;
+  }
+}
+
+// Matrix elements of filled rows (the search only records the columns):
+// row q holds entries [start[q], start[q] + len) of col/val, with
+// len = start[q+1] - start[q] (DENSE) or lens[q]; four entries per lane in
+// flight.
+template <bool DENSE>
+__global__ void __launch_bounds__(256) k_row_values(const int32_t* __restrict__ rowlist, int64_t nrows,
+                                                    const int64_t* __restrict__ start,
+                                                    const int64_t* __restrict__ lens, const int32_t* __restrict__ col,
+                                                    double* __restrict__ val, const ulonglong2* __restrict__ V,
+                                                    HamView H) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nrows; q += nwarps) {
+    const int64_t i = rowlist ? (int64_t)rowlist[q] : q;
+    const ulonglong2 ki = V[i];
+    const int64_t b = start[q];
+    const int64_t len = DENSE ? start[q + 1] - b : lens[q];
+    int64_t k = lane;
+    for (; k + 96 < len; k += 128) {
+      const ulonglong2 k0 = V[col[b + k]], k1 = V[col[b + k + 32]], k2 = V[col[b + k + 64]],
+                       k3 = V[col[b + k + 96]];
+      val[b + k] = connection_el(H, ki, k0);
+      val[b + k + 32] = connection_el(H, ki, k1);
+      val[b + k + 64] = connection_el(H, ki, k2);
+      val[b + k + 96] = connection_el(H, ki, k3);
+    }
+    for (; k < len; k += 32) val[b + k] = connection_el(H, ki, V[col[b + k]]);
   }
 }
 
@@ -966,6 +996,10 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   HCI_TRY(ensure_buf(ctx, G.col, (size_t)cap * 4));
   HCI_TRY(ensure_buf(ctx, G.val, (size_t)cap * 8));
   HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val)));
+  HCI_LAUNCH(k_row_values<false>, grid_for(nV * 32, 256), 256, 0, ctx->st)(
+      nullptr, nV, bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen), bp<int32_t>(G.col), bp<double>(G.val),
+      bp<ulonglong2>(G.keys), A.H);
+  HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_GRAPH_ROWS);
   HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
   HCI_TRY(compute_diag(ctx, nV, nullptr, bp<double>(G.diag)));
@@ -1038,6 +1072,10 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(ensure_buf(ctx, S.colN, (size_t)(nnzN + 1) * 4));
   HCI_TRY(ensure_buf(ctx, S.valN, (size_t)(nnzN + 1) * 8));
   HCI_TRY(rows_fill(ctx, A, bp<int64_t>(S.rpN), bp<int32_t>(S.colN), bp<double>(S.valN)));
+  HCI_LAUNCH(k_row_values<true>, grid_for(nnew * 32, 256), 256, 0, st)(
+      bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), nullptr, bp<int32_t>(S.colN), bp<double>(S.valN),
+      bp<ulonglong2>(G.keys), A.H);
+  HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_GRAPH_ROWS);
   // transposed entries for the old rows, sorted by the row they go to
   prof_tic(ctx, HCI_PH_GRAPH_MERGE);

@@ -15,7 +15,8 @@
 //     same spin only: rdm2[c,b,d,a] -= w; rdm2[d,a,c,b] -= w
 // Both orientations (i,j) and (j,i) are stored in the graph, so the RDMs
 // come out symmetric.  The diagonal part is reduced through the weighted
-// occupation correlation M[sp][tq] = sum_i c_i^2 n_sp(i) n_tq(i).
+// occupation correlation M[sp][tq] = sum_i c_i^2 n_sp(i) n_tq(i), folded over
+// the alpha and beta string groups of the graph.
 #include "hci_internal.cuh"
 
 namespace {
@@ -103,76 +104,170 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
 }
 
 // M[s*n+p][t*n+q] = sum_i c_i^2 n_sp(i) n_tq(i), folded over the string
-// groups of the cached graph.  One warp per alpha group g with weight
-// W_g = sum_{i in g} c_i^2: the alpha-alpha block gets W_g for every pair of
-// orbitals occupied in alpha_g, the alpha-beta block gets v_g[q] =
-// sum_{i in g} c_i^2 n_q(beta_i) for every occupied p of alpha_g.  The
-// beta-beta block is folded over the beta groups the same way.  Block
-// partials live in shared memory and are added to M once per block.
-__global__ void k_occ_groups(int n, const ulonglong2* __restrict__ V, const double* __restrict__ c,
-                             const int64_t* __restrict__ ga, int64_t nua, const ulonglong2* __restrict__ bk,
-                             const int32_t* __restrict__ permb, const int64_t* __restrict__ gb, int64_t nub,
-                             double* __restrict__ M) {
-  extern __shared__ double sm[];
+// groups of the cached graph without atomics.
+//  1. one warp per alpha group g: W_g = sum_{i in g} c_i^2 and
+//     v_g[q] = sum_{i in g} c_i^2 n_q(beta_i) (warp reductions); one warp per
+//     beta group h: Wb_h = sum_{i in h} c_i^2.
+//  2. one thread per M entry and block per slice of groups: alpha-alpha
+//     entries sum W_g over groups with p, q in alpha_g, alpha-beta entries
+//     sum v_g[q] over groups with p in alpha_g, beta-beta entries sum Wb_h;
+//     the slices' partial M are added in a fixed order.
+__global__ void k_group_weights(int n, const ulonglong2* __restrict__ V, const double* __restrict__ c,
+                                const int64_t* __restrict__ ga, int64_t nua, const int32_t* __restrict__ permb,
+                                const int64_t* __restrict__ gb, int64_t nub, double* __restrict__ Wa,
+                                double* __restrict__ va, double* __restrict__ Wb) {
+  // lane q accumulates orbitals q and q + 32 over the members in order
+  // (broadcast loads, no cross-lane reduction)
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < nua + nub; g += nwarps) {
+    if (g < nua) {
+      double v0 = 0.0, v1 = 0.0, W = 0.0;
+      const int64_t b = ga[g], e = ga[g + 1];
+      int64_t i = b;
+      for (; i + 8 <= e; i += 8) {
+        double cw[8];
+        uint64_t yy[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cw[u] = c[i + u];
+          yy[u] = V[i + u].y;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const double w = cw[u] * cw[u];
+          W += w;
+          if ((yy[u] >> lane) & 1ull) v0 += w;
+          if ((yy[u] >> (lane + 32)) & 1ull) v1 += w;
+        }
+      }
+      for (; i < e; ++i) {
+        const double ci = c[i];
+        const double w = ci * ci;
+        const uint64_t y = V[i].y;
+        W += w;
+        if ((y >> lane) & 1ull) v0 += w;
+        if ((y >> (lane + 32)) & 1ull) v1 += w;
+      }
+      if (lane == 0) Wa[g] = W;
+      if (lane < n) va[g * n + lane] = v0;
+      if (lane + 32 < n) va[g * n + lane + 32] = v1;
+    } else {
+      const int64_t h = g - nua;
+      double W = 0.0;
+      for (int64_t k = gb[h] + lane; k < gb[h + 1]; k += 32) {
+        const double cv = c[permb[k]];
+        W += cv * cv;
+      }
+      for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+      if (lane == 0) Wb[h] = W;
+    }
+  }
+}
+
+constexpr int OCC_SLICES = 256;
+
+__global__ void k_occ_sums(int n, const ulonglong2* __restrict__ V, const int64_t* __restrict__ ga, int64_t nua,
+                           const ulonglong2* __restrict__ bk, const int64_t* __restrict__ gb, int64_t nub,
+                           const double* __restrict__ Wa, const double* __restrict__ va,
+                           const double* __restrict__ Wb, double* __restrict__ part) {
+  // blockIdx.x: slice of groups, staged in shared memory in chunks; thread
+  // t < 3n^2 owns one entry of the alpha-alpha (t < n^2), alpha-beta
+  // (t < 2n^2) or beta-beta block
+  constexpr int CH = 128;
+  __shared__ uint64_t s_a[CH];
+  __shared__ double s_w[CH];
+  __shared__ double s_v[CH * HCI_MAXORB / 2];   // n <= 64: CH x n doubles staged in two halves
   const int m = 2 * n;
-  double* Ms = sm;                          // m*m
-  double* vq = sm + m * m;                  // [warps][64]
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* v = vq + wid * HCI_MAXORB;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ms[t] = 0.0;
-  __syncthreads();
-  const int64_t gw = (int64_t)blockIdx.x * nw + wid, nwarps = (int64_t)gridDim.x * nw;
-  for (int64_t g = gw; g < nua; g += nwarps) {
-    // v[q] = sum_{i in g} c_i^2 n_q(beta_i): lane q % 32 keeps v[q] in a
-    // register, each 32-member chunk is reduced across the warp per orbital
-    double v0 = 0.0, v1 = 0.0, W = 0.0;
-    const int64_t b = ga[g], e = ga[g + 1];
-    for (int64_t i0 = b; i0 < e; i0 += 32) {
-      const int64_t i = i0 + lane;
-      const double w = i < e ? c[i] * c[i] : 0.0;
-      const uint64_t y = i < e ? V[i].y : 0ull;
-      W += w;
-      for (int q = 0; q < n; ++q) {
-        double t = ((y >> q) & 1ull) ? w : 0.0;
-        if (__any_sync(0xffffffffu, t != 0.0)) {
-          for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          if (lane == (q & 31)) { if (q < 32) v0 += t; else v1 += t; }
+  const int64_t slice = blockIdx.x;
+  const int64_t a0 = nua * slice / OCC_SLICES, a1 = nua * (slice + 1) / OCC_SLICES;
+  const int64_t b0 = nub * slice / OCC_SLICES, b1 = nub * (slice + 1) / OCC_SLICES;
+  const int nt = 3 * n * n;
+  double acc[12];
+  for (int r = 0; r < 12; ++r) acc[r] = 0.0;
+  // alpha groups: strings, weights and v in chunks
+  for (int64_t g0 = a0; g0 < a1; g0 += CH) {
+    const int cnt = (int)(a1 - g0 < CH ? a1 - g0 : CH);
+    for (int half = 0; half < 2; ++half) {
+      const int q0 = half * (n / 2), q1 = half == 0 ? n / 2 : n;
+      const int nq = q1 - q0;
+      __syncthreads();
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        s_a[t] = V[ga[g0 + t]].x;
+        s_w[t] = Wa[g0 + t];
+      }
+      for (int t = threadIdx.x; t < cnt * nq; t += blockDim.x) {
+        const int gi = t / nq, qq = t % nq;
+        s_v[gi * nq + qq] = va[(g0 + gi) * n + q0 + qq];
+      }
+      __syncthreads();
+      int r = 0;
+      for (int t = threadIdx.x; t < nt; t += blockDim.x, ++r) {
+        if (t < n * n) {
+          if (half) continue;
+          const int p = t / n, q = t % n;
+          double a = 0.0;
+          for (int gi = 0; gi < cnt; ++gi) {
+            const uint64_t x = s_a[gi];
+            if (((x >> p) & 1ull) && ((x >> q) & 1ull)) a += s_w[gi];
+          }
+          acc[r] += a;
+        } else if (t < 2 * n * n) {
+          const int u = t - n * n, p = u / n, q = u % n;
+          if (q < q0 || q >= q1) continue;
+          double a = 0.0;
+          for (int gi = 0; gi < cnt; ++gi)
+            if ((s_a[gi] >> p) & 1ull) a += s_v[gi * nq + (q - q0)];
+          acc[r] += a;
         }
       }
     }
-    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
-    v[lane] = v0;
-    v[lane + 32] = v1;
-    __syncwarp();
-    const uint64_t a = V[b].x;
-    for (int t = lane; t < n * n; t += 32) {
-      const int p = t / n, q = t % n;
-      if (!((a >> p) & 1ull)) continue;
-      if ((a >> q) & 1ull) atomicAdd(&Ms[p * m + q], W);
-      if (v[q] != 0.0) {
-        atomicAdd(&Ms[p * m + n + q], v[q]);
-        atomicAdd(&Ms[(n + q) * m + p], v[q]);
+  }
+  // beta groups
+  for (int64_t h0 = b0; h0 < b1; h0 += CH) {
+    const int cnt = (int)(b1 - h0 < CH ? b1 - h0 : CH);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      s_a[t] = bk[gb[h0 + t]].x;
+      s_w[t] = Wb[h0 + t];
+    }
+    __syncthreads();
+    int r = 0;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x, ++r) {
+      if (t < 2 * n * n) continue;
+      const int u = t - 2 * n * n, p = u / n, q = u % n;
+      double a = 0.0;
+      for (int gi = 0; gi < cnt; ++gi) {
+        const uint64_t x = s_a[gi];
+        if (((x >> p) & 1ull) && ((x >> q) & 1ull)) a += s_w[gi];
       }
+      acc[r] += a;
     }
-    __syncwarp();
   }
-  for (int64_t g = gw; g < nub; g += nwarps) {
-    double W = 0.0;
-    const int64_t b = gb[g], e = gb[g + 1];
-    for (int64_t k = b + lane; k < e; k += 32) {
-      const double cv = c[permb[k]];
-      W += cv * cv;
-    }
-    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
-    const uint64_t bb = bk[b].x;
-    for (int t = lane; t < n * n; t += 32) {
+  int r = 0;
+  double* P = part + slice * (int64_t)m * m;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x, ++r) {
+    if (t < n * n) {
       const int p = t / n, q = t % n;
-      if (((bb >> p) & 1ull) && ((bb >> q) & 1ull)) atomicAdd(&Ms[(n + p) * m + n + q], W);
+      P[p * m + q] = acc[r];
+    } else if (t < 2 * n * n) {
+      const int u = t - n * n, p = u / n, q = u % n;
+      P[p * m + n + q] = acc[r];
+      P[(n + q) * m + p] = acc[r];
+    } else {
+      const int u = t - 2 * n * n, p = u / n, q = u % n;
+      P[(n + p) * m + n + q] = acc[r];
     }
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x)
-    if (Ms[t] != 0.0) atomicAdd(&M[t], Ms[t]);
+}
+
+__global__ void k_sum_slices(int mm, const double* __restrict__ part, double* __restrict__ M) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mm) return;
+  double s = 0.0;
+  for (int k = 0; k < OCC_SLICES; ++k) s += part[(int64_t)k * mm + t];
+  M[t] = s;
 }
 
 // diagonal contributions from M
@@ -213,12 +308,21 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   HCI_CUDA(ctx, cudaMemsetAsync(M, 0, 4 * n2 * 8, st));
   prof_tic(ctx, HCI_PH_RDM_DIAG);
   const ulonglong2* V = bp<ulonglong2>(ctx->graph.keys);
-  const size_t smem = (size_t)4 * n2 * 8 + 8 * HCI_MAXORB * 8;
-  HCI_CUDA(ctx, cudaFuncSetAttribute(k_occ_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     4 * 64 * 64 * 8 + 8 * HCI_MAXORB * 8));
-  HCI_LAUNCH(k_occ_groups, 152, 256, smem, st)(n, V, c, bp<int64_t>(ctx->g_ga), ctx->graph.nua,
-                                               bp<ulonglong2>(ctx->g_bkeys), bp<int32_t>(ctx->g_permb),
-                                               bp<int64_t>(ctx->g_gb), ctx->graph.nub, M);
+  {
+    const Graph& G = ctx->graph;
+    const int64_t nua = G.nua, nub = G.nub;
+    const size_t mm = (size_t)4 * n2;
+    HCI_TRY(ensure_buf(ctx, ctx->s_rdmw, (size_t)(nua + nub + nua * n + 16) * 8 + (size_t)OCC_SLICES * mm * 8));
+    double* Wa = bp<double>(ctx->s_rdmw);
+    double* Wb = Wa + nua;
+    double* va = Wb + nub;
+    double* part = va + nua * n;
+    HCI_LAUNCH(k_group_weights, grid_for((nua + nub) * 32, 256), 256, 0, st)(
+        n, V, c, bp<int64_t>(ctx->g_ga), nua, bp<int32_t>(ctx->g_permb), bp<int64_t>(ctx->g_gb), nub, Wa, va, Wb);
+    HCI_LAUNCH(k_occ_sums, OCC_SLICES, 1024, 0, st)(n, V, bp<int64_t>(ctx->g_ga), nua, bp<ulonglong2>(ctx->g_bkeys),
+                                                   bp<int64_t>(ctx->g_gb), nub, Wa, va, Wb, part);
+    HCI_LAUNCH(k_sum_slices, (unsigned)((mm + 255) / 256), 256, 0, st)((int)mm, part, M);
+  }
   HCI_LAUNCH(k_diag_rdm, grid_for((int64_t)n2, 256), 256, 0, st)(n, M, rdm1, rdm2);
   prof_toc(ctx, HCI_PH_RDM_DIAG);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
