@@ -280,7 +280,9 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.cnt, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T,
                     &ctx->inc.T2, &ctx->inc.tstart, &ctx->inc.len, &ctx->inc.keys_old, &ctx->inc.rp_old,
                     &ctx->inc.col_old, &ctx->inc.val_old, &ctx->inc.len_old, &ctx->inc.cap_old,
-                    &ctx->inc.diag_old, &ctx->graph.rowstart, &ctx->graph.rowlen, &ctx->graph.rowcap};
+                    &ctx->inc.diag_old, &ctx->graph.rowstart, &ctx->graph.rowlen, &ctx->graph.rowcap,
+                    &ctx->graph.keys_int, &ctx->graph.s2i, &ctx->graph.i2s, &ctx->inc.s2i_old,
+                    &ctx->inc.keys_int_old, &ctx->d_perm};
   for (DevBuf* b : bufs) free_buf(st, *b);
   prof_release(ctx);
   cudaStreamSynchronize(st);

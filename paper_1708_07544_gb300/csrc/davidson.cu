@@ -342,8 +342,8 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
   const double* diag = bp<double>(ctx->graph.diag);
   cudaStream_t st = ctx->st;
   HCI_CUDA(ctx, cudaMemsetAsync(D.d, 0, sizeof(DavDev), st));
-  // start vector
-  HCI_CUDA(ctx, cudaMemcpyAsync(D.V, c_inout, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+  // start vector, in the graph's internal order
+  HCI_TRY(to_internal(ctx, c_inout, D.V, 1));
   HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
   double nrm2 = 0.0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
@@ -409,13 +409,14 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
     ++k;
   }
   if (iters) *iters = it + (converged ? 1 : 0);
-  // final vector: normalise, fix phase
+  // final vector: normalise, back to the caller's order, fix the phase
+  // there (largest |c|, first sorted position on ties)
   HCI_TRY(D.dots(D.x, 1, D.x, &D.d->nrm2));
   HCI_LAUNCH(k_scale_by, D.nblk, DBLOCK, 0, st)(D.x, nullptr, nV, &D.d->nrm2);
-  HCI_LAUNCH(k_amax_part, D.nblk, DBLOCK, 0, st)(D.x, nV, amax_v, amax_i);
-  HCI_LAUNCH(k_phase_sign, 1, 1, 0, st)(D.x, amax_v, amax_i, D.nblk, &D.d->dots[0]);
-  HCI_LAUNCH(k_apply_sign, D.nblk, DBLOCK, 0, st)(D.x, nV, &D.d->dots[0]);
-  HCI_CUDA(ctx, cudaMemcpyAsync(c_inout, D.x, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+  HCI_TRY(to_sorted(ctx, D.x, c_inout, 1));
+  HCI_LAUNCH(k_amax_part, D.nblk, DBLOCK, 0, st)(c_inout, nV, amax_v, amax_i);
+  HCI_LAUNCH(k_phase_sign, 1, 1, 0, st)(c_inout, amax_v, amax_i, D.nblk, &D.d->dots[0]);
+  HCI_LAUNCH(k_apply_sign, D.nblk, DBLOCK, 0, st)(c_inout, nV, &D.d->dots[0]);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_DAVIDSON);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));

@@ -246,6 +246,7 @@ struct GraphArgs {
   int32_t* col;
   double* val;
   int64_t* rowcnt;         // count pass: entries per processed row
+  const int32_t* s2i;      // sorted position -> internal id (columns are stored as internal ids)
   unsigned long long* queue;
   HamView H;
 };
@@ -262,7 +263,7 @@ __device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t
   unsigned m = __ballot_sync(0xffffffffu, ok);
   if (FILL && ok) {
     int64_t pos = w + __popc(m & ((1u << lane) - 1u));
-    A.col[pos] = (int32_t)j;
+    A.col[pos] = A.s2i[j];
   }
   w += __popc(m);
 }
@@ -447,14 +448,14 @@ template <bool DENSE>
 __global__ void __launch_bounds__(256) k_row_values(const int32_t* __restrict__ rowlist, int64_t nrows,
                                                     const int64_t* __restrict__ start,
                                                     const int64_t* __restrict__ lens, const int32_t* __restrict__ col,
-                                                    double* __restrict__ val, const ulonglong2* __restrict__ V,
-                                                    HamView H) {
+                                                    double* __restrict__ val, const ulonglong2* __restrict__ Vrow,
+                                                    const ulonglong2* __restrict__ V, HamView H) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = warp; q < nrows; q += nwarps) {
     const int64_t i = rowlist ? (int64_t)rowlist[q] : q;
-    const ulonglong2 ki = V[i];
+    const ulonglong2 ki = Vrow[i];
     const int64_t b = start[q];
     const int64_t len = DENSE ? start[q + 1] - b : lens[q];
     int64_t k = lane;
@@ -522,8 +523,7 @@ __global__ void k_compact_idx(const int64_t* __restrict__ flag, const int64_t* _
 // per new row: number of entries whose column is an old determinant; also
 // the histogram of those columns (entries to append to old rows)
 __global__ void k_count_old_cols(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t nrows,
-                                 const int64_t* __restrict__ mark, int64_t* __restrict__ cnt,
-                                 int64_t* __restrict__ hist) {
+                                 int64_t nold, int64_t* __restrict__ cnt, int64_t* __restrict__ hist) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -531,7 +531,7 @@ __global__ void k_count_old_cols(const int64_t* __restrict__ rp, const int32_t* 
     int64_t c = 0;
     for (int64_t k = rp[q] + lane; k < rp[q + 1]; k += 32) {
       const int32_t j = col[k];
-      if (mark[j]) {
+      if (j < nold) {
         ++c;
         atomicAdd((unsigned long long*)&hist[j], 1ull);
       }
@@ -544,8 +544,7 @@ __global__ void k_count_old_cols(const int64_t* __restrict__ rp, const int32_t* 
 // T records {x = old column (row to append to), y = entry index in the new
 // rows' CSR}, written in CSR order (deterministic)
 __global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t nrows,
-                         const int64_t* __restrict__ mark, const int64_t* __restrict__ base,
-                         ulonglong2* __restrict__ T) {
+                         int64_t nold, const int64_t* __restrict__ base, ulonglong2* __restrict__ T) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -557,7 +556,7 @@ __global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restri
       int32_t j = 0;
       if (k < rp[q + 1]) {
         j = col[k];
-        ok = mark[j] != 0;
+        ok = j < nold;
       }
       const unsigned m = __ballot_sync(0xffffffffu, ok);
       if (ok) T[w + __popc(m & ((1u << lane) - 1u))] = make_ulonglong2((uint64_t)j, (uint64_t)k);
@@ -580,34 +579,31 @@ __global__ void k_caps(const int64_t* __restrict__ len, int64_t n, int64_t* __re
 
 // Plan of V' = V + N: new length of every row, its capacity, whether it stays
 // (start2 = old start) or needs a new range of `need` entries (start2 = -1).
-__global__ void k_plan_rows(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ start_old,
-                            const int64_t* __restrict__ len_old, const int64_t* __restrict__ cap_old, int64_t nold,
-                            const int32_t* __restrict__ newrows, const int64_t* __restrict__ rpN, int64_t nnew,
-                            const int64_t* __restrict__ hist, int repack, int64_t* __restrict__ start2,
+__global__ void k_plan_rows(const int64_t* __restrict__ start_old, const int64_t* __restrict__ len_old,
+                            const int64_t* __restrict__ cap_old, int64_t nold, const int64_t* __restrict__ rpN,
+                            int64_t nnew, const int64_t* __restrict__ hist, int repack, int64_t* __restrict__ start2,
                             int64_t* __restrict__ len2, int64_t* __restrict__ cap2, int64_t* __restrict__ need) {
   const int64_t tot = nold + nnew;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     if (t < nold) {
-      const int64_t p = pos_old[t];
-      const int64_t L = len_old[t] + hist[p];
-      len2[p] = L;
+      const int64_t L = len_old[t] + hist[t];
+      len2[t] = L;
       if (!repack && L <= cap_old[t]) {
-        start2[p] = start_old[t];
-        cap2[p] = cap_old[t];
-        need[p] = 0;
+        start2[t] = start_old[t];
+        cap2[t] = cap_old[t];
+        need[t] = 0;
       } else {
-        start2[p] = -1;
-        cap2[p] = slack_cap(L);
-        need[p] = cap2[p];
+        start2[t] = -1;
+        cap2[t] = slack_cap(L);
+        need[t] = cap2[t];
       }
     } else {
       const int64_t q = t - nold;
-      const int64_t p = newrows[q];
       const int64_t L = rpN[q + 1] - rpN[q];
-      len2[p] = L;
-      start2[p] = -1;
-      cap2[p] = slack_cap(L);
-      need[p] = cap2[p];
+      len2[t] = L;
+      start2[t] = -1;
+      cap2[t] = slack_cap(L);
+      need[t] = cap2[t];
     }
   }
 }
@@ -617,41 +613,39 @@ __global__ void k_assign_starts(int64_t* __restrict__ start2, const int64_t* __r
     if (start2[i] < 0) start2[i] = base + rel[i];
 }
 
-// old rows: columns remapped to V' positions (in place when the row stays),
-// then the appended transposes of the new rows' entries
-__global__ void k_move_old_rows(const int64_t* __restrict__ pos_old, const int64_t* __restrict__ start_old,
-                                const int64_t* __restrict__ len_old, int64_t nold, const int32_t* col_src,
-                                const double* val_src, const int64_t* __restrict__ start2, int32_t* col_dst,
-                                double* val_dst, const ulonglong2* __restrict__ T, const int64_t* __restrict__ tstart,
+// old rows (internal ids below nold): copied when they move (repack or
+// outgrown slack), then the transposes of the new rows' entries appended;
+// columns are stable internal ids, so rows that gain nothing are untouched
+__global__ void k_move_old_rows(const int64_t* __restrict__ start_old, const int64_t* __restrict__ len_old,
+                                int64_t nold, const int32_t* col_src, const double* val_src,
+                                const int64_t* __restrict__ start2, int32_t* col_dst, double* val_dst,
+                                const ulonglong2* __restrict__ T, const int64_t* __restrict__ tstart,
                                 const int64_t* __restrict__ hist, const int64_t* __restrict__ rpN, int64_t nnew,
-                                const int32_t* __restrict__ newrows, const double* __restrict__ valN) {
+                                const double* __restrict__ valN) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < nold; i += nwarps) {
-    const int64_t p = pos_old[i];
-    const int64_t src = start_old[i], dst = start2[p], len = len_old[i];
+  for (int64_t r = warp; r < nold; r += nwarps) {
+    const int64_t src = start_old[r], dst = start2[r], len = len_old[r];
+    const int64_t tn = hist[r];
     const bool moved = (dst != src) || (col_dst != col_src);
-    // four independent load -> gather -> store chains per lane
-    int64_t k = lane;
-    for (; k + 96 < len; k += 128) {
-      const int32_t j0 = col_src[src + k], j1 = col_src[src + k + 32], j2 = col_src[src + k + 64],
-                    j3 = col_src[src + k + 96];
-      const int64_t p0 = pos_old[j0], p1 = pos_old[j1], p2 = pos_old[j2], p3 = pos_old[j3];
-      if (moved) {
+    if (!moved && tn == 0) continue;
+    if (moved) {
+      int64_t k = lane;
+      for (; k + 96 < len; k += 128) {
+        const int32_t j0 = col_src[src + k], j1 = col_src[src + k + 32], j2 = col_src[src + k + 64],
+                      j3 = col_src[src + k + 96];
         const double v0 = val_src[src + k], v1 = val_src[src + k + 32], v2 = val_src[src + k + 64],
                      v3 = val_src[src + k + 96];
+        col_dst[dst + k] = j0; col_dst[dst + k + 32] = j1; col_dst[dst + k + 64] = j2; col_dst[dst + k + 96] = j3;
         val_dst[dst + k] = v0; val_dst[dst + k + 32] = v1; val_dst[dst + k + 64] = v2; val_dst[dst + k + 96] = v3;
       }
-      col_dst[dst + k] = (int32_t)p0; col_dst[dst + k + 32] = (int32_t)p1;
-      col_dst[dst + k + 64] = (int32_t)p2; col_dst[dst + k + 96] = (int32_t)p3;
+      for (; k < len; k += 32) {
+        col_dst[dst + k] = col_src[src + k];
+        val_dst[dst + k] = val_src[src + k];
+      }
     }
-    for (; k < len; k += 32) {
-      const int32_t j = col_src[src + k];
-      if (moved) val_dst[dst + k] = val_src[src + k];
-      col_dst[dst + k] = (int32_t)pos_old[j];
-    }
-    const int64_t t0 = tstart[p], tn = hist[p];
+    const int64_t t0 = tstart[r];
     for (int64_t k = lane; k < tn; k += 32) {
       const int64_t e = (int64_t)T[t0 + k].y;
       int64_t lo = 0, hi = nnew;
@@ -660,13 +654,13 @@ __global__ void k_move_old_rows(const int64_t* __restrict__ pos_old, const int64
         if (rpN[mid] <= e) lo = mid;
         else hi = mid;
       }
-      col_dst[dst + len + k] = newrows[lo];
+      col_dst[dst + len + k] = (int32_t)(nold + lo);
       val_dst[dst + len + k] = valN[e];
     }
   }
 }
 
-__global__ void k_place_new_rows(const int32_t* __restrict__ newrows, int64_t nnew, const int64_t* __restrict__ rpN,
+__global__ void k_place_new_rows(int64_t nold, int64_t nnew, const int64_t* __restrict__ rpN,
                                  const int32_t* __restrict__ colN, const double* __restrict__ valN,
                                  const int64_t* __restrict__ start2, int32_t* __restrict__ col_dst,
                                  double* __restrict__ val_dst) {
@@ -674,7 +668,7 @@ __global__ void k_place_new_rows(const int32_t* __restrict__ newrows, int64_t nn
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = warp; q < nnew; q += nwarps) {
-    const int64_t dst = start2[newrows[q]];
+    const int64_t dst = start2[nold + q];
     const int64_t b = rpN[q], len = rpN[q + 1] - b;
     for (int64_t k = lane; k < len; k += 32) {
       col_dst[dst + k] = colN[b + k];
@@ -683,11 +677,43 @@ __global__ void k_place_new_rows(const int32_t* __restrict__ newrows, int64_t nn
   }
 }
 
-__global__ void k_move_diag(const int64_t* __restrict__ pos_old, const double* __restrict__ dold, int64_t nold,
-                            double* __restrict__ dnew) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nold; i += (int64_t)gridDim.x * blockDim.x)
-    dnew[pos_old[i]] = dold[i];
+// sorted <-> internal maps of V' and the keys in internal order
+__global__ void k_build_perm(const int64_t* __restrict__ pos_old, const int32_t* __restrict__ s2i_old, int64_t nold,
+                             const int32_t* __restrict__ newrows, int64_t nnew, const ulonglong2* __restrict__ V,
+                             int32_t* __restrict__ s2i, int32_t* __restrict__ i2s, ulonglong2* __restrict__ keys_int) {
+  const int64_t tot = nold + nnew;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < nold) {
+      const int64_t p = pos_old[t];
+      const int32_t id = s2i_old[t];
+      s2i[p] = id;
+      i2s[id] = (int32_t)p;
+    } else {
+      const int64_t q = t - nold;
+      const int32_t p = newrows[q];
+      const int64_t id = nold + q;
+      s2i[p] = (int32_t)id;
+      i2s[id] = p;
+      keys_int[id] = V[p];
+    }
+  }
 }
+
+__global__ void k_iota(int32_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = b[i] = (int32_t)i;
+}
+
+// out[t] = in[idx[t]] for nvec vectors of length n
+__global__ void k_gather_vec(const double* __restrict__ in, const int32_t* __restrict__ idx, int64_t n, int nvec,
+                             double* __restrict__ out) {
+  const int64_t tot = n * nvec;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t / n, i = t % n;
+    out[t] = in[v * n + idx[i]];
+  }
+}
+
 
 // diagonal <D|H|D> (includes e_core)
 __global__ void k_diag(int n, const double* __restrict__ h, const double* __restrict__ eri, double ecore,
@@ -951,14 +977,13 @@ static int64_t read_i64(hci_ctx* ctx, const int64_t* d, hci_status* st) {
   return v;
 }
 
-static hci_status compute_diag(hci_ctx* ctx, int64_t nrows, const int32_t* rowlist, double* out) {
-  Graph& G = ctx->graph;
+static hci_status compute_diag(hci_ctx* ctx, int64_t nrows, const ulonglong2* keys, double* out) {
   const int n = ctx->n;
   prof_tic(ctx, HCI_PH_HDIAG);
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8));
   if (nrows > 0)
     HCI_LAUNCH(k_diag, grid_for(nrows, 128), 128, (size_t)2 * n * n * 8, ctx->st)(
-        n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, bp<ulonglong2>(G.keys), nrows, out, rowlist);
+        n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, keys, nrows, out, nullptr);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_HDIAG);
   return HCI_OK;
@@ -966,7 +991,6 @@ static hci_status compute_diag(hci_ctx* ctx, int64_t nrows, const int32_t* rowli
 
 hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   Graph& G = ctx->graph;
-  IncScratch& S = ctx->inc;
   G.valid = false;
   if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 columns");
   prof_tic(ctx, HCI_PH_GRAPH);
@@ -974,8 +998,15 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
   HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
   HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  // a fresh space: internal ids = sorted positions
+  HCI_TRY(ensure_buf(ctx, G.keys_int, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys_int.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  HCI_TRY(ensure_buf(ctx, G.s2i, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, G.i2s, (size_t)nV * 4));
+  HCI_LAUNCH(k_iota, grid_for(nV, 256), 256, 0, ctx->st)(bp<int32_t>(G.s2i), bp<int32_t>(G.i2s), nV);
   GraphArgs A;
   HCI_TRY(build_space(ctx, nV, A));
+  A.s2i = bp<int32_t>(G.s2i);
   prof_tic(ctx, HCI_PH_GRAPH_ROWS);
   HCI_TRY(ensure_buf(ctx, G.rowlen, (size_t)(nV + 1) * 8));
   HCI_TRY(rows_count(ctx, A, G.rowlen));
@@ -998,11 +1029,11 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val)));
   HCI_LAUNCH(k_row_values<false>, grid_for(nV * 32, 256), 256, 0, ctx->st)(
       nullptr, nV, bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen), bp<int32_t>(G.col), bp<double>(G.val),
-      bp<ulonglong2>(G.keys), A.H);
+      bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_GRAPH_ROWS);
   HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
-  HCI_TRY(compute_diag(ctx, nV, nullptr, bp<double>(G.diag)));
+  HCI_TRY(compute_diag(ctx, nV, bp<ulonglong2>(G.keys_int), bp<double>(G.diag)));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
   G.nV = nV;
@@ -1010,15 +1041,16 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   G.pool_used = used;
   G.pool_cap = (int64_t)(G.col.bytes / 4) < (int64_t)(G.val.bytes / 8) ? (int64_t)(G.col.bytes / 4)
                                                                         : (int64_t)(G.val.bytes / 8);
-  (void)S;
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   G.valid = true;
   return HCI_OK;
 }
 
-// V' contains every determinant of the cached space: search only the rows of
-// the new determinants, append their transposes to the old rows (in place
-// where the row's slack allows), remap the old columns to V' positions.
+// V' contains every determinant of the cached space.  Rows and columns of the
+// graph are internal ids (insertion order): old determinants keep theirs and
+// the new ones are numbered after them, so only the new rows are searched,
+// their transposes are appended to the old rows (in place where the row's
+// slack allows), and no stored column changes.
 static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, bool* done) {
   Graph& G = ctx->graph;
   IncScratch& S = ctx->inc;
@@ -1041,16 +1073,16 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   if (miss) return HCI_OK;        // not an extension: full rebuild
   prof_tic(ctx, HCI_PH_GRAPH);
   hci_status hs = HCI_OK;
-  // the old row arrays, keys and diagonal move to the scratch side
+  const int64_t nnew = nV - nold;
+  // keys, maps and row arrays of the old space move to the scratch side
   std::swap(G.keys, S.keys_old);
+  std::swap(G.s2i, S.s2i_old);
   std::swap(G.rowstart, S.rp_old);
   std::swap(G.rowlen, S.len_old);
   std::swap(G.rowcap, S.cap_old);
-  std::swap(G.diag, S.diag_old);
   HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
   HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st));
-  // new rows
-  const int64_t nnew = nV - nold;
+  // new determinants in sorted order, their internal ids nold + q
   HCI_TRY(ensure_buf(ctx, S.flag, (size_t)(2 * nV + 1) * 8));
   int64_t* nflag = bp<int64_t>(S.flag);
   int64_t* npos = nflag + nV;
@@ -1058,8 +1090,20 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(scan_i64(ctx, nflag, npos, nV, dtot));
   HCI_TRY(ensure_buf(ctx, S.newrows, (size_t)nnew * 4));
   HCI_LAUNCH(k_compact_idx, grid_for(nV, 256), 256, 0, st)(nflag, npos, nV, bp<int32_t>(S.newrows));
+  // maps and internal-order keys of V' (old ids and keys unchanged)
+  HCI_TRY(ensure_buf(ctx, G.s2i, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, G.i2s, (size_t)nV * 4));
+  if (G.keys_int.bytes < (size_t)nV * 16) {
+    HCI_TRY(ensure_buf(ctx, S.keys_int_old, (size_t)nV * 16 + (size_t)nV * 4));
+    HCI_CUDA(ctx, cudaMemcpyAsync(S.keys_int_old.p, G.keys_int.p, (size_t)nold * 16, cudaMemcpyDeviceToDevice, st));
+    std::swap(G.keys_int, S.keys_int_old);
+  }
+  HCI_LAUNCH(k_build_perm, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<int32_t>(S.s2i_old), nold,
+                                                          bp<int32_t>(S.newrows), nnew, Vn, bp<int32_t>(G.s2i),
+                                                          bp<int32_t>(G.i2s), bp<ulonglong2>(G.keys_int));
   GraphArgs A;
   HCI_TRY(build_space(ctx, nV, A));
+  A.s2i = bp<int32_t>(G.s2i);
   A.rowlist = bp<int32_t>(S.newrows);
   A.nrows = nnew;
   prof_tic(ctx, HCI_PH_GRAPH_ROWS);
@@ -1074,7 +1118,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(rows_fill(ctx, A, bp<int64_t>(S.rpN), bp<int32_t>(S.colN), bp<double>(S.valN)));
   HCI_LAUNCH(k_row_values<true>, grid_for(nnew * 32, 256), 256, 0, st)(
       bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), nullptr, bp<int32_t>(S.colN), bp<double>(S.valN),
-      bp<ulonglong2>(G.keys), A.H);
+      bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_GRAPH_ROWS);
   // transposed entries for the old rows, sorted by the row they go to
@@ -1082,7 +1126,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(ensure_buf(ctx, S.hist, (size_t)(nV + 1) * 8));
   HCI_CUDA(ctx, cudaMemsetAsync(S.hist.p, 0, (size_t)(nV + 1) * 8, st));
   const int gw = grid_for(nnew * 32, 256);
-  HCI_LAUNCH(k_count_old_cols, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, bp<int64_t>(S.mark),
+  HCI_LAUNCH(k_count_old_cols, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, nold,
                                                 bp<int64_t>(S.cnt), bp<int64_t>(S.hist));
   HCI_TRY(ensure_buf(ctx, S.tbase, (size_t)(nnew + 1) * 8));
   HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.tbase), nnew, dtot));
@@ -1090,14 +1134,14 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_TRY(hs);
   HCI_TRY(ensure_buf(ctx, S.T, (size_t)(nT + 1) * 16));
   HCI_TRY(ensure_buf(ctx, S.T2, (size_t)(nT + 1) * 16));
-  HCI_LAUNCH(k_emit_T, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, bp<int64_t>(S.mark),
-                                        bp<int64_t>(S.tbase), bp<ulonglong2>(S.T));
+  HCI_LAUNCH(k_emit_T, gw, 256, 0, st)(bp<int64_t>(S.rpN), bp<int32_t>(S.colN), nnew, nold, bp<int64_t>(S.tbase),
+                                        bp<ulonglong2>(S.T));
   int bits = 1;
-  while (((int64_t)1 << bits) < nV) ++bits;
+  while (((int64_t)1 << bits) < nold) ++bits;
   HCI_TRY(sort_keys(ctx, bp<uint64_t>(S.T), bp<uint64_t>(S.T2), nT, bits, 0));
   HCI_TRY(ensure_buf(ctx, S.tstart, (size_t)(nV + 1) * 8));
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.hist), bp<int64_t>(S.tstart), nV, dtot));
-  // plan the rows of V' in the pool: stay in place or take a new range
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.hist), bp<int64_t>(S.tstart), nold, dtot));
+  // plan the rows of V' (by internal id) in the pool: stay or take a new range
   HCI_TRY(ensure_buf(ctx, G.rowstart, (size_t)(nV + 1) * 8));
   HCI_TRY(ensure_buf(ctx, G.rowlen, (size_t)(nV + 1) * 8));
   HCI_TRY(ensure_buf(ctx, G.rowcap, (size_t)(nV + 1) * 8));
@@ -1108,9 +1152,8 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   int repack = 0;
   for (int pass = 0; pass < 2; ++pass) {
     HCI_LAUNCH(k_plan_rows, grid_for(nV, 256), 256, 0, st)(
-        bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), bp<int64_t>(S.cap_old), nold,
-        bp<int32_t>(S.newrows), bp<int64_t>(S.rpN), nnew, bp<int64_t>(S.hist), repack, bp<int64_t>(G.rowstart),
-        bp<int64_t>(G.rowlen), bp<int64_t>(G.rowcap), need);
+        bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), bp<int64_t>(S.cap_old), nold, bp<int64_t>(S.rpN), nnew,
+        bp<int64_t>(S.hist), repack, bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen), bp<int64_t>(G.rowcap), need);
     HCI_TRY(scan_i64(ctx, need, rel, nV, dtot));
     total = read_i64(ctx, dtot, &hs);
     HCI_TRY(hs);
@@ -1121,7 +1164,6 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   double* val_dst = bp<double>(G.val);
   int64_t base = G.pool_used;
   if (repack) {
-    // every row moves to a fresh pool sized with headroom
     const int64_t cap = total + total / 4 + 1024;
     HCI_TRY(ensure_buf(ctx, S.col_old, (size_t)cap * 4));
     HCI_TRY(ensure_buf(ctx, S.val_old, (size_t)cap * 8));
@@ -1131,10 +1173,10 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   }
   HCI_LAUNCH(k_assign_starts, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(G.rowstart), rel, nV, base);
   HCI_LAUNCH(k_move_old_rows, grid_for(nold * 32, 256), 256, 0, st)(
-      bp<int64_t>(S.pos_old), bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), nold, bp<int32_t>(G.col),
-      bp<double>(G.val), bp<int64_t>(G.rowstart), col_dst, val_dst, bp<ulonglong2>(S.T), bp<int64_t>(S.tstart),
-      bp<int64_t>(S.hist), bp<int64_t>(S.rpN), nnew, bp<int32_t>(S.newrows), bp<double>(S.valN));
-  HCI_LAUNCH(k_place_new_rows, gw, 256, 0, st)(bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), bp<int32_t>(S.colN),
+      bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), nold, bp<int32_t>(G.col), bp<double>(G.val),
+      bp<int64_t>(G.rowstart), col_dst, val_dst, bp<ulonglong2>(S.T), bp<int64_t>(S.tstart), bp<int64_t>(S.hist),
+      bp<int64_t>(S.rpN), nnew, bp<double>(S.valN));
+  HCI_LAUNCH(k_place_new_rows, gw, 256, 0, st)(nold, nnew, bp<int64_t>(S.rpN), bp<int32_t>(S.colN),
                                                 bp<double>(S.valN), bp<int64_t>(G.rowstart), col_dst, val_dst);
   HCI_CUDA(ctx, cudaGetLastError());
   if (repack) {
@@ -1146,7 +1188,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   } else {
     G.pool_used += total;
   }
-  // logical prefix of the row lengths
+  // logical prefix of the row lengths (internal order)
   HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
   HCI_TRY(scan_i64(ctx, bp<int64_t>(G.rowlen), bp<int64_t>(G.rowptr), nV, dtot));
   HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(G.rowptr), nV, dtot);
@@ -1156,11 +1198,13 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   if (nnz != G.nnz + nnzN + nT)
     return hci_fail(ctx, HCI_ERR_CUDA, "graph_extend: inconsistent sizes %lld != %lld + %lld + %lld", (long long)nnz,
                     (long long)G.nnz, (long long)nnzN, (long long)nT);
-  // diagonal: old values move, new rows are computed
-  HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
-  HCI_LAUNCH(k_move_diag, grid_for(nold, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<double>(S.diag_old), nold,
-                                                           bp<double>(G.diag));
-  HCI_TRY(compute_diag(ctx, nnew, bp<int32_t>(S.newrows), bp<double>(G.diag)));
+  // diagonal: old entries stay, the new ids are computed
+  if (G.diag.bytes < (size_t)nV * 8) {
+    HCI_TRY(ensure_buf(ctx, S.diag_old, (size_t)nV * 8 + (size_t)nV * 4));
+    HCI_CUDA(ctx, cudaMemcpyAsync(S.diag_old.p, G.diag.p, (size_t)nold * 8, cudaMemcpyDeviceToDevice, st));
+    std::swap(G.diag, S.diag_old);
+  }
+  HCI_TRY(compute_diag(ctx, nnew, bp<ulonglong2>(G.keys_int) + nold, bp<double>(G.diag) + nold));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   G.nV = nV;
@@ -1207,11 +1251,32 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
   return HCI_OK;
 }
 
+hci_status to_internal(hci_ctx* ctx, const double* sorted, double* internal, int nvec) {
+  const Graph& G = ctx->graph;
+  HCI_LAUNCH(k_gather_vec, grid_for(G.nV * nvec, 256), 256, 0, ctx->st)(sorted, bp<int32_t>(ctx->graph.i2s), G.nV,
+                                                                        nvec, internal);
+  HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}
+
+hci_status to_sorted(hci_ctx* ctx, const double* internal, double* sorted, int nvec) {
+  const Graph& G = ctx->graph;
+  HCI_LAUNCH(k_gather_vec, grid_for(G.nV * nvec, 256), 256, 0, ctx->st)(internal, bp<int32_t>(ctx->graph.s2i), G.nV,
+                                                                        nvec, sorted);
+  HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}
+
 extern "C" hci_status hci_sigma(hci_ctx* ctx, const uint64_t* keys, int64_t nV, const double* c, double* sigma,
                                 int nvec) {
   if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_sigma: null context");
   if (nV <= 0 || nvec <= 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_sigma: empty space or no vectors");
   if (!keys || !c || !sigma) return hci_fail(ctx, HCI_ERR_INVALID, "hci_sigma: null pointer");
   HCI_TRY(graph_ensure(ctx, keys, nV));
-  return sigma_apply(ctx, c, sigma, nvec);
+  HCI_TRY(ensure_buf(ctx, ctx->d_perm, (size_t)2 * nV * nvec * 8));
+  double* ci = bp<double>(ctx->d_perm);
+  double* si = ci + (int64_t)nV * nvec;
+  HCI_TRY(to_internal(ctx, c, ci, nvec));
+  HCI_TRY(sigma_apply(ctx, ci, si, nvec));
+  return to_sorted(ctx, si, sigma, nvec);
 }

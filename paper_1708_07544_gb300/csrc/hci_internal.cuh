@@ -39,7 +39,9 @@ struct Graph {
   DevBuf val;                // double pool of values
   int64_t pool_used = 0, pool_cap = 0;
   DevBuf diag;               // double [nV]
-  DevBuf keys;               // copy of the space's keys [nV][2]
+  DevBuf keys;               // copy of the space's keys [nV][2], sorted
+  DevBuf keys_int;           // the same keys by internal id (insertion order)
+  DevBuf s2i, i2s;           // int32 maps sorted position <-> internal id
 };
 
 struct Lists {
@@ -58,7 +60,7 @@ struct Lists {
 // Scratch of the incremental graph update (V' = V + new determinants).
 struct IncScratch {
   DevBuf pos_old, mark, flag, newrows, rpN, colN, valN, cnt, hist, tbase, T, T2, tstart, len;
-  DevBuf keys_old, rp_old, col_old, val_old, len_old, cap_old, diag_old;
+  DevBuf keys_old, rp_old, col_old, val_old, len_old, cap_old, diag_old, s2i_old, keys_int_old;
 };
 
 // Per-phase CUDA-event timers (enabled by hci_profile).
@@ -85,7 +87,7 @@ struct hci_ctx {
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval;
   IncScratch inc;
   bool incremental = true;
-  DevBuf d_vb, d_wb, d_diag, d_small, d_part;
+  DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm;
   int64_t last_candidates = 0;
   int64_t st_counts[HCI_ST_COUNT] = {};
   Prof prof;
@@ -151,7 +153,11 @@ hci_status check_sorted(hci_ctx* ctx, const uint64_t* keys, int64_t n, int* ok_h
 // graph.cu
 hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
+// sigma on vectors in internal order (rows/columns of the cached graph)
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec);
+// vectors between the caller's (sorted) order and the graph's internal order
+hci_status to_internal(hci_ctx* ctx, const double* sorted, double* internal, int nvec);
+hci_status to_sorted(hci_ctx* ctx, const double* internal, double* sorted, int nvec);
 
 // device helpers -------------------------------------------------------------
 __device__ __forceinline__ int popc64(uint64_t x) { return __popcll(x); }

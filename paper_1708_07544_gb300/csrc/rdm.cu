@@ -328,9 +328,14 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 56);
   HCI_CUDA(ctx, cudaMemsetAsync(queue, 0, 8, st));
-  HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, V, nV, c, bp<int64_t>(ctx->graph.rowptr),
+  // the connections are stored by internal id
+  HCI_TRY(ensure_buf(ctx, ctx->d_perm, (size_t)nV * 8));
+  double* ci = bp<double>(ctx->d_perm);
+  HCI_TRY(to_internal(ctx, c, ci, 1));
+  HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
+                                                         bp<int64_t>(ctx->graph.rowptr),
                                                          bp<int64_t>(ctx->graph.rowstart),
-                                                   bp<int32_t>(ctx->graph.col), rdm1, rdm2, queue);
+                                                         bp<int32_t>(ctx->graph.col), rdm1, rdm2, queue);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
