@@ -80,13 +80,20 @@ __global__ void k_swap_keys(const ulonglong2* __restrict__ in, int64_t n, ulongl
 // ib[permb[k]] = beta group of position k
 __global__ void k_perm_b(const ulonglong2* __restrict__ bkeys, int64_t n, const ulonglong2* __restrict__ V,
                          const int32_t* __restrict__ bgroup_of_pos, int32_t* __restrict__ permb,
-                         int32_t* __restrict__ ib) {
+                         int32_t* __restrict__ ib, int32_t* __restrict__ posb, uint64_t* __restrict__ ba) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     ulonglong2 s = bkeys[k];
     int64_t j = lower_bound_k(V, n, make_ulonglong2(s.y, s.x));
     permb[k] = (int32_t)j;
     ib[j] = bgroup_of_pos[k];
+    posb[j] = (int32_t)k;
+    ba[k] = s.y;
   }
+}
+
+__global__ void k_pack_beta(const ulonglong2* __restrict__ V, int64_t n, uint64_t* __restrict__ vb) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    vb[i] = V[i].y;
 }
 
 // Open-addressing hash set of the distinct strings (value = group index),
@@ -234,6 +241,9 @@ struct GraphArgs {
   const int32_t* ib;       // beta group of each det
   const int64_t* gb;       // beta group starts (beta-major positions) [nub+1]
   const int32_t* permb;    // beta-major position -> det
+  const uint64_t* vb;      // beta string of each det, alpha-major order (packed)
+  const uint64_t* ba;      // alpha string of each det, beta-major order (packed)
+  const int32_t* posb;     // det -> its beta-major position
   const int64_t* anbr_ptr; // single-excitation neighbours of each distinct alpha string
   const int32_t* anbr;
   const int64_t* bnbr_ptr; // ... of each distinct beta string
@@ -320,8 +330,8 @@ __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, in
         }
         const int64_t pos = s_start[lo] + (v - s_pref[lo]);
         uint64_t other;
-        if (BETA) { j = A.permb[pos]; other = A.bk[pos].y; }
-        else { j = pos; other = A.V[pos].y; }
+        if (BETA) { j = A.permb[pos]; other = A.ba[pos]; }
+        else { j = pos; other = A.vb[pos]; }
         ok = __popcll(mine ^ other) == 2;
       }
       visit<FILL>(A, ki, j, ok, w);
@@ -340,12 +350,12 @@ __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, in
           int64_t lo = 0, hi = sz2;
           while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            const uint64_t x = BETA ? A.bk[st2 + mid].y : A.V[st2 + mid].y;
+            const uint64_t x = BETA ? A.ba[st2 + mid] : A.vb[st2 + mid];
             if (x < want) lo = mid + 1;
             else hi = mid;
           }
           if (lo < sz2) {
-            const uint64_t x = BETA ? A.bk[st2 + lo].y : A.V[st2 + lo].y;
+            const uint64_t x = BETA ? A.ba[st2 + lo] : A.vb[st2 + lo];
             if (x == want) { ok = true; j = BETA ? A.permb[st2 + lo] : st2 + lo; }
           }
         }
@@ -399,7 +409,7 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
         const int64_t j = j0 + lane;
         bool ok = false;
         if (j < e && j != i) {
-          const int d = __popcll(ki.y ^ A.V[j].y);
+          const int d = __popcll(ki.y ^ A.vb[j]);
           ok = d == 2 || d == 4;
         }
         visit<FILL>(A, ki, j, ok, w);
@@ -409,17 +419,15 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
     {
       const int g = A.ib[i];
       const int64_t b = A.gb[g], e = A.gb[g + 1];
+      const int64_t mypos = A.posb[i];
       for (int64_t k0 = b; k0 < e; k0 += 32) {
         const int64_t k = k0 + lane;
         bool ok = false;
-        int64_t j = -1;
-        if (k < e) {
-          j = A.permb[k];
-          if (j != i) {
-            const int d = __popcll(ki.x ^ A.bk[k].y);
-            ok = d == 2 || d == 4;
-          }
+        if (k < e && k != mypos) {
+          const int d = __popcll(ki.x ^ A.ba[k]);
+          ok = d == 2 || d == 4;
         }
+        const int64_t j = (FILL && ok) ? (int64_t)A.permb[k] : -1;
         visit<FILL>(A, ki, j, ok, w);
       }
     }
@@ -884,8 +892,13 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   HCI_LAUNCH(k_groups, gb, 256, 0, ctx->st)(bp<ulonglong2>(ctx->g_bkeys), nV, flag, excl, bgroup_of_pos,
                                              bp<uint64_t>(ctx->g_ub), bp<int64_t>(ctx->g_gb));
   HCI_LAUNCH(k_set_last, 1, 1, 0, ctx->st)(bp<int64_t>(ctx->g_gb), dtot, nV);
+  HCI_TRY(ensure_buf(ctx, ctx->g_posb, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, ctx->g_vb, (size_t)nV * 8));
+  HCI_TRY(ensure_buf(ctx, ctx->g_ba, (size_t)nV * 8));
   HCI_LAUNCH(k_perm_b, gb, 256, 0, ctx->st)(bp<ulonglong2>(ctx->g_bkeys), nV, V, bgroup_of_pos,
-                                             bp<int32_t>(ctx->g_permb), bp<int32_t>(ctx->g_ib));
+                                             bp<int32_t>(ctx->g_permb), bp<int32_t>(ctx->g_ib),
+                                             bp<int32_t>(ctx->g_posb), bp<uint64_t>(ctx->g_ba));
+  HCI_LAUNCH(k_pack_beta, gb, 256, 0, ctx->st)(V, nV, bp<uint64_t>(ctx->g_vb));
   int64_t nub = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&nub, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaGetLastError());
@@ -936,6 +949,9 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   A.ia = bp<int32_t>(ctx->g_ia); A.ga = bp<int64_t>(ctx->g_ga);
   A.ib = bp<int32_t>(ctx->g_ib); A.gb = bp<int64_t>(ctx->g_gb);
   A.permb = bp<int32_t>(ctx->g_permb);
+  A.vb = bp<uint64_t>(ctx->g_vb);
+  A.ba = bp<uint64_t>(ctx->g_ba);
+  A.posb = bp<int32_t>(ctx->g_posb);
   A.anbr_ptr = bp<int64_t>(ctx->g_nbr_ptr); A.anbr = bp<int32_t>(ctx->g_nbr);
   A.bnbr_ptr = bp<int64_t>(ctx->g_bnbr_ptr); A.bnbr = bp<int32_t>(ctx->g_bnbr);
   A.costa = bp<int64_t>(ctx->g_costa); A.costb = bp<int64_t>(ctx->g_costb);
