@@ -405,14 +405,20 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
     {
       const int g = A.ia[i];
       const int64_t b = A.ga[g], e = A.ga[g + 1];
-      for (int64_t j0 = b; j0 < e; j0 += 32) {
-        const int64_t j = j0 + lane;
-        bool ok = false;
+      for (int64_t j0 = b; j0 < e; j0 += 64) {
+        const int64_t j = j0 + lane, j2 = j + 32;
+        const uint64_t x1 = j < e ? A.vb[j] : 0ull, x2 = j2 < e ? A.vb[j2] : 0ull;
+        bool ok = false, ok2 = false;
         if (j < e && j != i) {
-          const int d = __popcll(ki.y ^ A.vb[j]);
+          const int d = __popcll(ki.y ^ x1);
           ok = d == 2 || d == 4;
         }
+        if (j2 < e && j2 != i) {
+          const int d = __popcll(ki.y ^ x2);
+          ok2 = d == 2 || d == 4;
+        }
         visit<FILL>(A, ki, j, ok, w);
+        if (j0 + 32 < e) visit<FILL>(A, ki, j2, ok2, w);
       }
     }
     // (B) same beta string
@@ -420,15 +426,24 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
       const int g = A.ib[i];
       const int64_t b = A.gb[g], e = A.gb[g + 1];
       const int64_t mypos = A.posb[i];
-      for (int64_t k0 = b; k0 < e; k0 += 32) {
-        const int64_t k = k0 + lane;
-        bool ok = false;
+      for (int64_t k0 = b; k0 < e; k0 += 64) {
+        const int64_t k = k0 + lane, k2 = k + 32;
+        const uint64_t x1 = k < e ? A.ba[k] : 0ull, x2 = k2 < e ? A.ba[k2] : 0ull;
+        bool ok = false, ok2 = false;
         if (k < e && k != mypos) {
-          const int d = __popcll(ki.x ^ A.ba[k]);
+          const int d = __popcll(ki.x ^ x1);
           ok = d == 2 || d == 4;
+        }
+        if (k2 < e && k2 != mypos) {
+          const int d = __popcll(ki.x ^ x2);
+          ok2 = d == 2 || d == 4;
         }
         const int64_t j = (FILL && ok) ? (int64_t)A.permb[k] : -1;
         visit<FILL>(A, ki, j, ok, w);
+        if (k0 + 32 < e) {
+          const int64_t j2 = (FILL && ok2) ? (int64_t)A.permb[k2] : -1;
+          visit<FILL>(A, ki, j2, ok2, w);
+        }
       }
     }
     // (C) single in alpha and single in beta, from the cheaper side
