@@ -122,10 +122,10 @@ class Clocks:
 
 
 # DRAM traffic of one sigma launch per (connection, row), from the ncu
-# capture of k_sigma1 on the pentacene (22e,22o) space (profiles/); traffic
-# grows in proportion to the connections, so it is scaled to the launch.
-# None while the kernel differs from the captured one.
-SIGMA_TRAFFIC_PER_CONN = 12.39
+# capture of k_sigma1 on the pentacene (22e,22o) space (profiles/);
+# traffic grows in proportion to the connections, so it is scaled to the
+# launch.  None while the kernel differs from the captured one.
+SIGMA_TRAFFIC_PER_CONN = 12.38
 
 
 def traffic_per_launch(nnz, nV):

@@ -786,9 +786,11 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
 
 // sigma = diag .* c + offdiag * c ; one warp per row.  In the single-vector
 // path each warp owns a contiguous range of rows holding an equal share of
-// the connections and keeps four independent (col, val, c[col]) chains per
-// lane in flight; the CSR stream is read with evict-first hints so that c
-// stays in L2.
+// the connections and keeps four (col, val, c[col]) loads per lane in
+// flight; the CSR stream is read with evict-first hints so that c stays in
+// L2.  Rows are summed four at a time, so that the cross-lane reduction
+// costs 1.5 FP64 additions per row instead of 8 (the FP64 pipe, 2 DFMA per
+// clock per SM, bounds this kernel).
 __global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ rowptr,
                                                   const int64_t* __restrict__ rowstart, const int32_t* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ diag,
@@ -810,24 +812,42 @@ __global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ r
       while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (rowptr[mid] < x) lo = mid + 1; else hi = mid; }
       r1 = warp == nwarps - 1 ? nV : lo;
     }
-    for (int64_t i = r0; i < r1; ++i) {
-      const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int64_t k = b + lane;
-      for (; k + 96 < e; k += 128) {
-        const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
-                      j3 = __ldcs(col + k + 96);
-        const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
-                     v3 = __ldcs(val + k + 96);
-        a0 = fma(v0, c[j0], a0);
-        a1 = fma(v1, c[j1], a1);
-        a2 = fma(v2, c[j2], a2);
-        a3 = fma(v3, c[j3], a3);
+    for (int64_t g = r0; g < r1; g += 4) {
+      double acc[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        double a = 0.0;
+        const int64_t i = g + r;
+        if (i < r1) {
+          const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
+          int64_t k = b + lane;
+          for (; k + 96 < e; k += 128) {
+            const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
+                          j3 = __ldcs(col + k + 96);
+            const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
+                         v3 = __ldcs(val + k + 96);
+            a = fma(v0, c[j0], a);
+            a = fma(v1, c[j1], a);
+            a = fma(v2, c[j2], a);
+            a = fma(v3, c[j3], a);
+          }
+          for (; k < e; k += 32) a = fma(__ldcs(val + k), c[__ldcs(col + k)], a);
+        }
+        acc[r] = a;
       }
-      for (; k < e; k += 32) a0 = fma(__ldcs(val + k), c[__ldcs(col + k)], a0);
-      double a = (a0 + a1) + (a2 + a3);
-      for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) sigma[i] = fma(diag[i], c[i], a);
+      // four row sums at once: halve the values held per lane across lanes
+      // 16 apart, then 8 apart, then a plain tree over the last 8 lanes
+      const bool h16 = lane & 16, h8 = lane & 8;
+      const double w0 = (h16 ? acc[2] : acc[0]) + __shfl_xor_sync(0xffffffffu, h16 ? acc[0] : acc[2], 16);
+      const double w1 = (h16 ? acc[3] : acc[1]) + __shfl_xor_sync(0xffffffffu, h16 ? acc[1] : acc[3], 16);
+      double u = (h8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, h8 ? w0 : w1, 8);
+      u += __shfl_xor_sync(0xffffffffu, u, 4);
+      u += __shfl_xor_sync(0xffffffffu, u, 2);
+      u += __shfl_xor_sync(0xffffffffu, u, 1);
+      if ((lane & 7) == 0) {
+        const int64_t i = g + (h16 ? 2 : 0) + (h8 ? 1 : 0);
+        if (i < r1) sigma[i] = fma(diag[i], c[i], u);
+      }
     }
   }
 }
