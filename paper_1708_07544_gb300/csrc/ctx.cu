@@ -238,7 +238,8 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
       (s = ensure_buf(ctx, ctx->eri, n * n * n * n * 8)) != HCI_OK ||
       (s = ensure_buf(ctx, ctx->jk_same, n * n * n * 8)) != HCI_OK ||
       (s = ensure_buf(ctx, ctx->j_opp, n * n * n * 8)) != HCI_OK ||
-      (s = ensure_buf(ctx, ctx->lists.single_bound, n * n * 8)) != HCI_OK) {
+      (s = ensure_buf(ctx, ctx->lists.single_bound, n * n * 8)) != HCI_OK ||
+      (s = ensure_buf(ctx, ctx->lists.f_ref, 2 * n * n * 8)) != HCI_OK) {
     snprintf(g_create_err, sizeof g_create_err, "%s", ctx->err);
     hci_destroy(ctx);
     return s;
@@ -251,6 +252,9 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
     HCI_LAUNCH(k_single_bound, (unsigned)((n * n + 255) / 256), 256, 0, ctx->st)(
         norb, bp<double>(ctx->h), bp<double>(ctx->jk_same), bp<double>(ctx->j_opp),
         bp<double>(ctx->lists.single_bound));
+    HCI_LAUNCH(k_fref, (unsigned)((2 * n * n + 255) / 256), 256, 0, ctx->st)(
+        norb, ctx->na, ctx->nb, bp<double>(ctx->h), bp<double>(ctx->jk_same), bp<double>(ctx->j_opp),
+        bp<double>(ctx->lists.f_ref));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
@@ -323,10 +327,6 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
                                                          bp<double>(L.same_mag), bp<uint16_t>(L.same_tgt));
     HCI_CUDA(ctx, cudaGetLastError());
   }
-  HCI_TRY(ensure_buf(ctx, L.f_ref, (size_t)2 * n * n * 8));
-  HCI_LAUNCH(k_fref, (2 * n * n + 255) / 256, 256, 0, ctx->st)(n, ctx->na, ctx->nb, bp<double>(ctx->h),
-                                                              bp<double>(ctx->jk_same), bp<double>(ctx->j_opp),
-                                                              bp<double>(L.f_ref));
   HCI_TRY(ensure_buf(ctx, L.list_max, (size_t)(n * n + L.npair_same + 1) * 8));
   HCI_LAUNCH(k_gather_first, (n * n + 255) / 256, 256, 0, ctx->st)(bp<double>(L.opp_mag), n * n, L.len_opp,
                                                                   bp<double>(L.list_max));

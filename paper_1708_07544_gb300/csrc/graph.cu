@@ -134,39 +134,6 @@ __device__ __forceinline__ int32_t hash_find(const unsigned long long* __restric
   return -1;
 }
 
-// single-excitation neighbours (within the distinct strings) of each
-// distinct string; count pass (out == nullptr) or fill pass
-__global__ void k_alpha_nbrs(int n, const uint64_t* __restrict__ ua, int64_t nua, const int64_t* __restrict__ ptr,
-                             int64_t* __restrict__ cnt, int32_t* __restrict__ out,
-                             const unsigned long long* __restrict__ tab, const int32_t* __restrict__ tval,
-                             uint64_t mask) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t g = warp; g < nua; g += nwarps) {
-    uint64_t s = ua[g];
-    int64_t w = out ? ptr[g] : 0;
-    int64_t c = 0;
-    const int npairs = n * n;
-    for (int b0 = 0; b0 < npairs; b0 += 32) {
-      int t = b0 + lane;
-      bool hit = false;
-      int32_t idx = -1;
-      if (t < npairs) {
-        int p = t / n, r = t % n;
-        if (((s >> p) & 1ull) && !((s >> r) & 1ull)) {
-          idx = hash_find(tab, tval, mask, s ^ (1ull << p) ^ (1ull << r));
-          hit = idx >= 0;
-        }
-      }
-      unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (out && hit) out[w + c + __popc(m & ((1u << lane) - 1u))] = idx;
-      c += __popc(m);
-    }
-    if (!out && lane == 0) cnt[g] = c;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Slater-Condon element <D_i|H|D_j> for a known connection
 // ---------------------------------------------------------------------------
@@ -174,23 +141,30 @@ struct HamView {
   int n;
   const double* h;
   const double* eri;
-  const double* jk_same;
-  const double* j_opp;
+  const double* jk_same;   // [p][r][k] (pr|kk) - (pk|kr)
+  const double* j_opp;     // [p][r][k] (pr|kk)
+  const double* f_ref;     // [spin][p][r] single p->r of the aufbau determinant
+  uint64_t ref_a, ref_b;   // aufbau alpha / beta strings
 };
 
-__device__ __forceinline__ double eri4(const HamView& H, int p, int q, int r, int s) {
-  return H.eri[(((int64_t)p * H.n + q) * H.n + r) * H.n + s];
+__device__ __forceinline__ double eri4(const HamView& H, int p, int r, int q, int s) {
+  return H.eri[(((int64_t)p * H.n + r) * H.n + q) * H.n + s];
 }
 
-// single p->r in spin string sj (other spin string oj), both of D_j
-__device__ __forceinline__ double single_el(const HamView& H, uint64_t sj, uint64_t oj, int p, int r) {
-  double v = H.h[p * H.n + r];
+// single p->r in spin string sj (other spin string oj), both of D_j; spin 0
+// = alpha.  h_pr + sum_{k in sj} [(pr|kk) - (pk|kr)] + sum_{k in oj} (pr|kk)
+// is taken as the aufbau determinant's value plus the terms of the orbitals
+// where sj and oj differ from the aufbau strings (a few for a selected
+// determinant, instead of a pass over all n orbitals).
+__device__ __forceinline__ double single_el(const HamView& H, uint64_t sj, uint64_t oj, int p, int r, int spin) {
+  const uint64_t rs = spin ? H.ref_b : H.ref_a, ro = spin ? H.ref_a : H.ref_b;
+  double v = H.f_ref[((int64_t)spin * H.n + p) * H.n + r];
   const double* js = H.jk_same + ((int64_t)p * H.n + r) * H.n;
   const double* jo = H.j_opp + ((int64_t)p * H.n + r) * H.n;
-  for (int k = 0; k < H.n; ++k) {
-    if ((sj >> k) & 1ull) v += js[k];
-    if ((oj >> k) & 1ull) v += jo[k];
-  }
+  for (uint64_t m = sj & ~rs; m; m &= m - 1) v += js[__ffsll((long long)m) - 1];
+  for (uint64_t m = rs & ~sj; m; m &= m - 1) v -= js[__ffsll((long long)m) - 1];
+  for (uint64_t m = oj & ~ro; m; m &= m - 1) v += jo[__ffsll((long long)m) - 1];
+  for (uint64_t m = ro & ~oj; m; m &= m - 1) v -= jo[__ffsll((long long)m) - 1];
   return exc_phase(sj, p, r) * v;
 }
 
@@ -212,14 +186,14 @@ __device__ double connection_el(const HamView& H, ulonglong2 ki, ulonglong2 kj) 
   if (da == 0) {
     if (db == 2) {
       int p = __ffsll((long long)(kj.y & xb)) - 1, r = __ffsll((long long)(ki.y & xb)) - 1;
-      return single_el(H, kj.y, kj.x, p, r);
+      return single_el(H, kj.y, kj.x, p, r, 1);
     }
     return same_double_el(H, kj.y, xb);
   }
   if (db == 0) {
     if (da == 2) {
       int p = __ffsll((long long)(kj.x & xa)) - 1, r = __ffsll((long long)(ki.x & xa)) - 1;
-      return single_el(H, kj.x, kj.y, p, r);
+      return single_el(H, kj.x, kj.y, p, r, 0);
     }
     return same_double_el(H, kj.x, xa);
   }
@@ -494,6 +468,40 @@ __global__ void __launch_bounds__(256) k_row_values(const int32_t* __restrict__ 
   }
 }
 
+// single-excitation neighbours (within the distinct strings) of each
+// distinct string with nocc electrons; count pass (out == nullptr) or fill
+// pass.  The nocc * (n - nocc) occupied -> empty pairs are enumerated from
+// per-warp occupied / empty lists, p-major, so each list is in (p, r) order.
+__global__ void __launch_bounds__(256) k_alpha_nbrs(int n, int nocc, const uint64_t* __restrict__ ua, int64_t nua,
+                                                    const int64_t* __restrict__ ptr, int64_t* __restrict__ cnt,
+                                                    int32_t* __restrict__ out,
+                                                    const unsigned long long* __restrict__ tab,
+                                                    const int32_t* __restrict__ tval, uint64_t mask) {
+  __shared__ int s_occ[8][HCI_MAXORB];
+  __shared__ int s_vir[8][HCI_MAXORB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nvir = n - nocc, L = nocc * nvir;
+  for (int64_t g = warp; g < nua; g += nwarps) {
+    const uint64_t s = ua[g];
+    occ_vir_lists(s, n, s_occ[wid], s_vir[wid]);
+    int64_t w = out ? ptr[g] : 0;
+    int64_t c = 0;
+    for (int t0 = 0; t0 < L; t0 += 32) {
+      const int t = t0 + lane;
+      int32_t idx = -1;
+      if (t < L) idx = hash_find(tab, tval, mask, s ^ (1ull << s_occ[wid][t / nvir]) ^ (1ull << s_vir[wid][t % nvir]));
+      const bool hit = idx >= 0;
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (out && hit) out[w + c + __popc(m & ((1u << lane) - 1u))] = idx;
+      c += __popc(m);
+    }
+    if (!out && lane == 0) cnt[g] = c;
+    __syncwarp();
+  }
+}
+
 // cost[u] = sum over the neighbours v of string u of min(scan, lookup) cost
 __global__ void k_nbr_cost(const int64_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                            const int64_t* __restrict__ gs, int64_t nu, int L, int64_t* __restrict__ cost) {
@@ -593,7 +601,7 @@ __global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restri
 // pools; rowlen <= rowcap entries are live.  Slack lets later updates append
 // in place; rows that outgrow it move to the end of the pool.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t slack_cap(int64_t len) { return len + len / 8 + 8; }
+__device__ __forceinline__ int64_t slack_cap(int64_t len) { return len + len / 4 + 8; }
 
 __global__ void k_caps(const int64_t* __restrict__ len, int64_t n, int64_t* __restrict__ cap) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -949,6 +957,7 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   const int64_t nu[2] = {nua, nub};
   // lookups on the alpha side generate beta singles and vice versa
   const int Lside[2] = {ctx->nb * (n - ctx->nb), ctx->na * (n - ctx->na)};
+  const int nel[2] = {ctx->na, ctx->nb};
   for (int s = 0; s < 2; ++s) {
     uint64_t tsize = 64;
     while (tsize < (uint64_t)(2 * nu[s] + 2)) tsize <<= 1;
@@ -961,7 +970,7 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
     HCI_TRY(ensure_buf(ctx, *ptrs[s], (size_t)(nu[s] + 1) * 8));
     HCI_TRY(ensure_buf(ctx, *costs[s], (size_t)(nu[s] + 1) * 8));
     const int gw = grid_for(nu[s] * 32, 256);
-    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], nullptr, bp<int64_t>(ctx->g_cnt), nullptr,
+    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, nel[s], uniq[s], nu[s], nullptr, bp<int64_t>(ctx->g_cnt), nullptr,
                                                    bp<unsigned long long>(ctx->g_htab), bp<int32_t>(ctx->g_hval),
                                                    tsize - 1);
     HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->g_cnt), bp<int64_t>(*ptrs[s]), nu[s], dtot));
@@ -970,7 +979,7 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
     HCI_CUDA(ctx, cudaMemcpyAsync(&nn, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
     HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
     HCI_TRY(ensure_buf(ctx, *lists[s], (size_t)(nn + 1) * 4));
-    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, uniq[s], nu[s], bp<int64_t>(*ptrs[s]), nullptr,
+    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, nel[s], uniq[s], nu[s], bp<int64_t>(*ptrs[s]), nullptr,
                                                    bp<int32_t>(*lists[s]), bp<unsigned long long>(ctx->g_htab),
                                                    bp<int32_t>(ctx->g_hval), tsize - 1);
     HCI_LAUNCH(k_nbr_cost, gw, 256, 0, ctx->st)(bp<int64_t>(*ptrs[s]), bp<int32_t>(*lists[s]), gstart[s], nu[s],
@@ -990,7 +999,14 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   A.anbr_ptr = bp<int64_t>(ctx->g_nbr_ptr); A.anbr = bp<int32_t>(ctx->g_nbr);
   A.bnbr_ptr = bp<int64_t>(ctx->g_bnbr_ptr); A.bnbr = bp<int32_t>(ctx->g_bnbr);
   A.costa = bp<int64_t>(ctx->g_costa); A.costb = bp<int64_t>(ctx->g_costb);
-  A.H = HamView{n, bp<double>(ctx->h), bp<double>(ctx->eri), bp<double>(ctx->jk_same), bp<double>(ctx->j_opp)};
+  A.H = HamView{n,
+                bp<double>(ctx->h),
+                bp<double>(ctx->eri),
+                bp<double>(ctx->jk_same),
+                bp<double>(ctx->j_opp),
+                bp<double>(ctx->lists.f_ref),
+                ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull),
+                ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull)};
   A.queue = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 48);
   A.rowlist = nullptr;
   A.nrows = nV;

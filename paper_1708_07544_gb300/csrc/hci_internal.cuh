@@ -53,7 +53,7 @@ struct Lists {
   DevBuf same_mag, same_tgt;         // [npair_same][len_same]
   DevBuf single_bound;               // [n*n] upper bound of |H| for single p->r
   DevBuf list_max;                   // [n*n + npair_same] first (largest) magnitude of each list
-  DevBuf f_ref;                      // [2][n][n] single-excitation rows of the aufbau determinant
+  DevBuf f_ref;                      // [2][n][n] single-excitation rows of the aufbau determinant (set at create)
   double max_opp = 0, max_same = 0, max_single = 0;
 };
 
