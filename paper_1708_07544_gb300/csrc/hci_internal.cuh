@@ -82,7 +82,7 @@ struct hci_ctx {
   Lists lists;
   Graph graph;
   // scratch
-  DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items, s_rdmw;
+  DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items, s_rdmw, s_rdmh;
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
   IncScratch inc;

@@ -13,8 +13,9 @@
 //   double a->c, b->d (holes a<b, particles c<d in one spin, or a->c alpha
 //   and b->d beta): rdm2[c,a,d,b] += w; rdm2[d,b,c,a] += w;
 //     same spin only: rdm2[c,b,d,a] -= w; rdm2[d,a,c,b] -= w
-// Both orientations (i,j) and (j,i) are stored in the graph, so the RDMs
-// come out symmetric.  The diagonal part is reduced through the weighted
+// The graph stores both orientations (i,j) and (j,i) of a pair; one is
+// accumulated and the other added as its transpose.  The diagonal part is
+// reduced through the weighted
 // occupation correlation M[sp][tq] = sum_i c_i^2 n_sp(i) n_tq(i), folded over
 // the alpha and beta string groups of the graph.
 #include "hci_internal.cuh"
@@ -27,12 +28,27 @@ __device__ __forceinline__ void add2(double* r2, int n, int p, int q, int r, int
   atomicAdd(&r2[(((int64_t)p * n + q) * n + r) * n + s], v);
 }
 
+// One orientation of every connected pair (column id above the row id): the
+// other orientation contributes the transpose (p,q,r,s) -> (q,p,s,r), added
+// in k_rdm_finish.  Doubles go to Hh (n^4).  A single a -> b of spin S in
+// D_j with weight w adds w to S1[S][b][a]; its spectator terms
+// sum w n_k(D_j) are split into the aufbau occupation (expanded in
+// k_rdm_finish) plus the orbitals where D_j's strings differ from the
+// aufbau ones, accumulated in Dt[b][a][k] (both spins) and Dx[b][a][k]
+// (same spin, for the exchange terms).
+struct RdmAcc {
+  double* Hh;
+  double* S1;
+  double* Dt;
+  double* Dx;
+  uint64_t ref_a, ref_b;
+};
+
 __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulonglong2* __restrict__ V, int64_t nV,
                                                               const double* __restrict__ c,
                                                               const int64_t* __restrict__ rowptr,
                                                               const int64_t* __restrict__ rowstart,
-                                                              const int32_t* __restrict__ col, double* __restrict__ r1,
-                                                              double* __restrict__ r2,
+                                                              const int32_t* __restrict__ col, RdmAcc R,
                                                               unsigned long long* __restrict__ queue) {
   const int lane = threadIdx.x & 31;
   while (true) {
@@ -45,6 +61,7 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
     const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
     for (int64_t k = b + lane; k < e; k += 32) {
       const int64_t j = col[k];
+      if (j <= i) continue;
       const ulonglong2 kj = V[j];
       const double cc = ci * c[j];
       if (cc == 0.0) continue;
@@ -58,24 +75,22 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
         const int a = __ffsll((long long)(sj & x)) - 1;
         const int bb = __ffsll((long long)(x & ~sj)) - 1;
         const double w = cc * exc_phase(sj, a, bb);
-        atomicAdd(&r1[a + (int64_t)bb * n], w);
-        // spectators of the same spin (excluding a) and of the other spin
-        uint64_t sp = sj & ~(1ull << a);
-        while (sp) {
-          const int kk = __ffsll((long long)sp) - 1;
-          sp &= sp - 1;
-          add2(r2, n, bb, a, kk, kk, w);
-          add2(r2, n, kk, kk, bb, a, w);
-          add2(r2, n, kk, a, bb, kk, -w);
-          add2(r2, n, bb, kk, kk, a, -w);
+        atomicAdd(&R.S1[((int64_t)S * n + bb) * n + a], w);
+        const uint64_t rs = S == 0 ? R.ref_a : R.ref_b, ro = S == 0 ? R.ref_b : R.ref_a;
+        double* dt = R.Dt + ((int64_t)bb * n + a) * n;
+        double* dx = R.Dx + ((int64_t)bb * n + a) * n;
+        for (uint64_t m = sj & ~rs; m; m &= m - 1) {
+          const int kk = __ffsll((long long)m) - 1;
+          atomicAdd(dt + kk, w);
+          atomicAdd(dx + kk, w);
         }
-        uint64_t so = oj;
-        while (so) {
-          const int kk = __ffsll((long long)so) - 1;
-          so &= so - 1;
-          add2(r2, n, bb, a, kk, kk, w);
-          add2(r2, n, kk, kk, bb, a, w);
+        for (uint64_t m = rs & ~sj; m; m &= m - 1) {
+          const int kk = __ffsll((long long)m) - 1;
+          atomicAdd(dt + kk, -w);
+          atomicAdd(dx + kk, -w);
         }
+        for (uint64_t m = oj & ~ro; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, w);
+        for (uint64_t m = ro & ~oj; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, -w);
       } else if (da == 4 || db == 4) {
         const uint64_t sj = da == 4 ? kj.x : kj.y;
         const uint64_t x = da == 4 ? xa : xb;
@@ -87,18 +102,55 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
         const double s1 = exc_phase(sj, a, cp);
         const uint64_t t = sj ^ (1ull << a) ^ (1ull << cp);
         const double w = cc * s1 * exc_phase(t, bh, d);
-        add2(r2, n, cp, a, d, bh, w);
-        add2(r2, n, d, bh, cp, a, w);
-        add2(r2, n, cp, bh, d, a, -w);
-        add2(r2, n, d, a, cp, bh, -w);
+        add2(R.Hh, n, cp, a, d, bh, w);
+        add2(R.Hh, n, d, bh, cp, a, w);
+        add2(R.Hh, n, cp, bh, d, a, -w);
+        add2(R.Hh, n, d, a, cp, bh, -w);
       } else {
         // alpha a -> c, beta b -> d
         const int a = __ffsll((long long)(kj.x & xa)) - 1, cp = __ffsll((long long)(ki.x & xa)) - 1;
         const int bh = __ffsll((long long)(kj.y & xb)) - 1, d = __ffsll((long long)(ki.y & xb)) - 1;
         const double w = cc * exc_phase(kj.x, a, cp) * exc_phase(kj.y, bh, d);
-        add2(r2, n, cp, a, d, bh, w);
-        add2(r2, n, d, bh, cp, a, w);
+        add2(R.Hh, n, cp, a, d, bh, w);
+        add2(R.Hh, n, d, bh, cp, a, w);
       }
+    }
+  }
+}
+
+// Single-excitation spectator sums: Xt[b][a][k] over both spins,
+// Xx[b][a][k] over the excitation's own spin (spectator k != a).
+__device__ __forceinline__ double rdm_xt(const RdmAcc& R, int n, int b, int a, int k) {
+  const int64_t ba = (int64_t)b * n + a;
+  const double s = R.S1[ba] + R.S1[(int64_t)n * n + ba];
+  const int occ = (int)((R.ref_a >> k) & 1ull) + (int)((R.ref_b >> k) & 1ull) - (k == a);
+  return s * occ + R.Dt[ba * n + k];
+}
+__device__ __forceinline__ double rdm_xx(const RdmAcc& R, int n, int b, int a, int k) {
+  const int64_t ba = (int64_t)b * n + a;
+  const int oa = (int)((R.ref_a >> k) & 1ull) - (k == a), ob = (int)((R.ref_b >> k) & 1ull) - (k == a);
+  return R.S1[ba] * oa + R.S1[(int64_t)n * n + ba] * ob + R.Dx[ba * n + k];
+}
+// the single-excitation terms of one orientation at (p,q,r,s)
+__device__ __forceinline__ double rdm_single_terms(const RdmAcc& R, int n, int p, int q, int r, int s) {
+  double v = 0.0;
+  if (r == s) v += rdm_xt(R, n, p, q, r);
+  if (p == q) v += rdm_xt(R, n, r, s, p);
+  if (s == p) v -= rdm_xx(R, n, r, q, p);
+  if (q == r) v -= rdm_xx(R, n, p, s, q);
+  return v;
+}
+
+// rdm2 += Hh + Hh^T + single terms and their transpose; rdm1 += S1 + S1^T
+__global__ void k_rdm_finish(int n, RdmAcc R, double* __restrict__ r1, double* __restrict__ r2) {
+  const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(t % n), r = (int)((t / n) % n), q = (int)((t / n2) % n), p = (int)(t / (n2 * n));
+    const int64_t tt = (((int64_t)q * n + p) * n + s) * n + r;
+    r2[t] += R.Hh[t] + R.Hh[tt] + rdm_single_terms(R, n, p, q, r, s) + rdm_single_terms(R, n, q, p, s, r);
+    if (t < n2) {
+      const int pp = (int)(t / n), qq = (int)(t % n);
+      r1[t] += R.S1[t] + R.S1[n2 + t] + R.S1[(int64_t)qq * n + pp] + R.S1[n2 + (int64_t)qq * n + pp];
     }
   }
 }
@@ -332,10 +384,21 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   HCI_TRY(ensure_buf(ctx, ctx->d_perm, (size_t)nV * 8));
   double* ci = bp<double>(ctx->d_perm);
   HCI_TRY(to_internal(ctx, c, ci, 1));
+  const size_t n3 = n2 * n;
+  HCI_TRY(ensure_buf(ctx, ctx->s_rdmh, (n4 + 2 * n2 + 2 * n3) * 8));
+  HCI_CUDA(ctx, cudaMemsetAsync(ctx->s_rdmh.p, 0, (n4 + 2 * n2 + 2 * n3) * 8, st));
+  RdmAcc R;
+  R.Hh = bp<double>(ctx->s_rdmh);
+  R.S1 = R.Hh + n4;
+  R.Dt = R.S1 + 2 * n2;
+  R.Dx = R.Dt + n3;
+  R.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
+  R.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
   HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
                                                          bp<int64_t>(ctx->graph.rowptr),
                                                          bp<int64_t>(ctx->graph.rowstart),
-                                                         bp<int32_t>(ctx->graph.col), rdm1, rdm2, queue);
+                                                         bp<int32_t>(ctx->graph.col), R, queue);
+  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, rdm1, rdm2);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));

@@ -178,11 +178,14 @@ def test_davidson_matches_oracle(pkg, name, make, nv):
     assert np.abs(c.cpu().numpy() - c_ref).max() < 1e-7
 
 
-def test_rdm_matches_oracle_random_vector(pkg):
-    inst = hi.random_tiny(6, 3, 3, 77)
-    keys = hi.random_det_keys(6, 3, 3, 250, seed=78)
+@pytest.mark.parametrize("norb,na,nb", [(6, 3, 3), (7, 4, 2), (7, 1, 3)])
+def test_rdm_matches_oracle_random_vector(pkg, norb, na, nb):
+    """Every element of both RDMs for a random vector on a random space,
+    closed and open shell (alpha and beta aufbau strings differ)."""
+    inst = hi.random_tiny(norb, na, nb, 77)
+    keys = hi.random_det_keys(norb, na, nb, 250, seed=78)
     c = hi.random_vector(len(keys), seed=79)
-    r1o, r2o = oracle.rdm12(6, keys, c)
+    r1o, r2o = oracle.rdm12(norb, keys, c)
     with solver(pkg, inst) as s:
         r1, r2 = s.rdm12(dev_keys(keys), torch.tensor(c).cuda())
     assert np.abs(r1.cpu().numpy() - r1o).max() < RDM_TOL
