@@ -16,13 +16,14 @@ constexpr int DBLOCK = 256;
 
 struct DavDev {
   double G[LDG * LDG];
+  double Qp[LDG * LDG];   // eigenvectors of the previous subspace matrix (kq x kq)
   double y[LDG];
   double dots[LDG];
   double theta;
   double rnorm2;
   double nrm2;
   int amax_idx;
-  int pad;
+  int kq;                 // size of Qp (0: none)
 };
 
 // partial[b][j] = sum over this block's elements of V_j . w (j < k)
@@ -81,17 +82,43 @@ __global__ void k_set_gcol(DavDev* d, int col) {
 // sweep is k-1 rounds of parallel row and column updates.  An off-diagonal
 // element too small to change either diagonal partner in floating point
 // (even scaled by 100) is zeroed; the sweeps stop when a sweep rotates none.
+//
+// When the matrix is the previous one bordered by one row and column, the
+// sweeps start from the previous eigenvectors Q0 = diag(Qp, 1): Q0^T G Q0 is
+// diagonal but for its last row and column, and takes a few sweeps instead
+// of a full diagonalisation.
 __global__ void k_jacobi(DavDev* d, int k) {
   __shared__ double A[32][33];
   __shared__ double Q[32][33];
+  __shared__ double T[32][33];
   __shared__ double rc[16], rs[16];
   __shared__ int rp[16], rq[16];
   const int l = threadIdx.x;
+  const bool warm = k > 1 && d->kq == k - 1;
   for (int j = 0; j < 32; ++j) {
     A[l][j] = (l < k && j < k) ? d->G[l * LDG + j] : 0.0;
-    Q[l][j] = (l == j) ? 1.0 : 0.0;
+    double q0 = (l == j) ? 1.0 : 0.0;
+    if (warm && l < k - 1 && j < k - 1) q0 = d->Qp[l * LDG + j];
+    Q[l][j] = q0;
   }
   __syncwarp();
+  if (warm) {
+    // T = G Q0 (lane = row), then A = Q0^T T (lane = column)
+    if (l < k)
+      for (int j = 0; j < k; ++j) {
+        double t = 0.0;
+        for (int m = 0; m < k; ++m) t = fma(A[l][m], Q[m][j], t);
+        T[l][j] = t;
+      }
+    __syncwarp();
+    if (l < k)
+      for (int i = 0; i < k; ++i) {
+        double t = 0.0;
+        for (int m = 0; m < k; ++m) t = fma(Q[m][i], T[m][l], t);
+        A[i][l] = t;
+      }
+    __syncwarp();
+  }
   const int m = (k + 1) & ~1;          // even number of players (index k is a dummy when k is odd)
   const int npairs = m / 2;
   for (int sweep = 0; sweep < 50 && k > 1; ++sweep) {
@@ -168,6 +195,9 @@ __global__ void k_jacobi(DavDev* d, int k) {
   __syncwarp();
   const int mi = s_m;
   if (l < LDG) d->y[l] = (l < k) ? Q[l][mi] : 0.0;
+  for (int j = 0; j < k; ++j)
+    if (l < k) d->Qp[l * LDG + j] = Q[l][j];
+  if (l == 0) d->kq = k;
 }
 
 // x = V y, wy = W y, r = wy - theta x, t = r / (theta - diag) (guarded),

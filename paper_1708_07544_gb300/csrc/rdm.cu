@@ -156,64 +156,87 @@ __global__ void k_rdm_finish(int n, RdmAcc R, double* __restrict__ r1, double* _
 }
 
 // M[s*n+p][t*n+q] = sum_i c_i^2 n_sp(i) n_tq(i), folded over the string
-// groups of the cached graph without atomics.
-//  1. one warp per alpha group g: W_g = sum_{i in g} c_i^2 and
-//     v_g[q] = sum_{i in g} c_i^2 n_q(beta_i) (warp reductions); one warp per
-//     beta group h: Wb_h = sum_{i in h} c_i^2.
+// groups of the cached graph:
+//  1. W_g = sum_{i in g} c_i^2 and v_g[q] = sum_{i in g} c_i^2 n_q(beta_i)
+//     per alpha group g, Wb_h = sum_{i in h} c_i^2 per beta group h.
 //  2. one thread per M entry and block per slice of groups: alpha-alpha
 //     entries sum W_g over groups with p, q in alpha_g, alpha-beta entries
 //     sum v_g[q] over groups with p in alpha_g, beta-beta entries sum Wb_h;
 //     the slices' partial M are added in a fixed order.
-__global__ void k_group_weights(int n, const ulonglong2* __restrict__ V, const double* __restrict__ c,
-                                const int64_t* __restrict__ ga, int64_t nua, const int32_t* __restrict__ permb,
-                                const int64_t* __restrict__ gb, int64_t nub, double* __restrict__ Wa,
-                                double* __restrict__ va, double* __restrict__ Wb) {
-  // lane q accumulates orbitals q and q + 32 over the members in order
-  // (broadcast loads, no cross-lane reduction)
+// Step 1 cuts the determinants (alpha-major) and the beta-major positions
+// into chunks of GW_CH consecutive members, one warp per chunk, so that a
+// group holding a large share of the space is spread over many warps; each
+// warp adds its partial sums to the groups it touched with atomics.
+constexpr int GW_CH = 256;
+
+__global__ void __launch_bounds__(256) k_group_weights(int n, const ulonglong2* __restrict__ V,
+                                                       const double* __restrict__ c, const int32_t* __restrict__ ia,
+                                                       int64_t nV, const int32_t* __restrict__ permb,
+                                                       const int32_t* __restrict__ ib, double* __restrict__ Wa,
+                                                       double* __restrict__ va, double* __restrict__ Wb) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t g = warp; g < nua + nub; g += nwarps) {
-    if (g < nua) {
-      double v0 = 0.0, v1 = 0.0, W = 0.0;
-      const int64_t b = ga[g], e = ga[g + 1];
-      int64_t i = b;
-      for (; i + 8 <= e; i += 8) {
+  const int64_t nch = (nV + GW_CH - 1) / GW_CH;
+  for (int64_t ch = warp; ch < 2 * nch; ch += nwarps) {
+    const bool beta = ch >= nch;
+    const int64_t i0 = (beta ? ch - nch : ch) * GW_CH;
+    const int64_t i1 = i0 + GW_CH < nV ? i0 + GW_CH : nV;
+    if (!beta) {
+      // members in order; lane q accumulates orbitals q and q + 32
+      // (broadcast loads, eight members fetched ahead)
+      int g = ia[i0];
+      double W = 0.0, v0 = 0.0, v1 = 0.0;
+      for (int64_t ib0 = i0; ib0 < i1; ib0 += 8) {
+        int gg[8];
         double cw[8];
         uint64_t yy[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          cw[u] = c[i + u];
-          yy[u] = V[i + u].y;
+          const int64_t i = ib0 + u;
+          gg[u] = i < i1 ? ia[i] : g;
+          cw[u] = i < i1 ? c[i] : 0.0;
+          yy[u] = i < i1 ? V[i].y : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
+          if (gg[u] != g) {
+            if (lane == 0) atomicAdd(&Wa[g], W);
+            if (lane < n) atomicAdd(&va[(int64_t)g * n + lane], v0);
+            if (lane + 32 < n) atomicAdd(&va[(int64_t)g * n + lane + 32], v1);
+            g = gg[u];
+            W = v0 = v1 = 0.0;
+          }
           const double w = cw[u] * cw[u];
           W += w;
           if ((yy[u] >> lane) & 1ull) v0 += w;
           if ((yy[u] >> (lane + 32)) & 1ull) v1 += w;
         }
       }
-      for (; i < e; ++i) {
-        const double ci = c[i];
-        const double w = ci * ci;
-        const uint64_t y = V[i].y;
-        W += w;
-        if ((y >> lane) & 1ull) v0 += w;
-        if ((y >> (lane + 32)) & 1ull) v1 += w;
-      }
-      if (lane == 0) Wa[g] = W;
-      if (lane < n) va[g * n + lane] = v0;
-      if (lane + 32 < n) va[g * n + lane + 32] = v1;
+      if (lane == 0) atomicAdd(&Wa[g], W);
+      if (lane < n) atomicAdd(&va[(int64_t)g * n + lane], v0);
+      if (lane + 32 < n) atomicAdd(&va[(int64_t)g * n + lane + 32], v1);
     } else {
-      const int64_t h = g - nua;
-      double W = 0.0;
-      for (int64_t k = gb[h] + lane; k < gb[h + 1]; k += 32) {
-        const double cv = c[permb[k]];
-        W += cv * cv;
+      // one member per lane; groups are runs of consecutive positions, so a
+      // sum over the lanes of equal group (shuffles down) leaves each run's
+      // total in its first lane
+      for (int64_t k0 = i0; k0 < i1; k0 += 32) {
+        const int64_t k = k0 + lane;
+        int h = -1;
+        double w = 0.0;
+        if (k < i1) {
+          const int32_t d = permb[k];
+          h = ib[d];
+          w = c[d] * c[d];
+        }
+        for (int o = 1; o < 32; o <<= 1) {
+          const double ow = __shfl_down_sync(0xffffffffu, w, o);
+          const int oh = __shfl_down_sync(0xffffffffu, h, o);
+          if (lane + o < 32 && oh == h) w += ow;
+        }
+        const int hp = __shfl_up_sync(0xffffffffu, h, 1);
+        if (h >= 0 && (lane == 0 || hp != h)) atomicAdd(&Wb[h], w);
       }
-      for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
-      if (lane == 0) Wb[h] = W;
     }
   }
 }
@@ -369,8 +392,9 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
     double* Wb = Wa + nua;
     double* va = Wb + nub;
     double* part = va + nua * n;
-    HCI_LAUNCH(k_group_weights, grid_for((nua + nub) * 32, 256), 256, 0, st)(
-        n, V, c, bp<int64_t>(ctx->g_ga), nua, bp<int32_t>(ctx->g_permb), bp<int64_t>(ctx->g_gb), nub, Wa, va, Wb);
+    HCI_CUDA(ctx, cudaMemsetAsync(Wa, 0, (size_t)(nua + nub + nua * n) * 8, st));
+    HCI_LAUNCH(k_group_weights, grid_for(2 * ((nV + GW_CH - 1) / GW_CH) * 32, 256), 256, 0, st)(
+        n, V, c, bp<int32_t>(ctx->g_ia), nV, bp<int32_t>(ctx->g_permb), bp<int32_t>(ctx->g_ib), Wa, va, Wb);
     HCI_LAUNCH(k_occ_sums, OCC_SLICES, 1024, 0, st)(n, V, bp<int64_t>(ctx->g_ga), nua, bp<ulonglong2>(ctx->g_bkeys),
                                                    bp<int64_t>(ctx->g_gb), nub, Wa, va, Wb, part);
     HCI_LAUNCH(k_sum_slices, (unsigned)((mm + 255) / 256), 256, 0, st)((int)mm, part, M);
