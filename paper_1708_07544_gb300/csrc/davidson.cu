@@ -20,8 +20,8 @@ struct DavDev {
   double y[LDG];
   double dots[LDG];
   double theta;
-  double rnorm2;
   double nrm2;
+  double ols[4];          // |r|^2, x . M^-1 r, x . M^-1 x (Olsen correction)
   int amax_idx;
   int kq;                 // size of Qp (0: none)
 };
@@ -200,18 +200,19 @@ __global__ void k_jacobi(DavDev* d, int k) {
   if (l == 0) d->kq = k;
 }
 
-// x = V y, wy = W y, r = wy - theta x, t = r / (theta - diag) (guarded),
-// partial[b] = sum r^2
+// x = V y, wy = W y, r = wy - theta x, t = M^-1 r with M = theta - diag
+// (guarded away from zero); partial[b][0..2] = block sums of r^2, x t and
+// x M^-1 x for the Olsen correction.
 __global__ void __launch_bounds__(DBLOCK) k_ritz(const double* __restrict__ V, const double* __restrict__ W, int64_t ld,
                                                  int k, const DavDev* __restrict__ d, const double* __restrict__ diag,
                                                  int64_t n, double* __restrict__ x, double* __restrict__ wy,
                                                  double* __restrict__ t, double* __restrict__ partial) {
   __shared__ double ys[LDG];
-  __shared__ double red[DBLOCK / 32];
+  __shared__ double red[3][DBLOCK / 32];
   if (threadIdx.x < LDG) ys[threadIdx.x] = d->y[threadIdx.x];
   __syncthreads();
   const double theta = d->theta;
-  double acc = 0.0;
+  double acc = 0.0, axt = 0.0, axx = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double xv = 0.0, wv = 0.0;
     for (int j = 0; j < k; ++j) {
@@ -221,18 +222,43 @@ __global__ void __launch_bounds__(DBLOCK) k_ritz(const double* __restrict__ V, c
     double r = wv - theta * xv;
     double den = theta - diag[i];
     if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
+    const double tv = r / den;
     x[i] = xv;
     wy[i] = wv;
-    t[i] = r / den;
+    t[i] = tv;
     acc = fma(r, r, acc);
+    axt = fma(xv, tv, axt);
+    axx = fma(xv, xv / den, axx);
   }
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int o = 16; o; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    axt += __shfl_xor_sync(0xffffffffu, axt, o);
+    axx += __shfl_xor_sync(0xffffffffu, axx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc;
+    red[1][threadIdx.x >> 5] = axt;
+    red[2][threadIdx.x >> 5] = axx;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 3) {
     double s = 0.0;
-    for (int w = 0; w < DBLOCK / 32; ++w) s += red[w];
-    partial[(int64_t)blockIdx.x * LDG] = s;
+    for (int w = 0; w < DBLOCK / 32; ++w) s += red[threadIdx.x][w];
+    partial[(int64_t)blockIdx.x * LDG + threadIdx.x] = s;
+  }
+}
+
+// Olsen correction: t = M^-1 (r - eps x) with eps = (x M^-1 r) / (x M^-1 x),
+// which makes the correction orthogonal to x to first order.
+__global__ void __launch_bounds__(DBLOCK) k_olsen(const DavDev* __restrict__ d, const double* __restrict__ diag,
+                                                  int64_t n, const double* __restrict__ x, double* __restrict__ t) {
+  const double den_x = d->ols[2];
+  const double eps = den_x != 0.0 ? d->ols[1] / den_x : 0.0;
+  const double theta = d->theta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double den = theta - diag[i];
+    if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
+    t[i] -= eps * x[i] / den;
   }
 }
 
@@ -394,11 +420,11 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
   for (; it < maxit; ++it) {
     HCI_LAUNCH(k_jacobi, 1, 32, 0, st)(D.d, k);
     HCI_LAUNCH(k_ritz, D.nblk, DBLOCK, 0, st)(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
-    HCI_LAUNCH(k_reduce, 1, 32, 0, st)(D.part, D.nblk, 1, &D.d->rnorm2);
+    HCI_LAUNCH(k_reduce, 1, 32 * 3, 0, st)(D.part, D.nblk, 3, D.d->ols);
     HCI_CUDA(ctx, cudaGetLastError());
     double hv[2];
     HCI_CUDA(ctx, cudaMemcpyAsync(&hv[0], &D.d->theta, 8, cudaMemcpyDeviceToHost, st));
-    HCI_CUDA(ctx, cudaMemcpyAsync(&hv[1], &D.d->rnorm2, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&hv[1], &D.d->ols[0], 8, cudaMemcpyDeviceToHost, st));
     HCI_CUDA(ctx, cudaStreamSynchronize(st));
     theta = hv[0];
     rn = std::sqrt(hv[1]);
@@ -418,6 +444,7 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
       HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, 0);
       k = 1;
     }
+    HCI_LAUNCH(k_olsen, D.nblk, DBLOCK, 0, st)(D.d, diag, nV, D.x, D.t);
     // orthogonalise the correction twice, normalise
     for (int pass = 0; pass < 2; ++pass) {
       HCI_TRY(D.dots(D.V, k, D.t, D.d->dots));
