@@ -12,11 +12,15 @@
 //       each distinct alpha string) and beta differs by a single.
 // The three sets are disjoint.  Rows are filled in scan order, so the CSR
 // layout (and the sigma summation order) is deterministic.
+#include <algorithm>
+
 #include "hci_internal.cuh"
 
 namespace {
 
 constexpr int G_WARPS = 8;
+constexpr int ROWS_GRID = 152 * 8;   // blocks of the row search
+constexpr int64_t ROW_SCR = 8192;    // scratch entries per warp of the staged row search
 
 __device__ __forceinline__ bool key_less(ulonglong2 a, ulonglong2 b) {
   return a.x < b.x || (a.x == b.x && a.y < b.y);
@@ -229,7 +233,13 @@ struct GraphArgs {
   const int64_t* rowptr;   // fill pass: output offset per processed row
   int32_t* col;
   double* val;
-  int64_t* rowcnt;         // count pass: entries per processed row
+  int64_t* rowcnt;         // count / staged pass: entries per processed row
+  int32_t* scr;            // staged pass: scr_cap entries of scratch per warp of the grid
+  int64_t scr_cap;
+  int32_t* stage;          // staged pass: rows, each contiguous, at rowoff[q]
+  int64_t stage_cap;
+  int64_t* rowoff;
+  unsigned long long* stage_ctl;  // [0] next free staging entry, [1] rows left to the fill pass
   const int32_t* s2i;      // sorted position -> internal id (columns are stored as internal ids)
   unsigned long long* queue;
   HamView H;
@@ -241,13 +251,18 @@ __device__ __forceinline__ bool use_lookup(int64_t m, int L) {
   return m > (int64_t)L * lg;
 }
 
-template <bool FILL>
-__device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t j, bool ok, int64_t& w) {
+// Row search modes: count only, fill at a known offset, or staged fill
+// (into the warp's scratch, capped at scr_cap entries, still counting past it).
+constexpr int ROWS_COUNT = 0, ROWS_FILL = 1, ROWS_STAGED = 2;
+
+template <int MODE>
+__device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t j, bool ok, int64_t& w,
+                                      int32_t* out) {
   const int lane = threadIdx.x & 31;
   unsigned m = __ballot_sync(0xffffffffu, ok);
-  if (FILL && ok) {
+  if (MODE != ROWS_COUNT && ok) {
     int64_t pos = w + __popc(m & ((1u << lane) - 1u));
-    A.col[pos] = A.s2i[j];
+    if (MODE == ROWS_FILL || pos < A.scr_cap) out[pos] = A.s2i[j];
   }
   w += __popc(m);
 }
@@ -258,10 +273,10 @@ __device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t
 // j = permb[pos], other-spin value bk[pos].y).  Small groups are scanned
 // (flattened, 32 groups at a time); large groups are probed with binary
 // searches for the L single excitations of the other-spin string.
-template <bool FILL, bool BETA>
-__device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, int g, int64_t& w, int64_t* s_start,
-                                           int64_t* s_pref, int64_t* s_size, const int* occ_o, const int* vir_o,
-                                           int nocc_o, int nvir_o) {
+template <int MODE, bool BETA>
+__device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, int g, int64_t& w, int32_t* out,
+                                           int64_t* s_start, int64_t* s_pref, int64_t* s_size, const int* occ_o,
+                                           const int* vir_o, int nocc_o, int nvir_o) {
   const int lane = threadIdx.x & 31;
   const int64_t* ptr = BETA ? A.bnbr_ptr : A.anbr_ptr;
   const int32_t* nbr = BETA ? A.bnbr : A.anbr;
@@ -308,7 +323,7 @@ __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, in
         else { j = pos; other = A.vb[pos]; }
         ok = __popcll(mine ^ other) == 2;
       }
-      visit<FILL>(A, ki, j, ok, w);
+      visit<MODE>(A, ki, j, ok, w, out);
     }
     unsigned lk = __ballot_sync(0xffffffffu, look);
     while (lk) {
@@ -333,7 +348,7 @@ __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, in
             if (x == want) { ok = true; j = BETA ? A.permb[st2 + lo] : st2 + lo; }
           }
         }
-        visit<FILL>(A, ki, j, ok, w);
+        visit<MODE>(A, ki, j, ok, w, out);
       }
     }
     __syncwarp();
@@ -359,7 +374,12 @@ __device__ __forceinline__ int occ_vir_lists(uint64_t s, int n, int* occ, int* v
   return bo;
 }
 
-template <bool FILL>
+// One warp per row taken from a queue.  ROWS_STAGED: the row goes to the
+// warp's scratch; at its end one atomic reserves the row's range of the
+// staging buffer and the row is copied there (rowoff[q] = its start, or -1
+// when the row outgrew the scratch or the staging buffer; rowcnt[q] is
+// exact either way).
+template <int MODE>
 __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
   __shared__ int64_t s_start[G_WARPS][32];
   __shared__ int64_t s_size[G_WARPS][32];
@@ -374,7 +394,10 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
     if (q >= A.nrows) break;
     const int64_t i = A.rowlist ? (int64_t)A.rowlist[q] : q;
     const ulonglong2 ki = A.V[i];
-    int64_t w = FILL ? A.rowptr[q] : 0;
+    int64_t w = MODE == ROWS_FILL ? A.rowptr[q] : 0;
+    int32_t* out = MODE == ROWS_FILL ? A.col
+                   : MODE == ROWS_STAGED ? A.scr + (int64_t)(blockIdx.x * G_WARPS + wid) * A.scr_cap
+                                         : nullptr;
     // (A) same alpha string
     {
       const int g = A.ia[i];
@@ -391,8 +414,8 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
           const int d = __popcll(ki.y ^ x2);
           ok2 = d == 2 || d == 4;
         }
-        visit<FILL>(A, ki, j, ok, w);
-        if (j0 + 32 < e) visit<FILL>(A, ki, j2, ok2, w);
+        visit<MODE>(A, ki, j, ok, w, out);
+        if (j0 + 32 < e) visit<MODE>(A, ki, j2, ok2, w, out);
       }
     }
     // (B) same beta string
@@ -412,11 +435,11 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
           const int d = __popcll(ki.x ^ x2);
           ok2 = d == 2 || d == 4;
         }
-        const int64_t j = (FILL && ok) ? (int64_t)A.permb[k] : -1;
-        visit<FILL>(A, ki, j, ok, w);
+        const int64_t j = (MODE != ROWS_COUNT && ok) ? (int64_t)A.permb[k] : -1;
+        visit<MODE>(A, ki, j, ok, w, out);
         if (k0 + 32 < e) {
-          const int64_t j2 = (FILL && ok2) ? (int64_t)A.permb[k2] : -1;
-          visit<FILL>(A, ki, j2, ok2, w);
+          const int64_t j2 = (MODE != ROWS_COUNT && ok2) ? (int64_t)A.permb[k2] : -1;
+          visit<MODE>(A, ki, j2, ok2, w, out);
         }
       }
     }
@@ -425,16 +448,62 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
       const int ga_i = A.ia[i], gb_i = A.ib[i];
       if (A.costa[ga_i] <= A.costb[gb_i]) {
         const int no = occ_vir_lists(ki.y, A.n, s_occ[wid], s_vir[wid]);
-        mixed_side<FILL, false>(A, ki, ga_i, w, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid], s_vir[wid],
-                                no, A.n - no);
+        mixed_side<MODE, false>(A, ki, ga_i, w, out, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid],
+                                s_vir[wid], no, A.n - no);
       } else {
         const int no = occ_vir_lists(ki.x, A.n, s_occ[wid], s_vir[wid]);
-        mixed_side<FILL, true>(A, ki, gb_i, w, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid], s_vir[wid],
-                               no, A.n - no);
+        mixed_side<MODE, true>(A, ki, gb_i, w, out, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid],
+                               s_vir[wid], no, A.n - no);
       }
     }
-    if (!FILL && lane == 0) A.rowcnt[q] = w;
+    if (MODE == ROWS_COUNT && lane == 0) A.rowcnt[q] = w;
+    if (MODE == ROWS_STAGED) {
+      __syncwarp();
+      int64_t base = -1;
+      if (lane == 0) {
+        A.rowcnt[q] = w;
+        if (w <= A.scr_cap) {
+          const int64_t b = (int64_t)atomicAdd(A.stage_ctl, (unsigned long long)w);
+          if (b + w <= A.stage_cap) base = b;
+        }
+        if (base < 0) atomicAdd(A.stage_ctl + 1, 1ull);
+        A.rowoff[q] = base;
+      }
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= 0)
+        for (int64_t t = lane; t < w; t += 32) A.stage[base + t] = out[t];
+      __syncwarp();
+    }
   }
+}
+
+// CSR of the staged rows: row q (rowoff[q] >= 0) copied from the staging
+// buffer to [rp[q], rp[q+1]) of col, one warp per row.
+__global__ void k_copy_staged(const int64_t* __restrict__ rowoff, const int64_t* __restrict__ rp, int64_t nrows,
+                              const int32_t* __restrict__ stage, int32_t* __restrict__ col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < nrows; q += nwarps) {
+    const int64_t off = rowoff[q];
+    if (off < 0) continue;
+    const int64_t b = rp[q], len = rp[q + 1] - b;
+    for (int64_t t = lane; t < len; t += 32) col[b + t] = stage[off + t];
+  }
+}
+
+// rows the staged pass could not keep: their ids and CSR offsets, for the
+// fill pass (any order: each row is written at its own offset)
+__global__ void k_collect_left(const int64_t* __restrict__ rowoff, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ rowlist, int64_t nrows,
+                               unsigned long long* __restrict__ counter, int32_t* __restrict__ left_rows,
+                               int64_t* __restrict__ left_off) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nrows; q += (int64_t)gridDim.x * blockDim.x)
+    if (rowoff[q] < 0) {
+      const unsigned long long m = atomicAdd(counter, 1ull);
+      left_rows[m] = rowlist[q];
+      left_off[m] = rp[q];
+    }
 }
 
 // Matrix elements of filled rows (the search only records the columns):
@@ -1011,6 +1080,7 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   A.rowlist = nullptr;
   A.nrows = nV;
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr; A.rowcnt = nullptr;
+  A.scr = nullptr; A.scr_cap = 0; A.stage = nullptr; A.stage_cap = 0; A.rowoff = nullptr; A.stage_ctl = nullptr;
   prof_toc(ctx, HCI_PH_GRAPH_SPACE);
   return HCI_OK;
 }
@@ -1021,7 +1091,7 @@ static hci_status rows_count(hci_ctx* ctx, GraphArgs& A, DevBuf& cnt) {
   A.rowcnt = bp<int64_t>(cnt);
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<false>, 152 * 8, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_LAUNCH(k_rows<ROWS_COUNT>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   A.rowcnt = nullptr;
   return HCI_OK;
@@ -1031,10 +1101,11 @@ static hci_status rows_count(hci_ctx* ctx, GraphArgs& A, DevBuf& cnt) {
 static hci_status rows_fill(hci_ctx* ctx, GraphArgs& A, const int64_t* offs, int32_t* col, double* val) {
   A.rowptr = offs; A.col = col; A.val = val;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<true>, 152 * 8, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_LAUNCH(k_rows<ROWS_FILL>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
 }
+
 
 static int64_t read_i64(hci_ctx* ctx, const int64_t* d, hci_status* st) {
   int64_t v = 0;
@@ -1042,6 +1113,66 @@ static int64_t read_i64(hci_ctx* ctx, const int64_t* d, hci_status* st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
   *st = e == cudaSuccess ? HCI_OK : hci_fail(ctx, HCI_ERR_CUDA, "graph: %s", cudaGetErrorString(e));
   return v;
+}
+
+// The rows listed in A (rowlist, nrows; a list is required) searched once:
+// counts into inc.cnt, the CSR offsets into inc.rpN and the columns into
+// inc.colN (inc.valN sized to match).  Rows longer than ROW_SCR, or beyond
+// the staging space (sized from est entries), are filled by a second search
+// at their offsets.  *nnz = entries of the listed rows.
+static hci_status rows_staged(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* nnz) {
+  IncScratch& S = ctx->inc;
+  cudaStream_t st = ctx->st;
+  const int64_t nrows = A.nrows;
+  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+  HCI_TRY(ensure_buf(ctx, S.cnt, (size_t)(nrows + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, S.roff, (size_t)(nrows + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, S.scr, (size_t)ROWS_GRID * G_WARPS * ROW_SCR * 4));
+  if (S.stage.bytes < (size_t)est * 4) HCI_TRY(ensure_buf(ctx, S.stage, (size_t)est * 4));
+  HCI_TRY(ensure_buf(ctx, S.ctl, 32));
+  HCI_CUDA(ctx, cudaMemsetAsync(S.ctl.p, 0, 32, st));
+  unsigned long long* ctl = bp<unsigned long long>(S.ctl);
+  A.rowcnt = bp<int64_t>(S.cnt);
+  A.scr = bp<int32_t>(S.scr);
+  A.scr_cap = ROW_SCR;
+  A.stage = bp<int32_t>(S.stage);
+  A.stage_cap = (int64_t)(S.stage.bytes / 4);
+  A.rowoff = bp<int64_t>(S.roff);
+  A.stage_ctl = ctl;
+  HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, st));
+  HCI_LAUNCH(k_rows<ROWS_STAGED>, ROWS_GRID, G_WARPS * 32, 0, st)(A);
+  HCI_CUDA(ctx, cudaGetLastError());
+  A.rowcnt = nullptr; A.scr = nullptr; A.scr_cap = 0; A.stage = nullptr; A.stage_cap = 0; A.rowoff = nullptr;
+  A.stage_ctl = nullptr;
+  HCI_TRY(ensure_buf(ctx, S.rpN, (size_t)(nrows + 1) * 8));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.rpN), nrows, dtot));
+  HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(S.rpN), nrows, dtot);
+  hci_status hs = HCI_OK;
+  const int64_t total = read_i64(ctx, dtot, &hs);
+  HCI_TRY(hs);
+  const int64_t left = read_i64(ctx, reinterpret_cast<const int64_t*>(ctl + 1), &hs);
+  HCI_TRY(hs);
+  HCI_TRY(ensure_buf(ctx, S.colN, (size_t)(total + 1) * 4));
+  HCI_TRY(ensure_buf(ctx, S.valN, (size_t)(total + 1) * 8));
+  HCI_LAUNCH(k_copy_staged, grid_for(nrows * 32, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN), nrows,
+                                                                    bp<int32_t>(S.stage), bp<int32_t>(S.colN));
+  HCI_CUDA(ctx, cudaGetLastError());
+  if (left > 0) {
+    HCI_TRY(ensure_buf(ctx, S.left, (size_t)left * 12 + 16));
+    int64_t* left_off = bp<int64_t>(S.left);
+    int32_t* left_rows = reinterpret_cast<int32_t*>(left_off + left);
+    HCI_LAUNCH(k_collect_left, grid_for(nrows, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN),
+                                                                  A.rowlist, nrows, ctl + 2, left_rows, left_off);
+    const int32_t* rl = A.rowlist;
+    A.rowlist = left_rows;
+    A.nrows = left;
+    hci_status fs = rows_fill(ctx, A, left_off, bp<int32_t>(S.colN), bp<double>(S.valN));
+    A.rowlist = rl;
+    A.nrows = nrows;
+    HCI_TRY(fs);
+  }
+  *nnz = total;
+  return HCI_OK;
 }
 
 static hci_status compute_diag(hci_ctx* ctx, int64_t nrows, const ulonglong2* keys, double* out) {
@@ -1174,15 +1305,10 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   A.rowlist = bp<int32_t>(S.newrows);
   A.nrows = nnew;
   prof_tic(ctx, HCI_PH_GRAPH_ROWS);
-  HCI_TRY(rows_count(ctx, A, S.cnt));
-  HCI_TRY(ensure_buf(ctx, S.rpN, (size_t)(nnew + 1) * 8));
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.rpN), nnew, dtot));
-  HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(S.rpN), nnew, dtot);
-  const int64_t nnzN = read_i64(ctx, dtot, &hs);
-  HCI_TRY(hs);
-  HCI_TRY(ensure_buf(ctx, S.colN, (size_t)(nnzN + 1) * 4));
-  HCI_TRY(ensure_buf(ctx, S.valN, (size_t)(nnzN + 1) * 8));
-  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(S.rpN), bp<int32_t>(S.colN), bp<double>(S.valN)));
+  // staging space: twice the old space's mean row length per new row
+  const int64_t mean_len = nold > 0 ? G.nnz / nold + 1 : 64;
+  int64_t nnzN = 0;
+  HCI_TRY(rows_staged(ctx, A, std::max<int64_t>((int64_t)1 << 22, 2 * nnew * mean_len), &nnzN));
   HCI_LAUNCH(k_row_values<true>, grid_for(nnew * 32, 256), 256, 0, st)(
       bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), nullptr, bp<int32_t>(S.colN), bp<double>(S.valN),
       bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);

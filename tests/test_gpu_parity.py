@@ -325,6 +325,36 @@ def test_incremental_graph_matches_oracle(pkg, name, make, nv):
         assert np.abs(got - oracle.hamiltonian(inst, sub) @ c).max() < 1e-11 * max(1.0, np.abs(got).max())
 
 
+def test_incremental_graph_row_beyond_scratch(pkg):
+    """A new row longer than the row search's per-warp scratch (8192
+    entries): the aufbau determinant of 20 orbitals with 10 + 10 electrons
+    joins a space of all its single and double excitations (14250 of them)
+    in an incremental update; its row is filled by the second search.  That
+    row of H c and sampled others equal the oracle's."""
+    norb, ne = 20, 10
+    inst = hi.random_tiny(norb, ne, ne, 31)
+    a0 = b0 = (1 << ne) - 1
+    occ, vir = range(ne), range(ne, norb)
+    singles = [a0 ^ (1 << i) ^ (1 << a) for i in occ for a in vir]
+    doubles = [a0 ^ (1 << i) ^ (1 << j) ^ (1 << a) ^ (1 << b)
+               for i, j in itertools.combinations(occ, 2) for a, b in itertools.combinations(vir, 2)]
+    exc = ([(x, b0) for x in singles + doubles] + [(a0, y) for y in singles + doubles]
+           + [(x, y) for x in singles for y in singles])
+    assert len(exc) == 14250
+    exc = np.array(sorted(exc), dtype=np.uint64)
+    full = np.array(sorted([tuple(r) for r in exc.tolist()] + [(a0, b0)]), dtype=np.uint64)
+    rng = np.random.default_rng(5)
+    first = exc[np.sort(rng.choice(len(exc), len(exc) // 2, replace=False))]
+    c = hi.random_vector(len(full), seed=6)
+    i0 = int(np.nonzero((full[:, 0] == a0) & (full[:, 1] == b0))[0][0])
+    rows = np.unique(np.concatenate([[i0], rng.choice(len(full), 64, replace=False)]))
+    with solver(pkg, inst) as s:
+        s.sigma(dev_keys(first), torch.tensor(hi.random_vector(len(first), seed=7)).cuda())
+        got = s.sigma(dev_keys(full), torch.tensor(c).cuda()).cpu().numpy()
+    want = oracle.sigma_rows(inst, full, c, rows)
+    assert np.abs(got[rows] - want).max() < 1e-11 * max(1.0, np.abs(want).max())
+
+
 def test_incremental_solve_matches_fresh_contexts(pkg, poly8_ref):
     """Davidson on each space of an HCI run with one context (incremental
     graphs) equals the oracle's eigenvalue on that space."""
