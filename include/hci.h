@@ -206,11 +206,14 @@ hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, co
  *   HCI_ST_CANDIDATES       candidates emitted by them in total
  *   HCI_ST_GRAPH_BUILDS     connection graphs built
  *   HCI_ST_WALK_ENTRIES     list entries examined by the heat-bath walks
- *   HCI_ST_SINGLES_EXACT    single excitations evaluated exactly */
+ *   HCI_ST_SINGLES_EXACT    single excitations evaluated exactly
+ *   HCI_ST_ROWS_REFILLED    new graph rows too long for the one-pass search,
+ *                           filled by a second search */
 enum {
   HCI_ST_GRAPH_NNZ = 0, HCI_ST_LAST_CANDIDATES = 1, HCI_ST_SIGMA_CALLS = 2, HCI_ST_SIGMA_ROWS = 3,
   HCI_ST_SIGMA_NNZ = 4, HCI_ST_SELECT_CALLS = 5, HCI_ST_SELECT_SOURCES = 6, HCI_ST_CANDIDATES = 7,
-  HCI_ST_GRAPH_BUILDS = 8, HCI_ST_WALK_ENTRIES = 9, HCI_ST_SINGLES_EXACT = 10, HCI_ST_COUNT = 11
+  HCI_ST_GRAPH_BUILDS = 8, HCI_ST_WALK_ENTRIES = 9, HCI_ST_SINGLES_EXACT = 10, HCI_ST_ROWS_REFILLED = 11,
+  HCI_ST_COUNT = 12
 };
 hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout);
 

@@ -31,7 +31,7 @@ EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hc
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
-         "select_sources", "candidates", "graph_builds", "walk_entries", "singles_exact"]
+         "select_sources", "candidates", "graph_builds", "walk_entries", "singles_exact", "rows_refilled"]
 
 
 class HCIError(RuntimeError):

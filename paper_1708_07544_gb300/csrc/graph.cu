@@ -13,14 +13,16 @@
 // The three sets are disjoint.  Rows are filled in scan order, so the CSR
 // layout (and the sigma summation order) is deterministic.
 #include <algorithm>
+#include <vector>
 
 #include "hci_internal.cuh"
 
 namespace {
 
 constexpr int G_WARPS = 8;
-constexpr int ROWS_GRID = 152 * 8;   // blocks of the row search
-constexpr int64_t ROW_SCR = 8192;    // scratch entries per warp of the staged row search
+constexpr int ROWS_GRID = 152 * 6;   // blocks of the row search (all resident at 40 registers)
+constexpr int64_t ROW_SCR = 32768;   // scratch entries per warp of the staged row search
+constexpr int64_t ROW_SAMPLE = 2048; // rows counted to size the staging buffer
 
 __device__ __forceinline__ bool key_less(ulonglong2 a, ulonglong2 b) {
   return a.x < b.x || (a.x == b.x && a.y < b.y);
@@ -475,6 +477,12 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
       __syncwarp();
     }
   }
+}
+
+// rows[t] = list[t * n / ns], an evenly strided sample of ns entries of list
+__global__ void k_stride_sample(const int32_t* __restrict__ list, int64_t n, int64_t ns, int32_t* __restrict__ rows) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ns) rows[t] = list[t * n / ns];
 }
 
 // CSR of the staged rows: row q (rowoff[q] >= 0) copied from the staging
@@ -1157,6 +1165,7 @@ static hci_status rows_staged(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* 
   HCI_LAUNCH(k_copy_staged, grid_for(nrows * 32, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN), nrows,
                                                                     bp<int32_t>(S.stage), bp<int32_t>(S.colN));
   HCI_CUDA(ctx, cudaGetLastError());
+  ctx->st_counts[HCI_ST_ROWS_REFILLED] += left;
   if (left > 0) {
     HCI_TRY(ensure_buf(ctx, S.left, (size_t)left * 12 + 16));
     int64_t* left_off = bp<int64_t>(S.left);
@@ -1305,10 +1314,32 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   A.rowlist = bp<int32_t>(S.newrows);
   A.nrows = nnew;
   prof_tic(ctx, HCI_PH_GRAPH_ROWS);
-  // staging space: twice the old space's mean row length per new row
-  const int64_t mean_len = nold > 0 ? G.nnz / nold + 1 : 64;
+  // staging space from the mean length of a strided sample of the new rows
+  // (the old rows' lengths say little when the space grows many-fold)
   int64_t nnzN = 0;
-  HCI_TRY(rows_staged(ctx, A, std::max<int64_t>((int64_t)1 << 22, 2 * nnew * mean_len), &nnzN));
+  {
+    const int64_t ns = std::min<int64_t>(nnew, ROW_SAMPLE);
+    HCI_TRY(ensure_buf(ctx, S.samp, (size_t)ns * 12 + 16));
+    int64_t* samp_cnt = bp<int64_t>(S.samp);
+    int32_t* samp_rows = reinterpret_cast<int32_t*>(samp_cnt + ns);
+    HCI_LAUNCH(k_stride_sample, grid_for(ns, 256), 256, 0, st)(bp<int32_t>(S.newrows), nnew, ns, samp_rows);
+    GraphArgs B = A;
+    B.rowlist = samp_rows;
+    B.nrows = ns;
+    B.rowcnt = samp_cnt;
+    HCI_CUDA(ctx, cudaMemsetAsync(B.queue, 0, 8, st));
+    HCI_LAUNCH(k_rows<ROWS_COUNT>, ROWS_GRID, G_WARPS * 32, 0, st)(B);
+    HCI_CUDA(ctx, cudaGetLastError());
+    std::vector<int64_t> cnt((size_t)ns);
+    HCI_CUDA(ctx, cudaMemcpyAsync(cnt.data(), samp_cnt, (size_t)ns * 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    double sum = 0.0;
+    for (int64_t v : cnt) sum += (double)v;
+    const double mean = ns > 0 ? sum / (double)ns : 0.0;
+    const double want = 1.5 * (double)nnew * mean;
+    const int64_t est = (int64_t)std::min((double)nnew * (double)nV, want) + ((int64_t)1 << 22);
+    HCI_TRY(rows_staged(ctx, A, est, &nnzN));
+  }
   HCI_LAUNCH(k_row_values<true>, grid_for(nnew * 32, 256), 256, 0, st)(
       bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), nullptr, bp<int32_t>(S.colN), bp<double>(S.valN),
       bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);

@@ -61,7 +61,7 @@ struct Lists {
 struct IncScratch {
   DevBuf pos_old, mark, flag, newrows, rpN, colN, valN, cnt, hist, tbase, T, T2, tstart, len;
   DevBuf keys_old, rp_old, col_old, val_old, len_old, cap_old, diag_old, s2i_old, keys_int_old;
-  DevBuf scr, stage, roff, ctl, left;   // staged row search
+  DevBuf scr, stage, roff, ctl, left, samp;   // staged row search
 };
 
 // Per-phase CUDA-event timers (enabled by hci_profile).

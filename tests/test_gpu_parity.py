@@ -326,12 +326,12 @@ def test_incremental_graph_matches_oracle(pkg, name, make, nv):
 
 
 def test_incremental_graph_row_beyond_scratch(pkg):
-    """A new row longer than the row search's per-warp scratch (8192
-    entries): the aufbau determinant of 20 orbitals with 10 + 10 electrons
-    joins a space of all its single and double excitations (14250 of them)
+    """A new row longer than the row search's per-warp scratch (32768
+    entries): the aufbau determinant of 26 orbitals with 13 + 13 electrons
+    joins a space of all its single and double excitations (41067 of them)
     in an incremental update; its row is filled by the second search.  That
     row of H c and sampled others equal the oracle's."""
-    norb, ne = 20, 10
+    norb, ne = 26, 13
     inst = hi.random_tiny(norb, ne, ne, 31)
     a0 = b0 = (1 << ne) - 1
     occ, vir = range(ne), range(ne, norb)
@@ -340,7 +340,7 @@ def test_incremental_graph_row_beyond_scratch(pkg):
                for i, j in itertools.combinations(occ, 2) for a, b in itertools.combinations(vir, 2)]
     exc = ([(x, b0) for x in singles + doubles] + [(a0, y) for y in singles + doubles]
            + [(x, y) for x in singles for y in singles])
-    assert len(exc) == 14250
+    assert len(exc) == 41067
     exc = np.array(sorted(exc), dtype=np.uint64)
     full = np.array(sorted([tuple(r) for r in exc.tolist()] + [(a0, b0)]), dtype=np.uint64)
     rng = np.random.default_rng(5)
@@ -351,6 +351,7 @@ def test_incremental_graph_row_beyond_scratch(pkg):
     with solver(pkg, inst) as s:
         s.sigma(dev_keys(first), torch.tensor(hi.random_vector(len(first), seed=7)).cuda())
         got = s.sigma(dev_keys(full), torch.tensor(c).cuda()).cpu().numpy()
+        assert s.stats()["rows_refilled"] >= 1
     want = oracle.sigma_rows(inst, full, c, rows)
     assert np.abs(got[rows] - want).max() < 1e-11 * max(1.0, np.abs(want).max())
 
