@@ -77,9 +77,10 @@ __global__ void k_set_gcol(DavDev* d, int col) {
 }
 
 // Lowest eigenpair of the k x k subspace matrix by parallel-order Jacobi on
-// one warp: in each round the indices are paired by a round-robin schedule
-// and all disjoint pairs rotate at once (their rotations commute), so a
-// sweep is k-1 rounds of parallel row and column updates.  An off-diagonal
+// one block of JW warps: in each round the indices are paired by a
+// round-robin schedule and all disjoint pairs rotate at once (their
+// rotations commute), so a sweep is k-1 rounds of parallel row and column
+// updates, the pairs split over the warps.  An off-diagonal
 // element too small to change either diagonal partner in floating point
 // (even scaled by 100) is zeroed; the sweeps stop when a sweep rotates none.
 //
@@ -87,48 +88,54 @@ __global__ void k_set_gcol(DavDev* d, int col) {
 // sweeps start from the previous eigenvectors Q0 = diag(Qp, 1): Q0^T G Q0 is
 // diagonal but for its last row and column, and takes a few sweeps instead
 // of a full diagonalisation.
-__global__ void k_jacobi(DavDev* d, int k) {
+constexpr int JW = 4;   // warps of k_jacobi: one per SM sub-partition (FP64 issue is the limit)
+
+__global__ void __launch_bounds__(JW * 32) k_jacobi(DavDev* d, int k) {
   __shared__ double A[32][33];
   __shared__ double Q[32][33];
   __shared__ double T[32][33];
   __shared__ double rc[16], rs[16];
   __shared__ int rp[16], rq[16];
-  const int l = threadIdx.x;
+  __shared__ int s_rot, s_m;
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool warm = k > 1 && d->kq == k - 1;
-  for (int j = 0; j < 32; ++j) {
+  for (int j = w; j < 32; j += JW) {
     A[l][j] = (l < k && j < k) ? d->G[l * LDG + j] : 0.0;
     double q0 = (l == j) ? 1.0 : 0.0;
     if (warm && l < k - 1 && j < k - 1) q0 = d->Qp[l * LDG + j];
     Q[l][j] = q0;
   }
-  __syncwarp();
+  __syncthreads();
   if (warm) {
-    // T = G Q0 (lane = row), then A = Q0^T T (lane = column)
+    // T = G Q0 (lane = row, warps split the columns), then A = Q0^T T
+    // (lane = column, warps split the rows)
     if (l < k)
-      for (int j = 0; j < k; ++j) {
+      for (int j = w; j < k; j += JW) {
         double t = 0.0;
-        for (int m = 0; m < k; ++m) t = fma(A[l][m], Q[m][j], t);
+        for (int mm = 0; mm < k; ++mm) t = fma(A[l][mm], Q[mm][j], t);
         T[l][j] = t;
       }
-    __syncwarp();
+    __syncthreads();
     if (l < k)
-      for (int i = 0; i < k; ++i) {
+      for (int i = w; i < k; i += JW) {
         double t = 0.0;
-        for (int m = 0; m < k; ++m) t = fma(Q[m][i], T[m][l], t);
+        for (int mm = 0; mm < k; ++mm) t = fma(Q[mm][i], T[mm][l], t);
         A[i][l] = t;
       }
-    __syncwarp();
+    __syncthreads();
   }
   const int m = (k + 1) & ~1;          // even number of players (index k is a dummy when k is odd)
   const int npairs = m / 2;
   for (int sweep = 0; sweep < 50 && k > 1; ++sweep) {
-    int rotated = 0;
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
     for (int r = 0; r < m - 1; ++r) {
-      // lane t < npairs: pair t of round r
-      if (l < npairs) {
+      // thread t < npairs: pair t of round r
+      if (threadIdx.x < npairs) {
+        const int t = threadIdx.x;
         int a, b;
-        if (l == 0) { a = r; b = m - 1; }
-        else { a = (r + l) % (m - 1); b = (r - l + (m - 1)) % (m - 1); }
+        if (t == 0) { a = r; b = m - 1; }
+        else { a = (r + t) % (m - 1); b = (r - t + (m - 1)) % (m - 1); }
         int p = a < b ? a : b, q = a < b ? b : a;
         double c = 1.0, sn = 0.0;
         int active = 0;
@@ -137,20 +144,20 @@ __global__ void k_jacobi(DavDev* d, int k) {
           const double g = 100.0 * fabs(apq);
           if (!((fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq)) || fabs(apq) < 1e-300)) {
             const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            sn = t * c;
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            sn = tt * c;
             active = 1;
           }
         }
-        rp[l] = p; rq[l] = q; rc[l] = c; rs[l] = active ? sn : 0.0;
+        rp[t] = p; rq[t] = q; rc[t] = c; rs[t] = active ? sn : 0.0;
         if (!active && q < k) { A[p][q] = 0.0; A[q][p] = 0.0; }
-        rotated |= active;
+        if (active) s_rot = 1;
       }
-      __syncwarp();
-      // columns: A <- A J, Q <- Q J (lane = row)
+      __syncthreads();
+      // columns: A <- A J, Q <- Q J (lane = row; warp w takes pairs w, w + JW, ...)
       if (l < k) {
-        for (int t = 0; t < npairs; ++t) {
+        for (int t = w; t < npairs; t += JW) {
           const double s2 = rs[t];
           if (s2 == 0.0) continue;
           const int p = rp[t], q = rq[t];
@@ -163,10 +170,10 @@ __global__ void k_jacobi(DavDev* d, int k) {
           Q[l][q] = s2 * vlp + c2 * vlq;
         }
       }
-      __syncwarp();
+      __syncthreads();
       // rows: A <- J^T A (lane = column)
       if (l < k) {
-        for (int t = 0; t < npairs; ++t) {
+        for (int t = w; t < npairs; t += JW) {
           const double s2 = rs[t];
           if (s2 == 0.0) continue;
           const int p = rp[t], q = rq[t];
@@ -176,28 +183,30 @@ __global__ void k_jacobi(DavDev* d, int k) {
           A[q][l] = s2 * apl + c2 * aql;
         }
       }
-      __syncwarp();
-      if (l < npairs && rs[l] != 0.0) { A[rp[l]][rq[l]] = 0.0; A[rq[l]][rp[l]] = 0.0; }
-      __syncwarp();
+      __syncthreads();
+      if (threadIdx.x < npairs && rs[threadIdx.x] != 0.0) {
+        A[rp[threadIdx.x]][rq[threadIdx.x]] = 0.0;
+        A[rq[threadIdx.x]][rp[threadIdx.x]] = 0.0;
+      }
+      __syncthreads();
     }
-    rotated = __any_sync(0xffffffffu, rotated);
+    const int rotated = s_rot;
+    __syncthreads();
     if (!rotated) break;
   }
-  __syncwarp();
-  __shared__ int s_m;
-  if (l == 0) {
+  if (threadIdx.x == 0) {
     int mm = 0;
     for (int j = 1; j < k; ++j)
       if (A[j][j] < A[mm][mm]) mm = j;
     s_m = mm;
     d->theta = A[mm][mm];
   }
-  __syncwarp();
+  __syncthreads();
   const int mi = s_m;
-  if (l < LDG) d->y[l] = (l < k) ? Q[l][mi] : 0.0;
-  for (int j = 0; j < k; ++j)
-    if (l < k) d->Qp[l * LDG + j] = Q[l][j];
-  if (l == 0) d->kq = k;
+  if (w == 0 && l < LDG) d->y[l] = (l < k) ? Q[l][mi] : 0.0;
+  if (l < k)
+    for (int j = w; j < k; j += JW) d->Qp[l * LDG + j] = Q[l][j];
+  if (threadIdx.x == 0) d->kq = k;
 }
 
 // x = V y, wy = W y, r = wy - theta x, t = M^-1 r with M = theta - diag
@@ -418,7 +427,7 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
   double theta = 0.0, rn = 0.0;
   int it = 0;
   for (; it < maxit; ++it) {
-    HCI_LAUNCH(k_jacobi, 1, 32, 0, st)(D.d, k);
+    HCI_LAUNCH(k_jacobi, 1, JW * 32, 0, st)(D.d, k);
     HCI_LAUNCH(k_ritz, D.nblk, DBLOCK, 0, st)(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
     HCI_LAUNCH(k_reduce, 1, 32 * 3, 0, st)(D.part, D.nblk, 3, D.d->ols);
     HCI_CUDA(ctx, cudaGetLastError());

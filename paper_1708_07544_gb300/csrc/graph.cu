@@ -649,8 +649,9 @@ __global__ void k_count_old_cols(const int64_t* __restrict__ rp, const int32_t* 
   }
 }
 
-// T records {x = old column (row to append to), y = entry index in the new
-// rows' CSR}, written in CSR order (deterministic)
+// T records {x = old column (row to append to) | emitting new row q << 32,
+// y = entry index in the new rows' CSR}, written in CSR order
+// (deterministic); the sort keys on the low 32 bits of x only
 __global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t nrows,
                          int64_t nold, const int64_t* __restrict__ base, ulonglong2* __restrict__ T) {
   const int lane = threadIdx.x & 31;
@@ -667,7 +668,8 @@ __global__ void k_emit_T(const int64_t* __restrict__ rp, const int32_t* __restri
         ok = j < nold;
       }
       const unsigned m = __ballot_sync(0xffffffffu, ok);
-      if (ok) T[w + __popc(m & ((1u << lane) - 1u))] = make_ulonglong2((uint64_t)j, (uint64_t)k);
+      if (ok)
+        T[w + __popc(m & ((1u << lane) - 1u))] = make_ulonglong2((uint64_t)j | ((uint64_t)q << 32), (uint64_t)k);
       w += __popc(m);
     }
   }
@@ -728,8 +730,7 @@ __global__ void k_move_old_rows(const int64_t* __restrict__ start_old, const int
                                 int64_t nold, const int32_t* col_src, const double* val_src,
                                 const int64_t* __restrict__ start2, int32_t* col_dst, double* val_dst,
                                 const ulonglong2* __restrict__ T, const int64_t* __restrict__ tstart,
-                                const int64_t* __restrict__ hist, const int64_t* __restrict__ rpN, int64_t nnew,
-                                const double* __restrict__ valN) {
+                                const int64_t* __restrict__ hist, const double* __restrict__ valN) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -755,15 +756,9 @@ __global__ void k_move_old_rows(const int64_t* __restrict__ start_old, const int
     }
     const int64_t t0 = tstart[r];
     for (int64_t k = lane; k < tn; k += 32) {
-      const int64_t e = (int64_t)T[t0 + k].y;
-      int64_t lo = 0, hi = nnew;
-      while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (rpN[mid] <= e) lo = mid;
-        else hi = mid;
-      }
-      col_dst[dst + len + k] = (int32_t)(nold + lo);
-      val_dst[dst + len + k] = valN[e];
+      const ulonglong2 t = T[t0 + k];
+      col_dst[dst + len + k] = (int32_t)(nold + (int64_t)(t.x >> 32));
+      val_dst[dst + len + k] = valN[t.y];
     }
   }
 }
@@ -1399,7 +1394,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   HCI_LAUNCH(k_move_old_rows, grid_for(nold * 32, 256), 256, 0, st)(
       bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), nold, bp<int32_t>(G.col), bp<double>(G.val),
       bp<int64_t>(G.rowstart), col_dst, val_dst, bp<ulonglong2>(S.T), bp<int64_t>(S.tstart), bp<int64_t>(S.hist),
-      bp<int64_t>(S.rpN), nnew, bp<double>(S.valN));
+      bp<double>(S.valN));
   HCI_LAUNCH(k_place_new_rows, gw, 256, 0, st)(nold, nnew, bp<int64_t>(S.rpN), bp<int32_t>(S.colN),
                                                 bp<double>(S.valN), bp<int64_t>(G.rowstart), col_dst, val_dst);
   HCI_CUDA(ctx, cudaGetLastError());
