@@ -26,34 +26,40 @@ struct DavDev {
   int kq;                 // size of Qp (0: none)
 };
 
-// partial[b][j] = sum over this block's elements of V_j . w (j < k)
-template <int MAXK>
+// partial[b][j] = sum over this block's elements of V_j . w (j < k); the
+// vectors come in groups of DOTS_GROUP (blockIdx.y = group), which keeps the
+// accumulators few and the kernel at full occupancy for any k
+constexpr int DOTS_GROUP = 8;
+
 __global__ void __launch_bounds__(DBLOCK) k_dots(const double* __restrict__ V, int64_t ld, int k,
                                                  const double* __restrict__ w, int64_t n, double* __restrict__ partial) {
-  double acc[MAXK];
+  const int j0 = blockIdx.y * DOTS_GROUP;
+  const int kg = k - j0 < DOTS_GROUP ? k - j0 : DOTS_GROUP;
+  const double* Vg = V + (int64_t)j0 * ld;
+  double acc[DOTS_GROUP];
 #pragma unroll
-  for (int j = 0; j < MAXK; ++j) acc[j] = 0.0;
+  for (int j = 0; j < DOTS_GROUP; ++j) acc[j] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double wv = w[i];
 #pragma unroll
-    for (int j = 0; j < MAXK; ++j)
-      if (j < k) acc[j] = fma(V[(int64_t)j * ld + i], wv, acc[j]);
+    for (int j = 0; j < DOTS_GROUP; ++j)
+      if (j < kg) acc[j] = fma(Vg[(int64_t)j * ld + i], wv, acc[j]);
   }
-  __shared__ double red[DBLOCK / 32][MAXK];
+  __shared__ double red[DBLOCK / 32][DOTS_GROUP];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < MAXK; ++j) {
-    if (j < k) {
+  for (int j = 0; j < DOTS_GROUP; ++j) {
+    if (j < kg) {
       double a = acc[j];
       for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       if (lane == 0) red[wid][j] = a;
     }
   }
   __syncthreads();
-  if (threadIdx.x < k) {
+  if (threadIdx.x < kg) {
     double s = 0.0;
     for (int w2 = 0; w2 < DBLOCK / 32; ++w2) s += red[w2][threadIdx.x];
-    partial[(int64_t)blockIdx.x * LDG + threadIdx.x] = s;
+    partial[(int64_t)blockIdx.x * LDG + j0 + threadIdx.x] = s;
   }
 }
 
@@ -367,8 +373,8 @@ struct Dav {
   int nblk;
 
   hci_status dots(const double* Vb, int k, const double* w, double* out) {
-    if (k <= 8) HCI_LAUNCH(k_dots<8>, nblk, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part);
-    else HCI_LAUNCH(k_dots<LDG>, nblk, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part);
+    const dim3 grid((unsigned)nblk, (unsigned)((k + DOTS_GROUP - 1) / DOTS_GROUP));
+    HCI_LAUNCH(k_dots, grid, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part);
     HCI_LAUNCH(k_reduce, 1, 32 * LDG, 0, ctx->st)(part, nblk, k, out);
     HCI_CUDA(ctx, cudaGetLastError());
     return HCI_OK;
