@@ -17,6 +17,11 @@ What each function follows:
 * ``hci``         -- the variational stage V^{mu+1} = V^mu + C^mu(eps1)
                      (Sec. II.A, Fig. 1) iterated until C^mu is empty.
 * ``rdm12``       -- the variational RDMs by their definition (Sec. IV).
+* ``pt2``         -- the screened Epstein-Nesbet correction E2(eps2),
+                     Eq. (pt_hci) of Sec. II.B, by enumerating every single
+                     and double of every D_i (terms with |H_ai c_i| > eps2
+                     kept; pinned against numerators taken from the
+                     Jordan-Wigner FCI matrix).
 * ``rotate`` / ``gradient`` -- vHCISCF gradient Eq. (vdedk2): the
                      derivative of the rotated integrals contracted with
                      the RDMs, chained through U = exp(kappa) (Sec. III.B).
@@ -63,6 +68,7 @@ def _lib():
         L.orc_sel_copy.argtypes = [P, P, P]
         L.orc_sel_free.argtypes = [P]
         L.orc_rdm12.argtypes = [ctypes.c_int, P, i64, P, P, P]
+        L.orc_pt2.argtypes = [ctypes.c_int, P, P, d, P, P, i64, d, d, P, P]
         L.orc_num_threads.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -135,6 +141,21 @@ def sigma_rows(inst, keys, c, rows) -> np.ndarray:
     _lib().orc_sigma_rows(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), len(keys), _p(c),
                           _p(rows), len(rows), _p(out))
     return out
+
+
+def pt2(inst, keys, c, eps2, e0):
+    """Screened second-order Epstein-Nesbet correction (Sec. II.B,
+    Eq. pt_hci): E2 = sum over D_a outside V of (sum'_i H_ai c_i)^2 /
+    (e0 - H_aa), the screened sum keeping the terms with |H_ai c_i| > eps2
+    (strict, as for eps1).  Returns (E2, |C(eps2)|)."""
+    P = Problem.of(inst)
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    e2 = ctypes.c_double(0.0)
+    n_ext = ctypes.c_int64(0)
+    _lib().orc_pt2(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), _p(c), len(keys), float(eps2), float(e0),
+                   ctypes.byref(e2), ctypes.byref(n_ext))
+    return e2.value, n_ext.value
 
 
 def select(inst, keys, c, eps1, band=1e-12, sources=None):

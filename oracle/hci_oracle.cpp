@@ -320,6 +320,60 @@ void* orc_select(int n, const double* h, const double* eri, const uint64_t* keys
   }
   return s;
 }
+// Second-order Epstein-Nesbet correction with screening (Sec. II.B,
+// Eq. pt_hci):  E2 = sum over D_a not in V of (sum'_i H_ai c_i)^2 / (e0 - H_aa),
+// where the screened sum keeps the terms with |H_ai c_i| > eps2 and D_a
+// belongs to C(eps2) when at least one term is kept.  Every single and double
+// of every D_i is enumerated.  Each thread owns the targets of one hash
+// class and adds their terms in ascending source order; the contributions
+// are summed in ascending key order, so the result does not depend on the
+// number of threads.
+void orc_pt2(int n, const double* h, const double* eri, double ecore, const uint64_t* keys, const double* c,
+             int64_t nV, double eps2, double e0, double* e2, int64_t* n_ext) {
+  Ham H{n, h, eri, ecore};
+  Index idx(keys, nV);
+#ifdef _OPENMP
+  int nt = omp_get_max_threads();
+#else
+  int nt = 1;
+#endif
+  std::vector<std::vector<std::pair<Key, double>>> contrib((size_t)nt);
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    int tid = omp_get_thread_num();
+#else
+    int tid = 0;
+#endif
+    std::unordered_map<Key, double, KeyHash> num;
+    KeyHash kh;
+    for (int64_t i = 0; i < nV; ++i) {
+      const double ci = c[i];
+      for_each_excitation(H, keys[2 * i], keys[2 * i + 1], [&](uint64_t a, uint64_t b, double v) {
+        const Key k{a, b};
+        if ((int)(kh(k) % (size_t)nt) != tid) return;
+        const double t = v * ci;
+        if (!(std::fabs(t) > eps2)) return;
+        if (idx.find(a, b) >= 0) return;
+        num[k] += t;
+      });
+    }
+    auto& out = contrib[(size_t)tid];
+    out.reserve(num.size());
+    for (auto& kv : num) {
+      const double haa = diag_element(H, kv.first.a, kv.first.b);
+      out.emplace_back(kv.first, kv.second * kv.second / (e0 - haa));
+    }
+  }
+  std::vector<std::pair<Key, double>> all;
+  for (auto& v : contrib) all.insert(all.end(), v.begin(), v.end());
+  std::sort(all.begin(), all.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  double sum = 0.0;
+  for (auto& kv : all) sum += kv.second;
+  *e2 = sum;
+  *n_ext = (int64_t)all.size();
+}
+
 int64_t orc_sel_count(void* p) { return (int64_t)((Selection*)p)->f.size(); }
 void orc_sel_copy(void* p, uint64_t* keys, double* f) {
   Selection* s = (Selection*)p;
