@@ -120,6 +120,20 @@ hci_status hci_sigma(hci_ctx* ctx, const uint64_t* keys, int64_t nV, const doubl
 hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout,
                         double* energy, double tol, int maxit, int* iters);
 
+/* Second-order Epstein-Nesbet correction with screening (Sec. II.B,
+ * Eq. pt_hci):
+ *   E2(eps2) = sum over D_a not in V of (sum'_i H_ai c_i)^2 / (e0 - H_aa),
+ * the screened sum keeping the terms with |H_ai c_i| > eps2 (eps2 <= 0: every
+ * single and double of V); D_a is in C(eps2) when one of its terms is kept.
+ * keys: device [nV][2], strictly ascending; c: device [nV], the normalised
+ * state on V; e0: its variational energy (including e_core).  The (target,
+ * term) pairs are processed in hash classes of at most about max_pairs
+ * pairs (0: 2^26), so device memory stays near 64 bytes x max_pairs.
+ * e2: host out; n_ext: host out, |C(eps2)| (may be NULL).  Synchronises.
+ * Builds the heat-bath lists if needed. */
+hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV, double e0,
+                   int64_t max_pairs, double* e2, int64_t* n_ext);
+
 /* Spin-summed variational RDMs (Sec. IV, Gamma^{c,c}; accumulated over the
  * connections of V):
  *   rdm1[p*n+q]            = sum_s <a+_ps a_qs>

@@ -27,7 +27,7 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
-           "hci_solve_batch"]
+           "hci_solve_batch", "hci_pt2"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -67,6 +67,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_sigma.argtypes = [V, V, I64, V, V, I]
     L.hci_davidson.argtypes = [V, V, I64, V, P(D), D, I, P(I)]
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
+    L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64)]
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
@@ -178,6 +179,16 @@ def hci_davidson(ctx, keys, c0=None, tol=1e-10, maxit=400, allow_unconverged=Fal
     if not (allow_unconverged and st == HCI_ERR_NOT_CONVERGED):
         _check(st, ctx)
     return e.value, c, it.value
+
+
+def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0):
+    """Screened second-order Epstein-Nesbet correction; returns (E2, |C(eps2)|)."""
+    L = load()
+    e2 = ctypes.c_double(0.0)
+    n_ext = ctypes.c_int64(0)
+    _check(L.hci_pt2(ctx, float(eps2), _ptr(keys), _ptr(c), keys.shape[0], float(e0), int(max_pairs),
+                     ctypes.byref(e2), ctypes.byref(n_ext)), ctx)
+    return e2.value, n_ext.value
 
 
 def hci_rdm12(ctx, keys, c, norb):

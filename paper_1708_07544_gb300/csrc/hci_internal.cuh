@@ -84,6 +84,7 @@ struct hci_ctx {
   Graph graph;
   // scratch
   DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items, s_rdmw, s_rdmh;
+  DevBuf p2_vals, p2_vals2, p2_ref;   // perturbative correction
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
   IncScratch inc;
@@ -146,6 +147,9 @@ hci_status scan_i64(hci_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, in
 // Stable LSD radix sort of 128-bit keys (a = high word, b = low word) on
 // the low `bits_a` / `bits_b` bits.  Result in keys (tmp is scratch of same size).
 hci_status sort_keys(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, int64_t n, int bits_a, int bits_b);
+// the same, carrying one double per key (vals, with vtmp as scratch)
+hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals, double* vtmp, int64_t n, int bits_a,
+                      int bits_b);
 // 64-bit content hash of a key array (device result).
 hci_status hash_keys(hci_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t* hash_host);
 // Checks that keys are strictly ascending (device reduction); *ok_host = 1 if sorted.

@@ -2,6 +2,8 @@
 // heat-bath walk over the sorted double-excitation lists, exact singles
 // behind an upper-bound screen, sort-based deduplication against V, and the
 // sorted merge V^{mu+1} = V^mu + C^mu.
+#include <algorithm>
+
 #include "hci_internal.cuh"
 
 namespace {
@@ -38,7 +40,24 @@ struct WalkArgs {
   unsigned long long* nitems;
   const double* f_ref;             // [2][n][n] single-excitation rows of the aufbau determinant
   uint64_t ref_a, ref_b;
+  // perturbative mode (vals != nullptr): every emitted target also gets its
+  // term H_ai c_i, emitted only when |H_ai c_i| > eps1 and the target's hash
+  // class is `part` of `npart`
+  double* vals;
+  int npart, part;
+  const double* eri;
 };
+
+__device__ __forceinline__ uint64_t key_mix(ulonglong2 k) {
+  uint64_t x = k.x * 0x9E3779B97F4A7C15ull ^ (k.y + 0x632BE59BD9B4E019ull + (k.x << 6) + (k.x >> 2));
+  x ^= x >> 31; x *= 0xBF58476D1CE4E5B9ull; x ^= x >> 29;
+  return x;
+}
+
+// perturbative mode: keep the term and the target?
+__device__ __forceinline__ bool pt_keep(const WalkArgs& A, ulonglong2 key, double term) {
+  return fabs(term) > A.eps1 && (A.npart <= 1 || (int)(key_mix(key) % (uint64_t)A.npart) == A.part);
+}
 
 __device__ __forceinline__ void tri_decode_dev(int t, int& lo, int& hi) {
   int h = (int)((1.0 + sqrt(1.0 + 8.0 * (double)t)) * 0.5);
@@ -48,8 +67,8 @@ __device__ __forceinline__ void tri_decode_dev(int t, int& lo, int& hi) {
   lo = t - h * (h - 1) / 2;
 }
 
-// Warp-aggregated append of one optional key per lane.
-__device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, const WalkArgs& A) {
+// Warp-aggregated append of one optional key (and term) per lane.
+__device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, double term, const WalkArgs& A) {
   const int lane = threadIdx.x & 31;
   unsigned m = __ballot_sync(0xffffffffu, emit);
   if (!m) return;
@@ -58,7 +77,10 @@ __device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, const WalkA
   base = __shfl_sync(0xffffffffu, base, 0);
   if (emit) {
     unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-    if ((int64_t)idx < A.cap) A.out[idx] = key;
+    if ((int64_t)idx < A.cap) {
+      A.out[idx] = key;
+      if (A.vals) A.vals[idx] = term;
+    }
   }
 }
 
@@ -193,10 +215,13 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_exec(WalkArgs A, int64_
     const ulonglong2 k = A.keys[w.x];
     const int sk = w.y & 3, sp = (w.y >> 2) & 63, sq = (w.y >> 8) & 63, sl = w.y >> 14;
     const uint16_t* tg = sk == 2 ? A.opp_tgt + (int64_t)sl * A.Lo : A.same_tgt + (int64_t)sl * A.Ls;
+    const double ci = A.vals ? A.c[w.x] : 0.0;
+    const int64_t n = A.n;
     for (int k0 = w.z; k0 < w.w; k0 += 32) {
       const int e = k0 + lane;
       bool emit = false;
       ulonglong2 key = k;
+      double term = 0.0;
       if (e < w.w) {
         const uint16_t tt = tg[e];
         const int r = tt & 0xff, s2 = tt >> 8;
@@ -217,8 +242,21 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_exec(WalkArgs A, int64_
             key.y = k.y ^ (1ull << sq) ^ (1ull << s2);
           }
         }
+        if (emit && A.vals) {
+          // signed <D_a|H|D_i> (same rule as the graph's elements), times c_i
+          double v;
+          if (sk == 2) {
+            v = exc_phase(k.x, sp, r) * exc_phase(k.y, sq, s2) * A.eri[((sp * n + r) * n + sq) * n + s2];
+          } else {
+            const uint64_t s0 = sk == 0 ? k.x : k.y;
+            const double ph = exc_phase(s0, sp, r) * exc_phase(s0 ^ (1ull << sp) ^ (1ull << r), sq, s2);
+            v = ph * (A.eri[((sp * n + r) * n + sq) * n + s2] - A.eri[((sp * n + s2) * n + sq) * n + r]);
+          }
+          term = v * ci;
+          emit = pt_keep(A, key, term);
+        }
       }
-      warp_emit(emit, key, A);
+      warp_emit(emit, key, term, A);
     }
   }
 }
@@ -293,6 +331,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
       int t = base + lane;
       bool emit = false;
       ulonglong2 key = k;
+      double term = 0.0;
       if (t < P) {
         int spin = t < Pa ? 0 : 1;
         int u = spin == 0 ? t : t - Pa;
@@ -301,9 +340,10 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
         int nocc = spin == 0 ? A.na : A.nb;
         int nvirt = n - nocc;
         const int p = s_ov[w][spin][0][u / nvirt], r = s_ov[w][spin][1][u % nvirt];
-        if (A.accept_all) {
+        if (A.accept_all && !A.vals) {
           emit = true;
-        } else if (s_bound[p * n + r] * absc > A.eps1 && single_tight(A, spin, p, r, s, o, s_bound[p * n + r]) * absc > A.eps1) {
+        } else if (A.accept_all || (s_bound[p * n + r] * absc > A.eps1 &&
+                                    single_tight(A, spin, p, r, s, o, s_bound[p * n + r]) * absc > A.eps1)) {
           atomicAdd(&A.walkstat[1], 1ull);
           double v = A.h[p * n + r];
           const double* js = A.jk_same + ((int64_t)p * n + r) * n;
@@ -313,13 +353,15 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
             if ((o >> x) & 1ull) v += jo[x];
           }
           emit = fabs(v) * absc > A.eps1;
+          term = exc_phase(s, p, r) * v * A.c[i];
         }
         if (emit) {
           uint64_t ns = s ^ (1ull << p) ^ (1ull << r);
           if (spin == 0) key.x = ns; else key.y = ns;
+          if (A.vals) emit = pt_keep(A, key, term);
         }
       }
-      warp_emit(emit, key, A);
+      warp_emit(emit, key, term, A);
     }
   }
 }
@@ -456,6 +498,7 @@ extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys
   A.f_ref = bp<double>(L.f_ref);
   A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
   A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
+  A.vals = nullptr; A.npart = 1; A.part = 0; A.eri = bp<double>(ctx->eri);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   A.counter = bp<unsigned long long>(ctx->s_counter);
   // candidate buffer: grow and rerun when the first guess overflows
@@ -520,5 +563,246 @@ extern "C" hci_status hci_merge(hci_ctx* ctx, const uint64_t* keys, const double
     HCI_LAUNCH(k_merge_new, grid_for(n_new, 256), 256, 0, ctx->st)(V, nV, N, n_new, O, out_c);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_MERGE);
+  return HCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Second-order Epstein-Nesbet correction with screening (Sec. II.B,
+// Eq. pt_hci): the walk and the singles emit every target D_a with its term
+// H_ai c_i when |H_ai c_i| > eps2; the (target, term) pairs are sorted by
+// target, targets in V are dropped, and each remaining target contributes
+// (sum of its terms)^2 / (E0 - H_aa).  The targets are processed in hash
+// classes so that at most max_pairs pairs are held at once.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Aufbau reference R for diagonal elements by differences, over spin
+// orbitals k (alpha 0..n-1, beta n..2n-1): g_kl = (kk|ll) - [same spin] (kl|lk),
+// F_k = h_kk + sum_{l in R, l != k} g_kl, E_R = e_core + sum_{k in R} h_kk +
+// sum_{k<l in R} g_kl.  out = [E_R, F (2n), g (2n x 2n)].
+__global__ void k_pt2_ref(int n, const double* __restrict__ h, const double* __restrict__ eri, double ecore,
+                          uint64_t ra, uint64_t rb, double* __restrict__ out) {
+  const int m = 2 * n;
+  double* F = out + 1;
+  double* g = out + 1 + m;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int k = t / m, l = t % m, p = k % n, q = l % n;
+    double v = eri[(((int64_t)p * n + p) * n + q) * n + q];
+    if ((k < n) == (l < n)) v -= eri[(((int64_t)p * n + q) * n + q) * n + p];
+    g[t] = k == l ? 0.0 : v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    double f = h[(k % n) * n + (k % n)];
+    for (int l = 0; l < m; ++l) {
+      const bool occ = l < n ? ((ra >> l) & 1ull) : ((rb >> (l - n)) & 1ull);
+      if (occ && l != k) f += g[k * m + l];
+    }
+    F[k] = f;
+  }
+  if (threadIdx.x == 0) {
+    double e = ecore;
+    for (int k = 0; k < m; ++k) {
+      if (!(k < n ? ((ra >> k) & 1ull) : ((rb >> (k - n)) & 1ull))) continue;
+      e += h[(k % n) * n + (k % n)];
+      for (int l = k + 1; l < m; ++l)
+        if (l < n ? ((ra >> l) & 1ull) : ((rb >> (l - n)) & 1ull)) e += g[k * m + l];
+    }
+    out[0] = e;
+  }
+}
+
+// H_aa = E_R + sum_k d_k F_k + sum_{k<l} d_k d_l g_kl over the spin orbitals
+// where D_a differs from R (d = +1 occupied in D_a only, -1 in R only)
+__device__ __forceinline__ double pt2_diag(const double* s_ref, int n, ulonglong2 key, uint64_t ra, uint64_t rb) {
+  const int m = 2 * n;
+  const double* F = s_ref + 1;
+  const double* g = s_ref + 1 + m;
+  const uint64_t da = key.x ^ ra, db = key.y ^ rb;
+  double e = s_ref[0];
+  for (uint64_t x = da; x; x &= x - 1) {
+    const int k = __ffsll((long long)x) - 1;
+    const double dk = ((key.x >> k) & 1ull) ? 1.0 : -1.0;
+    e += dk * F[k];
+    for (uint64_t y = x & (x - 1); y; y &= y - 1) {
+      const int l = __ffsll((long long)y) - 1;
+      e += dk * (((key.x >> l) & 1ull) ? 1.0 : -1.0) * g[k * m + l];
+    }
+    for (uint64_t y = db; y; y &= y - 1) {
+      const int l = __ffsll((long long)y) - 1;
+      e += dk * (((key.y >> l) & 1ull) ? 1.0 : -1.0) * g[k * m + n + l];
+    }
+  }
+  for (uint64_t x = db; x; x &= x - 1) {
+    const int k = __ffsll((long long)x) - 1;
+    const double dk = ((key.y >> k) & 1ull) ? 1.0 : -1.0;
+    e += dk * F[n + k];
+    for (uint64_t y = x & (x - 1); y; y &= y - 1) {
+      const int l = __ffsll((long long)y) - 1;
+      e += dk * (((key.y >> l) & 1ull) ? 1.0 : -1.0) * g[(n + k) * m + n + l];
+    }
+  }
+  return e;
+}
+
+// On the first pair of every run of equal targets (sorted): the run's terms
+// summed, the target dropped when it is in V, else contrib = sum^2 /
+// (e0 - H_aa) and ext = 1; zero on every other pair.
+__global__ void k_pt2_terms(const ulonglong2* __restrict__ t, const double* __restrict__ v, int64_t m,
+                            const ulonglong2* __restrict__ V, int64_t nV, int n, const double* __restrict__ ref,
+                            uint64_t ra, uint64_t rb, double e0, double* __restrict__ contrib,
+                            int64_t* __restrict__ ext) {
+  extern __shared__ double s_ref[];
+  const int nref = 1 + 2 * n + 4 * n * n;
+  for (int u = threadIdx.x; u < nref; u += blockDim.x) s_ref[u] = ref[u];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double cv = 0.0;
+    int64_t e = 0;
+    const ulonglong2 key = t[i];
+    if (i == 0 || !key_eq(key, t[i - 1])) {
+      const int64_t pos = lower_bound(V, nV, key);
+      if (!(pos < nV && key_eq(V[pos], key))) {
+        double num = 0.0;
+        for (int64_t j = i; j < m && key_eq(t[j], key); ++j) num += v[j];
+        cv = num * num / (e0 - pt2_diag(s_ref, n, key, ra, rb));
+        e = 1;
+      }
+    }
+    contrib[i] = cv;
+    ext[i] = e;
+  }
+}
+
+constexpr int PT2_SUM_BLOCKS = 1024;
+
+// part[b] = sum of a[] over block b's contiguous slice, in order
+__global__ void k_sum_slices_d(const double* __restrict__ a, int64_t m, double* __restrict__ part) {
+  __shared__ double red[256];
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < m ? lo + per : m;
+  double s = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += a[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_parts_d(const double* __restrict__ part, int np, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < np; ++b) s += part[b];
+    *out = s;
+  }
+}
+
+}  // namespace
+
+extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV,
+                              double e0, int64_t max_pairs, double* e2, int64_t* n_ext) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_pt2: null context");
+  if (!e2) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: e2 is NULL");
+  *e2 = 0.0;
+  if (n_ext) *n_ext = 0;
+  if (nV < 0 || max_pairs < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: negative size");
+  if (nV > 0 && (!keys || !c)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: null keys or c");
+  if (nV == 0) return HCI_OK;
+  HCI_TRY(hci_build_lists(ctx));
+  int ok = 0;
+  HCI_TRY(check_sorted(ctx, keys, nV, &ok));
+  if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: keys are not strictly ascending");
+  cudaStream_t st = ctx->st;
+  const int n = ctx->n;
+  Lists& L = ctx->lists;
+  WalkArgs A;
+  A.n = n; A.na = ctx->na; A.nb = ctx->nb;
+  A.keys = reinterpret_cast<const ulonglong2*>(keys);
+  A.c = c; A.nV = nV; A.eps1 = eps2; A.accept_all = eps2 <= 0.0 ? 1 : 0;
+  A.opp_mag = bp<double>(L.opp_mag); A.opp_tgt = bp<uint16_t>(L.opp_tgt); A.Lo = L.len_opp;
+  A.same_mag = bp<double>(L.same_mag); A.same_tgt = bp<uint16_t>(L.same_tgt); A.Ls = L.len_same;
+  A.max_dbl = L.max_opp > L.max_same ? L.max_opp : L.max_same;
+  A.h = bp<double>(ctx->h); A.jk_same = bp<double>(ctx->jk_same); A.j_opp = bp<double>(ctx->j_opp);
+  A.single_bound = bp<double>(L.single_bound); A.max_single = L.max_single;
+  A.list_max = bp<double>(L.list_max);
+  A.f_ref = bp<double>(L.f_ref);
+  A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
+  A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
+  A.eri = bp<double>(ctx->eri);
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  A.counter = bp<unsigned long long>(ctx->s_counter);
+  // counting walk: every kept pair is counted, none stored
+  HCI_TRY(ensure_buf(ctx, ctx->s_cand, 16));
+  HCI_TRY(ensure_buf(ctx, ctx->p2_vals, 16));
+  A.out = bp<ulonglong2>(ctx->s_cand);
+  A.vals = bp<double>(ctx->p2_vals);
+  A.cap = 0;
+  A.npart = 1; A.part = 0;
+  int64_t total = 0;
+  HCI_TRY(run_walk(ctx, A, &total));
+  if (total == 0) return HCI_OK;
+  const int64_t per = max_pairs > 0 ? max_pairs : ((int64_t)1 << 26);
+  const int64_t np64 = (total + per - 1) / per;
+  if (np64 > (1 << 20)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: max_pairs too small for %lld pairs",
+                                        (long long)total);
+  const int npart = (int)np64;
+  // aufbau reference of the diagonal elements
+  const size_t nref = 1 + 2 * (size_t)n + 4 * (size_t)n * n;
+  HCI_TRY(ensure_buf(ctx, ctx->p2_ref, nref * 8 + (PT2_SUM_BLOCKS + 1) * 8));
+  double* ref = bp<double>(ctx->p2_ref);
+  double* part = ref + nref;
+  double* dsum = part + PT2_SUM_BLOCKS;
+  HCI_LAUNCH(k_pt2_ref, 1, 256, 0, st)(n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, A.ref_a, A.ref_b,
+                                       ref);
+  HCI_CUDA(ctx, cudaGetLastError());
+  double acc = 0.0;
+  int64_t next_total = 0;
+  int64_t cap = total / npart + total / (8 * (int64_t)npart) + 4096;
+  for (int pc = 0; pc < npart; ++pc) {
+    A.npart = npart;
+    A.part = pc;
+    int64_t m = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)cap * 16));
+      HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)cap * 8));
+      A.out = bp<ulonglong2>(ctx->s_cand);
+      A.vals = bp<double>(ctx->p2_vals);
+      A.cap = (int64_t)std::min(ctx->s_cand.bytes / 16, ctx->p2_vals.bytes / 8);
+      HCI_TRY(run_walk(ctx, A, &m));
+      if (m <= A.cap) break;
+      cap = m + m / 8 + 4096;
+    }
+    if (m > A.cap) return hci_fail(ctx, HCI_ERR_CUDA, "hci_pt2: pair count changed between runs");
+    if (m == 0) continue;
+    HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)m * 16));
+    HCI_TRY(ensure_buf(ctx, ctx->p2_vals2, (size_t)m * 8));
+    HCI_TRY(sort_pairs(ctx, bp<uint64_t>(ctx->s_cand), bp<uint64_t>(ctx->s_cand2), bp<double>(ctx->p2_vals),
+                       bp<double>(ctx->p2_vals2), m, n, n));
+    HCI_TRY(ensure_buf(ctx, ctx->s_flags, (size_t)(2 * m + 1) * 8));
+    int64_t* ext = bp<int64_t>(ctx->s_flags);
+    int64_t* ext_scan = ext + m;
+    double* contrib = bp<double>(ctx->p2_vals2);
+    const size_t sm = nref * 8;
+    HCI_CUDA(ctx, cudaFuncSetAttribute(k_pt2_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HCI_LAUNCH(k_pt2_terms, grid_for(m, 256), 256, sm, st)(bp<ulonglong2>(ctx->s_cand), bp<double>(ctx->p2_vals), m,
+                                                          A.keys, nV, n, ref, A.ref_a, A.ref_b, e0, contrib, ext);
+    HCI_LAUNCH(k_sum_slices_d, PT2_SUM_BLOCKS, 256, 0, st)(contrib, m, part);
+    HCI_LAUNCH(k_sum_parts_d, 1, 32, 0, st)(part, PT2_SUM_BLOCKS, dsum);
+    int64_t* cnt_dev = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+    HCI_TRY(scan_i64(ctx, ext, ext_scan, m, cnt_dev));
+    HCI_CUDA(ctx, cudaGetLastError());
+    double hs = 0.0;
+    int64_t hc = 0;
+    HCI_CUDA(ctx, cudaMemcpyAsync(&hs, dsum, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&hc, cnt_dev, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    acc += hs;
+    next_total += hc;
+  }
+  *e2 = acc;
+  if (n_ext) *n_ext = next_total;
   return HCI_OK;
 }
