@@ -3,7 +3,8 @@ can follow: sampled rows of H c, the selection criterion on sampled
 sources (a converged space yields no new determinant, Sec. II.A), the RDM
 invariants and E = sum h rdm1 + 1/2 sum (pq|rs) rdm2 (Sec. IV), and the
 vHCISCF gradient (Eq. vdedk2) against central finite differences at fixed V
-and against the oracle's chain rule applied to the GPU RDMs.
+and against the oracle's chain rule applied to the GPU RDMs, and the
+perturbative correction's independence of its hash-class split.
 """
 import numpy as np
 import pytest
@@ -101,6 +102,14 @@ def test_df44_bench_configuration(pkg):
     try:
         assert 1e6 < out["keys"].shape[0] < 1e7
         r1, r2 = check_space(pkg, s, out, R, 1e-4, nrows=8, nsrc=16)
+        # perturbative correction at eps2 = 1e-5 (Sec. II.B, Eq. pt_hci): the
+        # same sum when the targets are split into many hash classes; a
+        # looser eps2 keeps fewer targets and a smaller |E2|
+        e2, n2 = s.pt2(out["keys"], out["c"], 1e-5, out["E"])
+        e2m, n2m = s.pt2(out["keys"], out["c"], 1e-5, out["E"], max_pairs=1 << 22)
+        e2l, n2l = s.pt2(out["keys"], out["c"], 3e-5, out["E"])
+        assert abs(e2m - e2) < 1e-12 * abs(e2) and n2m == n2
+        assert e2 < e2l < 0.0 and n2l < n2
     finally:
         s.close()
     # backward through the rotation against the oracle's chain rule on the same RDMs
