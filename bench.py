@@ -298,11 +298,13 @@ def gpu_arm(args):
     pt2 = {}
     if args.pt2_reps > 0:
         ts = []
+        torch.cuda.nvtx.range_push("pt2")
         for _ in range(args.pt2_reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             e2v, n_ext = s.pt2(keys, c, PT2_EPS2, last["E"])
             ts.append(time.perf_counter() - t0)
+        torch.cuda.nvtx.range_pop()
         pt2 = {"eps2": PT2_EPS2, "E2": e2v, "E_var_plus_E2": last["E"] + e2v, "targets": n_ext,
                "seconds": round(statistics.median(ts), 4), "reps": args.pt2_reps}
     s.close()

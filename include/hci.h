@@ -127,8 +127,9 @@ hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* 
  * single and double of V); D_a is in C(eps2) when one of its terms is kept.
  * keys: device [nV][2], strictly ascending; c: device [nV], the normalised
  * state on V; e0: its variational energy (including e_core).  The (target,
- * term) pairs are processed in hash classes of at most about max_pairs
- * pairs (0: 2^26), so device memory stays near 64 bytes x max_pairs.
+ * term) pairs are processed at once when they number at most max_pairs
+ * (0: 2^28), else in hash classes of about max_pairs pairs; device memory
+ * stays near 64 bytes x max_pairs.
  * e2: host out; n_ext: host out, |C(eps2)| (may be NULL).  Synchronises.
  * Builds the heat-bath lists if needed. */
 hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV, double e0,

@@ -342,6 +342,21 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
         const int p = s_ov[w][spin][0][u / nvirt], r = s_ov[w][spin][1][u % nvirt];
         if (A.accept_all && !A.vals) {
           emit = true;
+        } else if (A.vals) {
+          // perturbative mode: the element from the aufbau value plus the
+          // orbitals where the strings differ (no bit-exact decision needed)
+          if (A.accept_all || s_bound[p * n + r] * absc > A.eps1) {
+            const uint64_t rs = spin == 0 ? A.ref_a : A.ref_b, ro = spin == 0 ? A.ref_b : A.ref_a;
+            const double* js = A.jk_same + ((int64_t)p * n + r) * n;
+            const double* jo = A.j_opp + ((int64_t)p * n + r) * n;
+            double v = A.f_ref[((int64_t)spin * n + p) * n + r];
+            for (uint64_t mm = s & ~rs; mm; mm &= mm - 1) v += js[__ffsll((long long)mm) - 1];
+            for (uint64_t mm = rs & ~s; mm; mm &= mm - 1) v -= js[__ffsll((long long)mm) - 1];
+            for (uint64_t mm = o & ~ro; mm; mm &= mm - 1) v += jo[__ffsll((long long)mm) - 1];
+            for (uint64_t mm = ro & ~o; mm; mm &= mm - 1) v -= jo[__ffsll((long long)mm) - 1];
+            term = exc_phase(s, p, r) * v * A.c[i];
+            emit = true;
+          }
         } else if (A.accept_all || (s_bound[p * n + r] * absc > A.eps1 &&
                                     single_tight(A, spin, p, r, s, o, s_bound[p * n + r]) * absc > A.eps1)) {
           atomicAdd(&A.walkstat[1], 1ull);
@@ -734,21 +749,6 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
   A.eri = bp<double>(ctx->eri);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   A.counter = bp<unsigned long long>(ctx->s_counter);
-  // counting walk: every kept pair is counted, none stored
-  HCI_TRY(ensure_buf(ctx, ctx->s_cand, 16));
-  HCI_TRY(ensure_buf(ctx, ctx->p2_vals, 16));
-  A.out = bp<ulonglong2>(ctx->s_cand);
-  A.vals = bp<double>(ctx->p2_vals);
-  A.cap = 0;
-  A.npart = 1; A.part = 0;
-  int64_t total = 0;
-  HCI_TRY(run_walk(ctx, A, &total));
-  if (total == 0) return HCI_OK;
-  const int64_t per = max_pairs > 0 ? max_pairs : ((int64_t)1 << 26);
-  const int64_t np64 = (total + per - 1) / per;
-  if (np64 > (1 << 20)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: max_pairs too small for %lld pairs",
-                                        (long long)total);
-  const int npart = (int)np64;
   // aufbau reference of the diagonal elements
   const size_t nref = 1 + 2 * (size_t)n + 4 * (size_t)n * n;
   HCI_TRY(ensure_buf(ctx, ctx->p2_ref, nref * 8 + (PT2_SUM_BLOCKS + 1) * 8));
@@ -758,25 +758,28 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
   HCI_LAUNCH(k_pt2_ref, 1, 256, 0, st)(n, bp<double>(ctx->h), bp<double>(ctx->eri), ctx->ecore, A.ref_a, A.ref_b,
                                        ref);
   HCI_CUDA(ctx, cudaGetLastError());
+  const int64_t per = max_pairs > 0 ? max_pairs : ((int64_t)1 << 28);
   double acc = 0.0;
   int64_t next_total = 0;
-  int64_t cap = total / npart + total / (8 * (int64_t)npart) + 4096;
-  for (int pc = 0; pc < npart; ++pc) {
+  // one hash class of targets: walk into the pair buffer (walked again with
+  // a larger buffer if it was too small), sort, reduce
+  auto run_class = [&](int npart, int pc, int64_t* m_out, bool reduce) -> hci_status {
     A.npart = npart;
     A.part = pc;
     int64_t m = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-      HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)cap * 16));
-      HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)cap * 8));
       A.out = bp<ulonglong2>(ctx->s_cand);
       A.vals = bp<double>(ctx->p2_vals);
       A.cap = (int64_t)std::min(ctx->s_cand.bytes / 16, ctx->p2_vals.bytes / 8);
       HCI_TRY(run_walk(ctx, A, &m));
-      if (m <= A.cap) break;
-      cap = m + m / 8 + 4096;
+      if (m <= A.cap || (npart == 1 && m > per)) break;
+      HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)(m + m / 8 + 4096) * 16));
+      HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)(m + m / 8 + 4096) * 8));
     }
-    if (m > A.cap) return hci_fail(ctx, HCI_ERR_CUDA, "hci_pt2: pair count changed between runs");
-    if (m == 0) continue;
+    *m_out = m;
+    if (npart == 1 && m > per) return HCI_OK;   // too many for one class: the caller splits the targets
+    if (m > A.cap) return hci_fail(ctx, HCI_ERR_CUDA, "hci_pt2: pair count changed between walks");
+    if (!reduce || m == 0) return HCI_OK;
     HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)m * 16));
     HCI_TRY(ensure_buf(ctx, ctx->p2_vals2, (size_t)m * 8));
     HCI_TRY(sort_pairs(ctx, bp<uint64_t>(ctx->s_cand), bp<uint64_t>(ctx->s_cand2), bp<double>(ctx->p2_vals),
@@ -801,6 +804,25 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
     HCI_CUDA(ctx, cudaStreamSynchronize(st));
     acc += hs;
     next_total += hc;
+    return HCI_OK;
+  };
+  HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)4096 * 16));
+  HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)4096 * 8));
+  // all targets at once when they fit max_pairs; else hash classes
+  int64_t total = 0;
+  HCI_TRY(run_class(1, 0, &total, true));
+  if (total > per) {
+    const int64_t np64 = (total + per - 1) / per;
+    if (np64 > (1 << 20))
+      return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: max_pairs too small for %lld pairs", (long long)total);
+    const int npart = (int)np64;
+    const int64_t cap = total / npart + total / (8 * (int64_t)npart) + 4096;
+    HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)cap * 16));
+    HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)cap * 8));
+    for (int pc = 0; pc < npart; ++pc) {
+      int64_t m = 0;
+      HCI_TRY(run_class(npart, pc, &m, true));
+    }
   }
   *e2 = acc;
   if (n_ext) *n_ext = next_total;
