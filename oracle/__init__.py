@@ -21,7 +21,8 @@ What each function follows:
                      Eq. (pt_hci) of Sec. II.B, by enumerating every single
                      and double of every D_i (terms with |H_ai c_i| > eps2
                      kept; pinned against numerators taken from the
-                     Jordan-Wigner FCI matrix).
+                     Jordan-Wigner FCI matrix); ``pt2_rdm`` its density
+                     matrices Gamma^dd and Gamma^dc by their definition.
 * ``rotate`` / ``gradient`` -- vHCISCF gradient Eq. (vdedk2): the
                      derivative of the rotated integrals contracted with
                      the RDMs, chained through U = exp(kappa) (Sec. III.B).
@@ -69,6 +70,7 @@ def _lib():
         L.orc_sel_free.argtypes = [P]
         L.orc_rdm12.argtypes = [ctypes.c_int, P, i64, P, P, P]
         L.orc_pt2.argtypes = [ctypes.c_int, P, P, d, P, P, i64, d, d, P, P]
+        L.orc_pt2_rdm.argtypes = [ctypes.c_int, P, P, d, P, P, i64, d, d, P, P, P, P]
         L.orc_num_threads.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -156,6 +158,23 @@ def pt2(inst, keys, c, eps2, e0):
     _lib().orc_pt2(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), _p(c), len(keys), float(eps2), float(e0),
                    ctypes.byref(e2), ctypes.byref(n_ext))
     return e2.value, n_ext.value
+
+
+def pt2_rdm(inst, keys, c, eps2, e0):
+    """Density matrices of the perturbative correction (Sec. V,
+    Computational Details), spin-summed like rdm12:
+    Gamma^dd = sum_a d_a^2 <D_a|op|D_a> and Gamma^dc = sum over the screened
+    pairs of c_i d_a <D_i|op|D_a>, d_a = (sum'_i H_ai c_i) / (e0 - H_aa),
+    the pairs being those of pt2 (|H_ai c_i| > eps2).  Returns
+    (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
+    P = Problem.of(inst)
+    n = P.norb
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    out = [np.zeros((n, n)), np.zeros((n,) * 4), np.zeros((n, n)), np.zeros((n,) * 4)]
+    _lib().orc_pt2_rdm(n, _p(P.h), _p(P.eri), P.e_core, _p(keys), _p(c), len(keys), float(eps2), float(e0),
+                       *[_p(x) for x in out])
+    return tuple(out)
 
 
 def select(inst, keys, c, eps1, band=1e-12, sources=None):

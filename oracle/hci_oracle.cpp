@@ -374,6 +374,84 @@ void orc_pt2(int n, const double* h, const double* eri, double ecore, const uint
   *n_ext = (int64_t)all.size();
 }
 
+// Density matrices of the perturbative correction (Sec. V, Computational
+// Details), in the spin-summed order of orc_rdm12:
+//   dd:  sum over D_a in C(eps2) of d_a^2 <D_a| op |D_a>
+//   dc:  sum over the screened pairs (D_i in V, D_a in C(eps2)) of
+//        c_i d_a <D_i| op |D_a>
+// with d_a = (sum'_i H_ai c_i) / (e0 - H_aa), the same screened sum as
+// orc_pt2 (a pair is kept when |H_ai c_i| > eps2).  Every operator string
+// is applied to the ket determinant and the result compared with the bra.
+static void pair_rdm(int n, uint64_t ka, uint64_t kb, uint64_t ba, uint64_t bb, double w, double* g1, double* g2) {
+  const int M = 2 * n;
+  for (int s = 0; s < 2; ++s)
+    for (int q = 0; q < n; ++q)
+      for (int p = 0; p < n; ++p) {
+        uint64_t a = ka, b = kb;
+        double sg = 1.0;
+        if (!apply_op(a, b, n, mode_of(n, q, s), false, sg)) continue;
+        if (!apply_op(a, b, n, mode_of(n, p, s), true, sg)) continue;
+        if (a == ba && b == bb) g1[(size_t)p * n + q] += w * sg;
+      }
+  for (int mq = 0; mq < M; ++mq) {
+    uint64_t a1 = ka, b1 = kb;
+    double sg1 = 1.0;
+    if (!apply_op(a1, b1, n, mq, false, sg1)) continue;
+    for (int ms = 0; ms < M; ++ms) {
+      uint64_t a2 = a1, b2 = b1;
+      double sg2 = sg1;
+      if (!apply_op(a2, b2, n, ms, false, sg2)) continue;
+      const int spinq = mq / n, spins = ms / n;
+      for (int mr = spins * n; mr < spins * n + n; ++mr) {
+        uint64_t a3 = a2, b3 = b2;
+        double sg3 = sg2;
+        if (!apply_op(a3, b3, n, mr, true, sg3)) continue;
+        for (int mp = spinq * n; mp < spinq * n + n; ++mp) {
+          uint64_t a4 = a3, b4 = b3;
+          double sg4 = sg3;
+          if (!apply_op(a4, b4, n, mp, true, sg4)) continue;
+          if (a4 != ba || b4 != bb) continue;
+          const int p = mp % n, q = mq % n, r = mr % n, s = ms % n;
+          g2[(((size_t)p * n + q) * n + r) * n + s] += w * sg4;
+        }
+      }
+    }
+  }
+}
+
+void orc_pt2_rdm(int n, const double* h, const double* eri, double ecore, const uint64_t* keys, const double* c,
+                 int64_t nV, double eps2, double e0, double* rdm1_dd, double* rdm2_dd, double* rdm1_dc,
+                 double* rdm2_dc) {
+  Ham H{n, h, eri, ecore};
+  Index idx(keys, nV);
+  std::unordered_map<Key, double, KeyHash> num;
+  std::vector<std::pair<int64_t, Key>> pairs;
+  for (int64_t i = 0; i < nV; ++i) {
+    const double ci = c[i];
+    for_each_excitation(H, keys[2 * i], keys[2 * i + 1], [&](uint64_t a, uint64_t b, double v) {
+      const double t = v * ci;
+      if (!(std::fabs(t) > eps2)) return;
+      if (idx.find(a, b) >= 0) return;
+      const Key k{a, b};
+      num[k] += t;
+      pairs.emplace_back(i, k);
+    });
+  }
+  std::unordered_map<Key, double, KeyHash> d;
+  for (auto& kv : num) d[kv.first] = kv.second / (e0 - diag_element(H, kv.first.a, kv.first.b));
+  const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+  std::fill(rdm1_dd, rdm1_dd + n2, 0.0);
+  std::fill(rdm2_dd, rdm2_dd + n4, 0.0);
+  std::fill(rdm1_dc, rdm1_dc + n2, 0.0);
+  std::fill(rdm2_dc, rdm2_dc + n4, 0.0);
+  for (auto& kv : d) pair_rdm(n, kv.first.a, kv.first.b, kv.first.a, kv.first.b, kv.second * kv.second, rdm1_dd, rdm2_dd);
+  for (auto& pr : pairs) {
+    const int64_t i = pr.first;
+    const Key& k = pr.second;
+    pair_rdm(n, k.a, k.b, keys[2 * i], keys[2 * i + 1], c[i] * d[k], rdm1_dc, rdm2_dc);
+  }
+}
+
 int64_t orc_sel_count(void* p) { return (int64_t)((Selection*)p)->f.size(); }
 void orc_sel_copy(void* p, uint64_t* keys, double* f) {
   Selection* s = (Selection*)p;
