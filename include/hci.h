@@ -130,10 +130,19 @@ hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* 
  * term) pairs are processed at once when they number at most max_pairs
  * (0: 2^28), else in hash classes of about max_pairs pairs; device memory
  * stays near 64 bytes x max_pairs.
- * e2: host out; n_ext: host out, |C(eps2)| (may be NULL).  Synchronises.
- * Builds the heat-bath lists if needed. */
+ * e2: host out; n_ext: host out, |C(eps2)| (may be NULL).
+ * Density matrices of the correction (Sec. V, Computational Details), in
+ * the spin-summed order of hci_rdm12, with d_a = (sum'_i H_ai c_i) /
+ * (e0 - H_aa) the first-order coefficients:
+ *   rdm?_dd = sum over D_a in C(eps2) of d_a^2 <D_a| op |D_a>
+ *   rdm?_dc = sum over the screened pairs of c_i d_a <D_i| op |D_a>
+ * (the pairs are those of the screened sum: |H_ai c_i| > eps2).  rdm1_dd,
+ * rdm1_dc: device [n][n]; rdm2_dd, rdm2_dc: device [n][n][n][n]; give all
+ * four or none (NULL: not computed).  Synchronises.  Builds the heat-bath
+ * lists if needed. */
 hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV, double e0,
-                   int64_t max_pairs, double* e2, int64_t* n_ext);
+                   int64_t max_pairs, double* e2, int64_t* n_ext, double* rdm1_dd, double* rdm2_dd,
+                   double* rdm1_dc, double* rdm2_dc);
 
 /* Spin-summed variational RDMs (Sec. IV, Gamma^{c,c}; accumulated over the
  * connections of V):

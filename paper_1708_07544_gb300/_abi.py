@@ -67,7 +67,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_sigma.argtypes = [V, V, I64, V, V, I]
     L.hci_davidson.argtypes = [V, V, I64, V, P(D), D, I, P(I)]
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
-    L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64)]
+    L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V]
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
@@ -181,14 +181,21 @@ def hci_davidson(ctx, keys, c0=None, tol=1e-10, maxit=400, allow_unconverged=Fal
     return e.value, c, it.value
 
 
-def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0):
-    """Screened second-order Epstein-Nesbet correction; returns (E2, |C(eps2)|)."""
+def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None):
+    """Screened second-order Epstein-Nesbet correction; returns (E2, |C(eps2)|),
+    and with norb given also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
     L = load()
     e2 = ctypes.c_double(0.0)
     n_ext = ctypes.c_int64(0)
+    rd = [None] * 4
+    if norb is not None:
+        shapes = [(norb, norb), (norb,) * 4, (norb, norb), (norb,) * 4]
+        rd = [torch.empty(sh, dtype=torch.float64, device=keys.device) for sh in shapes]
     _check(L.hci_pt2(ctx, float(eps2), _ptr(keys), _ptr(c), keys.shape[0], float(e0), int(max_pairs),
-                     ctypes.byref(e2), ctypes.byref(n_ext)), ctx)
-    return e2.value, n_ext.value
+                     ctypes.byref(e2), ctypes.byref(n_ext), *[_ptr(x) if x is not None else None for x in rd]), ctx)
+    if norb is None:
+        return e2.value, n_ext.value
+    return e2.value, n_ext.value, tuple(rd)
 
 
 def hci_rdm12(ctx, keys, c, norb):

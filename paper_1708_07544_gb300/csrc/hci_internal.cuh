@@ -84,7 +84,7 @@ struct hci_ctx {
   Graph graph;
   // scratch
   DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items, s_rdmw, s_rdmh;
-  DevBuf p2_vals, p2_vals2, p2_ref;   // perturbative correction
+  DevBuf p2_vals, p2_vals2, p2_ref, p2_src, p2_src2, p2_d, p2_dd;   // perturbative correction
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
   IncScratch inc;
@@ -147,9 +147,10 @@ hci_status scan_i64(hci_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, in
 // Stable LSD radix sort of 128-bit keys (a = high word, b = low word) on
 // the low `bits_a` / `bits_b` bits.  Result in keys (tmp is scratch of same size).
 hci_status sort_keys(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, int64_t n, int bits_a, int bits_b);
-// the same, carrying one double per key (vals, with vtmp as scratch)
-hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals, double* vtmp, int64_t n, int bits_a,
-                      int bits_b);
+// the same, carrying one double (vals, with vtmp as scratch) and one int32
+// (idx, with itmp as scratch) per key; either may be NULL
+hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals, double* vtmp, int32_t* idx,
+                      int32_t* itmp, int64_t n, int bits_a, int bits_b);
 // 64-bit content hash of a key array (device result).
 hci_status hash_keys(hci_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t* hash_host);
 // Checks that keys are strictly ascending (device reduction); *ok_host = 1 if sorted.
@@ -160,6 +161,11 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 // sigma on vectors in internal order (rows/columns of the cached graph)
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec);
+// density matrices of the perturbative correction (rdm.cu)
+hci_status pt2_rdm_begin(hci_ctx* ctx);
+hci_status pt2_rdm_pairs(hci_ctx* ctx, const ulonglong2* V, const double* c, const ulonglong2* tgt, const int32_t* src,
+                         const double* d, int64_t m);
+hci_status pt2_rdm_finish(hci_ctx* ctx, double* r1dd, double* r2dd, double* r1dc, double* r2dc);
 // vectors between the caller's (sorted) order and the graph's internal order
 hci_status to_internal(hci_ctx* ctx, const double* sorted, double* internal, int nvec);
 hci_status to_sorted(hci_ctx* ctx, const double* internal, double* sorted, int nvec);

@@ -120,7 +120,8 @@ __global__ void k_rs_hist(const ulonglong2* __restrict__ keys, int64_t n, int wo
 
 __global__ void k_rs_scatter(const ulonglong2* __restrict__ in, ulonglong2* __restrict__ out, int64_t n,
                              int word, int shift, const int64_t* __restrict__ offs, int64_t ntiles,
-                             const double* __restrict__ pin, double* __restrict__ pout) {
+                             const double* __restrict__ pin, double* __restrict__ pout,
+                             const int32_t* __restrict__ qin, int32_t* __restrict__ qout) {
   __shared__ int64_t base[256];
   __shared__ int wcnt[RS_BLOCK / 32][256];
   __shared__ int tot[256];
@@ -153,6 +154,7 @@ __global__ void k_rs_scatter(const ulonglong2* __restrict__ in, ulonglong2* __re
       const int64_t dst = base[d] + wcnt[warp][d] + rank;
       out[dst] = key;
       if (pin) pout[dst] = pin[i];
+      if (qin) qout[dst] = qin[i];
     }
     __syncthreads();
     base[tid] += tot[tid];
@@ -209,11 +211,11 @@ hci_status scan_i64(hci_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, in
 }
 
 hci_status sort_keys(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, int64_t n, int bits_a, int bits_b) {
-  return sort_pairs(ctx, keys, tmp, nullptr, nullptr, n, bits_a, bits_b);
+  return sort_pairs(ctx, keys, tmp, nullptr, nullptr, nullptr, nullptr, n, bits_a, bits_b);
 }
 
-hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals, double* vtmp, int64_t n, int bits_a,
-                      int bits_b) {
+hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals, double* vtmp, int32_t* idx,
+                      int32_t* itmp, int64_t n, int bits_a, int bits_b) {
   if (n <= 1) return HCI_OK;
   int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
   HCI_TRY(ensure_buf(ctx, ctx->s_hist, (size_t)ntiles * 256 * 2 * sizeof(int64_t)));
@@ -223,15 +225,19 @@ hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals,
   ulonglong2* b = reinterpret_cast<ulonglong2*>(tmp);
   double* va = vals;
   double* vb = vtmp;
+  int32_t* ia = idx;
+  int32_t* ib = itmp;
   int passes = 0;
   for (int word = 0; word < 2; ++word) {
     int bits = word == 0 ? bits_b : bits_a;
     for (int shift = 0; shift < bits; shift += 8) {
       HCI_LAUNCH(k_rs_hist, (unsigned)ntiles, RS_BLOCK, 0, ctx->st)(a, n, word, shift, hist, ntiles);
       HCI_TRY(scan_i64(ctx, hist, offs, ntiles * 256, nullptr));
-      HCI_LAUNCH(k_rs_scatter, (unsigned)ntiles, RS_BLOCK, 0, ctx->st)(a, b, n, word, shift, offs, ntiles, va, vb);
+      HCI_LAUNCH(k_rs_scatter, (unsigned)ntiles, RS_BLOCK, 0, ctx->st)(a, b, n, word, shift, offs, ntiles, va, vb,
+                                                                       ia, ib);
       ulonglong2* t = a; a = b; b = t;
       double* tv = va; va = vb; vb = tv;
+      int32_t* ti = ia; ia = ib; ib = ti;
       ++passes;
     }
   }
@@ -239,6 +245,7 @@ hci_status sort_pairs(hci_ctx* ctx, uint64_t* keys, uint64_t* tmp, double* vals,
   if (passes & 1) {
     HCI_CUDA(ctx, cudaMemcpyAsync(keys, tmp, (size_t)n * 16, cudaMemcpyDeviceToDevice, ctx->st));
     if (vals) HCI_CUDA(ctx, cudaMemcpyAsync(vals, vtmp, (size_t)n * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    if (idx) HCI_CUDA(ctx, cudaMemcpyAsync(idx, itmp, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->st));
   }
   return HCI_OK;
 }

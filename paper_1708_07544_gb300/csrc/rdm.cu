@@ -44,6 +44,61 @@ struct RdmAcc {
   uint64_t ref_a, ref_b;
 };
 
+// <ki| op |kj> of one connected pair (a single or double excitation apart)
+// with weight cc, accumulated into R (doubles into Hh, singles into S1 / Dt /
+// Dx as described above)
+__device__ __forceinline__ void rdm_accumulate(const RdmAcc& R, int n, ulonglong2 ki, ulonglong2 kj, double cc) {
+  const uint64_t xa = ki.x ^ kj.x, xb = ki.y ^ kj.y;
+  const int da = __popcll(xa), db = __popcll(xb);
+  if (da + db == 2) {
+    // single a -> b in spin S
+    const int S = da == 2 ? 0 : 1;
+    const uint64_t sj = S == 0 ? kj.x : kj.y, oj = S == 0 ? kj.y : kj.x;
+    const uint64_t x = S == 0 ? xa : xb;
+    const int a = __ffsll((long long)(sj & x)) - 1;
+    const int bb = __ffsll((long long)(x & ~sj)) - 1;
+    const double w = cc * exc_phase(sj, a, bb);
+    atomicAdd(&R.S1[((int64_t)S * n + bb) * n + a], w);
+    const uint64_t rs = S == 0 ? R.ref_a : R.ref_b, ro = S == 0 ? R.ref_b : R.ref_a;
+    double* dt = R.Dt + ((int64_t)bb * n + a) * n;
+    double* dx = R.Dx + ((int64_t)bb * n + a) * n;
+    for (uint64_t m = sj & ~rs; m; m &= m - 1) {
+      const int kk = __ffsll((long long)m) - 1;
+      atomicAdd(dt + kk, w);
+      atomicAdd(dx + kk, w);
+    }
+    for (uint64_t m = rs & ~sj; m; m &= m - 1) {
+      const int kk = __ffsll((long long)m) - 1;
+      atomicAdd(dt + kk, -w);
+      atomicAdd(dx + kk, -w);
+    }
+    for (uint64_t m = oj & ~ro; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, w);
+    for (uint64_t m = ro & ~oj; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, -w);
+  } else if (da == 4 || db == 4) {
+    const uint64_t sj = da == 4 ? kj.x : kj.y;
+    const uint64_t x = da == 4 ? xa : xb;
+    uint64_t holes = sj & x, parts = x & ~sj;
+    const int a = __ffsll((long long)holes) - 1; holes &= holes - 1;
+    const int bh = __ffsll((long long)holes) - 1;
+    const int cp = __ffsll((long long)parts) - 1; parts &= parts - 1;
+    const int d = __ffsll((long long)parts) - 1;
+    const double s1 = exc_phase(sj, a, cp);
+    const uint64_t t = sj ^ (1ull << a) ^ (1ull << cp);
+    const double w = cc * s1 * exc_phase(t, bh, d);
+    add2(R.Hh, n, cp, a, d, bh, w);
+    add2(R.Hh, n, d, bh, cp, a, w);
+    add2(R.Hh, n, cp, bh, d, a, -w);
+    add2(R.Hh, n, d, a, cp, bh, -w);
+  } else {
+    // alpha a -> c, beta b -> d
+    const int a = __ffsll((long long)(kj.x & xa)) - 1, cp = __ffsll((long long)(ki.x & xa)) - 1;
+    const int bh = __ffsll((long long)(kj.y & xb)) - 1, d = __ffsll((long long)(ki.y & xb)) - 1;
+    const double w = cc * exc_phase(kj.x, a, cp) * exc_phase(kj.y, bh, d);
+    add2(R.Hh, n, cp, a, d, bh, w);
+    add2(R.Hh, n, d, bh, cp, a, w);
+  }
+}
+
 __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulonglong2* __restrict__ V, int64_t nV,
                                                               const double* __restrict__ c,
                                                               const int64_t* __restrict__ rowptr,
@@ -62,58 +117,9 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
     for (int64_t k = b + lane; k < e; k += 32) {
       const int64_t j = col[k];
       if (j <= i) continue;
-      const ulonglong2 kj = V[j];
       const double cc = ci * c[j];
       if (cc == 0.0) continue;
-      const uint64_t xa = ki.x ^ kj.x, xb = ki.y ^ kj.y;
-      const int da = __popcll(xa), db = __popcll(xb);
-      if (da + db == 2) {
-        // single a -> b in spin S
-        const int S = da == 2 ? 0 : 1;
-        const uint64_t sj = S == 0 ? kj.x : kj.y, oj = S == 0 ? kj.y : kj.x;
-        const uint64_t x = S == 0 ? xa : xb;
-        const int a = __ffsll((long long)(sj & x)) - 1;
-        const int bb = __ffsll((long long)(x & ~sj)) - 1;
-        const double w = cc * exc_phase(sj, a, bb);
-        atomicAdd(&R.S1[((int64_t)S * n + bb) * n + a], w);
-        const uint64_t rs = S == 0 ? R.ref_a : R.ref_b, ro = S == 0 ? R.ref_b : R.ref_a;
-        double* dt = R.Dt + ((int64_t)bb * n + a) * n;
-        double* dx = R.Dx + ((int64_t)bb * n + a) * n;
-        for (uint64_t m = sj & ~rs; m; m &= m - 1) {
-          const int kk = __ffsll((long long)m) - 1;
-          atomicAdd(dt + kk, w);
-          atomicAdd(dx + kk, w);
-        }
-        for (uint64_t m = rs & ~sj; m; m &= m - 1) {
-          const int kk = __ffsll((long long)m) - 1;
-          atomicAdd(dt + kk, -w);
-          atomicAdd(dx + kk, -w);
-        }
-        for (uint64_t m = oj & ~ro; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, w);
-        for (uint64_t m = ro & ~oj; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, -w);
-      } else if (da == 4 || db == 4) {
-        const uint64_t sj = da == 4 ? kj.x : kj.y;
-        const uint64_t x = da == 4 ? xa : xb;
-        uint64_t holes = sj & x, parts = x & ~sj;
-        const int a = __ffsll((long long)holes) - 1; holes &= holes - 1;
-        const int bh = __ffsll((long long)holes) - 1;
-        const int cp = __ffsll((long long)parts) - 1; parts &= parts - 1;
-        const int d = __ffsll((long long)parts) - 1;
-        const double s1 = exc_phase(sj, a, cp);
-        const uint64_t t = sj ^ (1ull << a) ^ (1ull << cp);
-        const double w = cc * s1 * exc_phase(t, bh, d);
-        add2(R.Hh, n, cp, a, d, bh, w);
-        add2(R.Hh, n, d, bh, cp, a, w);
-        add2(R.Hh, n, cp, bh, d, a, -w);
-        add2(R.Hh, n, d, a, cp, bh, -w);
-      } else {
-        // alpha a -> c, beta b -> d
-        const int a = __ffsll((long long)(kj.x & xa)) - 1, cp = __ffsll((long long)(ki.x & xa)) - 1;
-        const int bh = __ffsll((long long)(kj.y & xb)) - 1, d = __ffsll((long long)(ki.y & xb)) - 1;
-        const double w = cc * exc_phase(kj.x, a, cp) * exc_phase(kj.y, bh, d);
-        add2(R.Hh, n, cp, a, d, bh, w);
-        add2(R.Hh, n, d, bh, cp, a, w);
-      }
+      rdm_accumulate(R, n, ki, V[j], cc);
     }
   }
 }
@@ -141,17 +147,94 @@ __device__ __forceinline__ double rdm_single_terms(const RdmAcc& R, int n, int p
   return v;
 }
 
-// rdm2 += Hh + Hh^T + single terms and their transpose; rdm1 += S1 + S1^T
-__global__ void k_rdm_finish(int n, RdmAcc R, double* __restrict__ r1, double* __restrict__ r2) {
+// rdm2 += Hh + single terms, rdm1 += S1 (the accumulated orientation), and
+// with sym also their transposes (the other orientation of every pair)
+__global__ void k_rdm_finish(int n, RdmAcc R, double* __restrict__ r1, double* __restrict__ r2, int sym) {
   const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
     const int s = (int)(t % n), r = (int)((t / n) % n), q = (int)((t / n2) % n), p = (int)(t / (n2 * n));
-    const int64_t tt = (((int64_t)q * n + p) * n + s) * n + r;
-    r2[t] += R.Hh[t] + R.Hh[tt] + rdm_single_terms(R, n, p, q, r, s) + rdm_single_terms(R, n, q, p, s, r);
+    double v = R.Hh[t] + rdm_single_terms(R, n, p, q, r, s);
+    if (sym) {
+      const int64_t tt = (((int64_t)q * n + p) * n + s) * n + r;
+      v += R.Hh[tt] + rdm_single_terms(R, n, q, p, s, r);
+    }
+    r2[t] += v;
     if (t < n2) {
       const int pp = (int)(t / n), qq = (int)(t % n);
-      r1[t] += R.S1[t] + R.S1[n2 + t] + R.S1[(int64_t)qq * n + pp] + R.S1[n2 + (int64_t)qq * n + pp];
+      double w = R.S1[t] + R.S1[n2 + t];
+      if (sym) w += R.S1[(int64_t)qq * n + pp] + R.S1[n2 + (int64_t)qq * n + pp];
+      r1[t] += w;
     }
+  }
+}
+
+// Transition density of screened perturbative pairs: <V[src[j]]| op |tgt[j]>
+// with weight c[src[j]] d[j] (pairs with d = 0 skipped).
+__global__ void k_rdm_pairs(int n, const ulonglong2* __restrict__ V, const double* __restrict__ c,
+                            const ulonglong2* __restrict__ tgt, const int32_t* __restrict__ src,
+                            const double* __restrict__ d, int64_t m, RdmAcc R) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const double dj = d[j];
+    if (dj == 0.0) continue;
+    const int32_t i = src[j];
+    rdm_accumulate(R, n, V[i], tgt[j], c[i] * dj);
+  }
+}
+
+// Occupation correlation sum_a w_a n(a) n(a)^T of the distinct targets (the
+// first pair of each run of equal keys, w_a = d_a^2), over spin orbitals
+// (alpha 0..n-1, beta n..2n-1), split about the aufbau occupations n_R:
+// n(a) = n_R + delta_a, so acc = [W = sum w, u = sum w delta (2n),
+// Q = sum w delta delta^T (2n x 2n)], block-local in shared memory first.
+__global__ void k_dd_acc(int n, const ulonglong2* __restrict__ tgt, const double* __restrict__ d, int64_t m,
+                         uint64_t ra, uint64_t rb, double* __restrict__ acc) {
+  extern __shared__ double s_acc[];
+  const int mm = 2 * n, nacc = 1 + mm + mm * mm;
+  for (int t = threadIdx.x; t < nacc; t += blockDim.x) s_acc[t] = 0.0;
+  __syncthreads();
+  double* su = s_acc + 1;
+  double* sq = s_acc + 1 + mm;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 key = tgt[j];
+    if (j > 0) {
+      const ulonglong2 prev = tgt[j - 1];
+      if (prev.x == key.x && prev.y == key.y) continue;
+    }
+    const double dj = d[j];
+    if (dj == 0.0) continue;
+    const double w = dj * dj;
+    atomicAdd(&s_acc[0], w);
+    const uint64_t da = key.x ^ ra, db = key.y ^ rb;
+    for (int sk = 0; sk < 2; ++sk)
+      for (uint64_t x = sk ? db : da; x; x &= x - 1) {
+        const int ko = __ffsll((long long)x) - 1;
+        const int k = sk * n + ko;
+        const double dk = (((sk ? key.y : key.x) >> ko) & 1ull) ? 1.0 : -1.0;
+        atomicAdd(&su[k], w * dk);
+        for (int sl = 0; sl < 2; ++sl)
+          for (uint64_t y = sl ? db : da; y; y &= y - 1) {
+            const int lo = __ffsll((long long)y) - 1;
+            const double dl = (((sl ? key.y : key.x) >> lo) & 1ull) ? 1.0 : -1.0;
+            atomicAdd(&sq[k * mm + sl * n + lo], w * dk * dl);
+          }
+      }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nacc; t += blockDim.x)
+    if (s_acc[t] != 0.0) atomicAdd(&acc[t], s_acc[t]);
+}
+
+// M = W n_R n_R^T + n_R u^T + u n_R^T + Q, the layout k_diag_rdm reads
+__global__ void k_dd_matrix(int n, const double* __restrict__ acc, uint64_t ra, uint64_t rb, double* __restrict__ M) {
+  const int mm = 2 * n;
+  const double W = acc[0];
+  const double* u = acc + 1;
+  const double* Q = acc + 1 + mm;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < mm * mm; t += gridDim.x * blockDim.x) {
+    const int k = t / mm, l = t % mm;
+    const double nk = (k < n ? ((ra >> k) & 1ull) : ((rb >> (k - n)) & 1ull)) ? 1.0 : 0.0;
+    const double nl = (l < n ? ((ra >> l) & 1ull) : ((rb >> (l - n)) & 1ull)) ? 1.0 : 0.0;
+    M[t] = W * nk * nl + nk * u[l] + u[k] * nl + Q[t];
   }
 }
 
@@ -422,9 +505,64 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
                                                          bp<int64_t>(ctx->graph.rowptr),
                                                          bp<int64_t>(ctx->graph.rowstart),
                                                          bp<int32_t>(ctx->graph.col), R, queue);
-  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, rdm1, rdm2);
+  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, rdm1, rdm2, 1);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  return HCI_OK;
+}
+
+// Density matrices of the perturbative correction, accumulated over the
+// hash classes of hci_pt2: begin (clear), pairs (once per class), finish.
+static RdmAcc pt2_acc(hci_ctx* ctx) {
+  const size_t n = (size_t)ctx->n, n2 = n * n, n4 = n2 * n2;
+  RdmAcc R;
+  R.Hh = bp<double>(ctx->s_rdmh);
+  R.S1 = R.Hh + n4;
+  R.Dt = R.S1 + 2 * n2;
+  R.Dx = R.Dt + n2 * n;
+  R.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
+  R.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
+  return R;
+}
+
+hci_status pt2_rdm_begin(hci_ctx* ctx) {
+  const size_t n = (size_t)ctx->n, n2 = n * n, n4 = n2 * n2, m = 2 * n;
+  HCI_TRY(ensure_buf(ctx, ctx->s_rdmh, (n4 + 2 * n2 + 2 * n2 * n) * 8));
+  HCI_CUDA(ctx, cudaMemsetAsync(ctx->s_rdmh.p, 0, (n4 + 2 * n2 + 2 * n2 * n) * 8, ctx->st));
+  HCI_TRY(ensure_buf(ctx, ctx->p2_dd, (1 + m + 2 * m * m) * 8));
+  HCI_CUDA(ctx, cudaMemsetAsync(ctx->p2_dd.p, 0, (1 + m + 2 * m * m) * 8, ctx->st));
+  return HCI_OK;
+}
+
+hci_status pt2_rdm_pairs(hci_ctx* ctx, const ulonglong2* V, const double* c, const ulonglong2* tgt, const int32_t* src,
+                         const double* d, int64_t m) {
+  if (m <= 0) return HCI_OK;
+  const int n = ctx->n, mm = 2 * n;
+  RdmAcc R = pt2_acc(ctx);
+  HCI_LAUNCH(k_rdm_pairs, grid_for(m, 256), 256, 0, ctx->st)(n, V, c, tgt, src, d, m, R);
+  const size_t sm = (size_t)(1 + mm + mm * mm) * 8;
+  HCI_CUDA(ctx, cudaFuncSetAttribute(k_dd_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  HCI_LAUNCH(k_dd_acc, grid_for(m, 256, 152 * 2), 256, sm, ctx->st)(n, tgt, d, m, R.ref_a, R.ref_b,
+                                                                     bp<double>(ctx->p2_dd));
+  HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}
+
+hci_status pt2_rdm_finish(hci_ctx* ctx, double* r1dd, double* r2dd, double* r1dc, double* r2dc) {
+  const int n = ctx->n, mm = 2 * n;
+  const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+  cudaStream_t st = ctx->st;
+  RdmAcc R = pt2_acc(ctx);
+  HCI_CUDA(ctx, cudaMemsetAsync(r1dc, 0, n2 * 8, st));
+  HCI_CUDA(ctx, cudaMemsetAsync(r2dc, 0, n4 * 8, st));
+  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, r1dc, r2dc, 0);
+  double* acc = bp<double>(ctx->p2_dd);
+  double* M = acc + 1 + mm + mm * mm;
+  HCI_LAUNCH(k_dd_matrix, grid_for((int64_t)mm * mm, 256), 256, 0, st)(n, acc, R.ref_a, R.ref_b, M);
+  HCI_CUDA(ctx, cudaMemsetAsync(r1dd, 0, n2 * 8, st));
+  HCI_CUDA(ctx, cudaMemsetAsync(r2dd, 0, n4 * 8, st));
+  HCI_LAUNCH(k_diag_rdm, grid_for((int64_t)n2, 256), 256, 0, st)(n, M, r1dd, r2dd);
+  HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
 }

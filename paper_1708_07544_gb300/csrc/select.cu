@@ -44,6 +44,7 @@ struct WalkArgs {
   // term H_ai c_i, emitted only when |H_ai c_i| > eps1 and the target's hash
   // class is `part` of `npart`
   double* vals;
+  int32_t* srcs;         // perturbative mode with density matrices: source determinant of each pair
   int npart, part;
   const double* eri;
 };
@@ -68,7 +69,7 @@ __device__ __forceinline__ void tri_decode_dev(int t, int& lo, int& hi) {
 }
 
 // Warp-aggregated append of one optional key (and term) per lane.
-__device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, double term, const WalkArgs& A) {
+__device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, double term, int src, const WalkArgs& A) {
   const int lane = threadIdx.x & 31;
   unsigned m = __ballot_sync(0xffffffffu, emit);
   if (!m) return;
@@ -80,6 +81,7 @@ __device__ __forceinline__ void warp_emit(bool emit, ulonglong2 key, double term
     if ((int64_t)idx < A.cap) {
       A.out[idx] = key;
       if (A.vals) A.vals[idx] = term;
+      if (A.srcs) A.srcs[idx] = src;
     }
   }
 }
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_exec(WalkArgs A, int64_
           emit = pt_keep(A, key, term);
         }
       }
-      warp_emit(emit, key, term, A);
+      warp_emit(emit, key, term, w.x, A);
     }
   }
 }
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
           if (A.vals) emit = pt_keep(A, key, term);
         }
       }
-      warp_emit(emit, key, term, A);
+      warp_emit(emit, key, term, (int)i, A);
     }
   }
 }
@@ -513,7 +515,7 @@ extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys
   A.f_ref = bp<double>(L.f_ref);
   A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
   A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
-  A.vals = nullptr; A.npart = 1; A.part = 0; A.eri = bp<double>(ctx->eri);
+  A.vals = nullptr; A.srcs = nullptr; A.npart = 1; A.part = 0; A.eri = bp<double>(ctx->eri);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   A.counter = bp<unsigned long long>(ctx->s_counter);
   // candidate buffer: grow and rerun when the first guess overflows
@@ -666,7 +668,7 @@ __device__ __forceinline__ double pt2_diag(const double* s_ref, int n, ulonglong
 __global__ void k_pt2_terms(const ulonglong2* __restrict__ t, const double* __restrict__ v, int64_t m,
                             const ulonglong2* __restrict__ V, int64_t nV, int n, const double* __restrict__ ref,
                             uint64_t ra, uint64_t rb, double e0, double* __restrict__ contrib,
-                            int64_t* __restrict__ ext) {
+                            int64_t* __restrict__ ext, double* __restrict__ dpair) {
   extern __shared__ double s_ref[];
   const int nref = 1 + 2 * n + 4 * n * n;
   for (int u = threadIdx.x; u < nref; u += blockDim.x) s_ref[u] = ref[u];
@@ -677,12 +679,20 @@ __global__ void k_pt2_terms(const ulonglong2* __restrict__ t, const double* __re
     const ulonglong2 key = t[i];
     if (i == 0 || !key_eq(key, t[i - 1])) {
       const int64_t pos = lower_bound(V, nV, key);
+      double da = 0.0;
+      int64_t end = i + 1;
       if (!(pos < nV && key_eq(V[pos], key))) {
         double num = 0.0;
-        for (int64_t j = i; j < m && key_eq(t[j], key); ++j) num += v[j];
-        cv = num * num / (e0 - pt2_diag(s_ref, n, key, ra, rb));
+        for (end = i; end < m && key_eq(t[end], key); ++end) num += v[end];
+        da = num / (e0 - pt2_diag(s_ref, n, key, ra, rb));
+        cv = num * da;
         e = 1;
+      } else if (dpair) {
+        while (end < m && key_eq(t[end], key)) ++end;
       }
+      // first-order coefficient d_a on every pair of the run (0 for D_a in V)
+      if (dpair)
+        for (int64_t j = i; j < end; ++j) dpair[j] = da;
     }
     contrib[i] = cv;
     ext[i] = e;
@@ -718,13 +728,25 @@ __global__ void k_sum_parts_d(const double* __restrict__ part, int np, double* _
 }  // namespace
 
 extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV,
-                              double e0, int64_t max_pairs, double* e2, int64_t* n_ext) {
+                              double e0, int64_t max_pairs, double* e2, int64_t* n_ext, double* rdm1_dd,
+                              double* rdm2_dd, double* rdm1_dc, double* rdm2_dc) {
   if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_pt2: null context");
   if (!e2) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: e2 is NULL");
   *e2 = 0.0;
   if (n_ext) *n_ext = 0;
   if (nV < 0 || max_pairs < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: negative size");
   if (nV > 0 && (!keys || !c)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: null keys or c");
+  const int nrdm = (rdm1_dd != nullptr) + (rdm2_dd != nullptr) + (rdm1_dc != nullptr) + (rdm2_dc != nullptr);
+  if (nrdm != 0 && nrdm != 4) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: give all four density matrices or none");
+  const bool want_rdm = nrdm == 4;
+  if (want_rdm) {
+    const size_t n2 = (size_t)ctx->n * ctx->n;
+    HCI_CUDA(ctx, cudaMemsetAsync(rdm1_dd, 0, n2 * 8, ctx->st));
+    HCI_CUDA(ctx, cudaMemsetAsync(rdm2_dd, 0, n2 * n2 * 8, ctx->st));
+    HCI_CUDA(ctx, cudaMemsetAsync(rdm1_dc, 0, n2 * 8, ctx->st));
+    HCI_CUDA(ctx, cudaMemsetAsync(rdm2_dc, 0, n2 * n2 * 8, ctx->st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  }
   if (nV == 0) return HCI_OK;
   HCI_TRY(hci_build_lists(ctx));
   int ok = 0;
@@ -747,8 +769,10 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
   A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
   A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
   A.eri = bp<double>(ctx->eri);
+  A.srcs = nullptr;
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   A.counter = bp<unsigned long long>(ctx->s_counter);
+  if (want_rdm) HCI_TRY(pt2_rdm_begin(ctx));
   // aufbau reference of the diagonal elements
   const size_t nref = 1 + 2 * (size_t)n + 4 * (size_t)n * n;
   HCI_TRY(ensure_buf(ctx, ctx->p2_ref, nref * 8 + (PT2_SUM_BLOCKS + 1) * 8));
@@ -771,6 +795,10 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
       A.out = bp<ulonglong2>(ctx->s_cand);
       A.vals = bp<double>(ctx->p2_vals);
       A.cap = (int64_t)std::min(ctx->s_cand.bytes / 16, ctx->p2_vals.bytes / 8);
+      if (want_rdm) {
+        HCI_TRY(ensure_buf(ctx, ctx->p2_src, (size_t)A.cap * 4));
+        A.srcs = bp<int32_t>(ctx->p2_src);
+      }
       HCI_TRY(run_walk(ctx, A, &m));
       if (m <= A.cap || (npart == 1 && m > per)) break;
       HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)(m + m / 8 + 4096) * 16));
@@ -782,8 +810,18 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
     if (!reduce || m == 0) return HCI_OK;
     HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)m * 16));
     HCI_TRY(ensure_buf(ctx, ctx->p2_vals2, (size_t)m * 8));
+    int32_t* src = nullptr;
+    int32_t* src2 = nullptr;
+    double* dpair = nullptr;
+    if (want_rdm) {
+      HCI_TRY(ensure_buf(ctx, ctx->p2_src2, (size_t)m * 4));
+      HCI_TRY(ensure_buf(ctx, ctx->p2_d, (size_t)m * 8));
+      src = bp<int32_t>(ctx->p2_src);
+      src2 = bp<int32_t>(ctx->p2_src2);
+      dpair = bp<double>(ctx->p2_d);
+    }
     HCI_TRY(sort_pairs(ctx, bp<uint64_t>(ctx->s_cand), bp<uint64_t>(ctx->s_cand2), bp<double>(ctx->p2_vals),
-                       bp<double>(ctx->p2_vals2), m, n, n));
+                       bp<double>(ctx->p2_vals2), src, src2, m, n, n));
     HCI_TRY(ensure_buf(ctx, ctx->s_flags, (size_t)(2 * m + 1) * 8));
     int64_t* ext = bp<int64_t>(ctx->s_flags);
     int64_t* ext_scan = ext + m;
@@ -791,7 +829,9 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
     const size_t sm = nref * 8;
     HCI_CUDA(ctx, cudaFuncSetAttribute(k_pt2_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HCI_LAUNCH(k_pt2_terms, grid_for(m, 256), 256, sm, st)(bp<ulonglong2>(ctx->s_cand), bp<double>(ctx->p2_vals), m,
-                                                          A.keys, nV, n, ref, A.ref_a, A.ref_b, e0, contrib, ext);
+                                                          A.keys, nV, n, ref, A.ref_a, A.ref_b, e0, contrib, ext,
+                                                          dpair);
+    if (want_rdm) HCI_TRY(pt2_rdm_pairs(ctx, A.keys, c, bp<ulonglong2>(ctx->s_cand), src, dpair, m));
     HCI_LAUNCH(k_sum_slices_d, PT2_SUM_BLOCKS, 256, 0, st)(contrib, m, part);
     HCI_LAUNCH(k_sum_parts_d, 1, 32, 0, st)(part, PT2_SUM_BLOCKS, dsum);
     int64_t* cnt_dev = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
@@ -823,6 +863,10 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
       int64_t m = 0;
       HCI_TRY(run_class(npart, pc, &m, true));
     }
+  }
+  if (want_rdm) {
+    HCI_TRY(pt2_rdm_finish(ctx, rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
   }
   *e2 = acc;
   if (n_ext) *n_ext = next_total;

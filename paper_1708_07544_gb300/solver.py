@@ -50,10 +50,11 @@ class HCISolver:
     def rdm12(self, keys, c):
         return _abi.hci_rdm12(self.ctx, keys, c, self.norb)
 
-    def pt2(self, keys, c, eps2, e0, max_pairs=0):
+    def pt2(self, keys, c, eps2, e0, max_pairs=0, rdms=False):
         """Screened Epstein-Nesbet correction E2(eps2) of the state (keys, c)
-        with variational energy e0; returns (E2, |C(eps2)|)."""
-        return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs)
+        with variational energy e0; returns (E2, |C(eps2)|), and with rdms
+        also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
+        return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs, self.norb if rdms else None)
 
     def solve(self, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24):
         keys, c, e, it = _abi.hci_solve(self.ctx, eps1, max_iter, dav_tol, dav_maxit, cap)

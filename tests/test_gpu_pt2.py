@@ -101,3 +101,39 @@ def test_pt2_full_space_and_empty(pkg):
         assert e2 == 0.0 and n == 0
         e2, n = s.pt2(out["keys"][:0], out["c"][:0], 1e-6, out["E"])
         assert e2 == 0.0 and n == 0
+
+
+def _rdm_close(got, want, rel=1e-10):
+    for g, w in zip(got, want):
+        g = g.cpu().numpy()
+        assert np.abs(g - w).max() <= rel * max(1.0, np.abs(w).max()), np.abs(g - w).max()
+
+
+@pytest.mark.parametrize("name,make,nv,eps2", [
+    ("tiny7_all", lambda: hi.random_tiny(7, 3, 2, 51), 150, -1.0),
+    ("tiny7", lambda: hi.random_tiny(7, 3, 2, 51), 150, 1e-4),
+    ("polyene8_open", lambda: hi.Instance("p8o", 8, 5, 3, hi.ppp_polyene(8).h, hi.ppp_polyene(8).eri, 0.3), 300,
+     1e-5),
+])
+def test_pt2_rdm_random_space_matches_oracle(pkg, name, make, nv, eps2):
+    """Gamma^dd and Gamma^dc (Sec. V) against the oracle's definition."""
+    inst = make()
+    keys = hi.random_det_keys(inst.norb, inst.nalpha, inst.nbeta, nv, seed=nv + 61)
+    c = hi.random_vector(len(keys), seed=nv + 62)
+    e0 = float(oracle.diag(inst, keys).min()) - 0.5
+    with solver(pkg, inst) as s:
+        e2, n, rd = s.pt2(dev_keys(keys), torch.tensor(c).cuda(), eps2, e0, rdms=True)
+        e2_plain, n_plain = s.pt2(dev_keys(keys), torch.tensor(c).cuda(), eps2, e0)
+    assert close(e2, e2_plain, 1e-13) and n == n_plain
+    _rdm_close(rd, oracle.pt2_rdm(inst, keys, c, eps2, e0))
+
+
+def test_pt2_rdm_polyene8_state_and_classes(pkg, poly8_state):
+    inst, out = poly8_state
+    keys, c = out["keys"], out["c"]
+    with solver(pkg, inst) as s:
+        _, _, rd = s.pt2(keys, c, 1e-5, out["E"], rdms=True)
+        _, _, rdm = s.pt2(keys, c, 1e-5, out["E"], max_pairs=700, rdms=True)
+    want = oracle.pt2_rdm(inst, host_keys(keys), c.cpu().numpy(), 1e-5, out["E"])
+    _rdm_close(rd, want)
+    _rdm_close(rdm, [x.cpu().numpy() for x in rd], 1e-12)
