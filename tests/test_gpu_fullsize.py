@@ -110,6 +110,15 @@ def test_df44_bench_configuration(pkg):
         e2l, n2l = s.pt2(out["keys"], out["c"], 3e-5, out["E"])
         assert abs(e2m - e2) < 1e-12 * abs(e2) and n2m == n2
         assert e2 < e2l < 0.0 and n2l < n2
+        # its density matrices (Sec. V): tr Gamma^dc_1 = N <c|d> = 0,
+        # sum_pr Gamma^dd_pprr = (N - 1) tr Gamma^dd_1, Gamma^dd_1 symmetric
+        e2r, n2r, (r1dd, r2dd, r1dc, r2dc) = s.pt2(out["keys"], out["c"], 1e-5, out["E"], rdms=True)
+        assert abs(e2r - e2) < 1e-12 * abs(e2) and n2r == n2
+        r1dd, r2dd, r1dc = r1dd.cpu().numpy(), r2dd.cpu().numpy(), r1dc.cpu().numpy()
+        N = R.nalpha + R.nbeta
+        assert np.trace(r1dd) > 0.0 and abs(np.trace(r1dc)) < 1e-10
+        assert abs(np.einsum("pprr->", r2dd) - (N - 1) * np.trace(r1dd)) < 1e-8 * N * N * np.trace(r1dd)
+        assert np.abs(r1dd - r1dd.T).max() < 1e-12
     finally:
         s.close()
     # backward through the rotation against the oracle's chain rule on the same RDMs
