@@ -138,11 +138,38 @@ hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* 
  *   rdm?_dc = sum over the screened pairs of c_i d_a <D_i| op |D_a>
  * (the pairs are those of the screened sum: |H_ai c_i| > eps2).  rdm1_dd,
  * rdm1_dc: device [n][n]; rdm2_dd, rdm2_dc: device [n][n][n][n]; give all
- * four or none (NULL: not computed).  Synchronises.  Builds the heat-bath
- * lists if needed. */
+ * four or none (NULL: not computed).  grad_c: device [nV] or NULL, the
+ * derivative of E2 with respect to c at a fixed set of screened pairs,
+ * 2 sum'_a d_a H_ai (the right-hand side of the z-vector equation, Sec.
+ * III.A).  Synchronises.  Builds the heat-bath lists if needed. */
 hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV, double e0,
                    int64_t max_pairs, double* e2, int64_t* n_ext, double* rdm1_dd, double* rdm2_dd,
-                   double* rdm1_dc, double* rdm2_dc);
+                   double* rdm1_dc, double* rdm2_dc, double* grad_c);
+
+/* The z-vector equation of the HCISCF gradient (Sec. III.A, Eq. lagc): z
+ * with (H - e0) z = P rhs on V and z orthogonal to c (P = 1 - c c^T), by
+ * preconditioned conjugate gradients in the complement of c (H - e0 is
+ * positive there when c is the lowest eigenvector; preconditioner
+ * diag(H) - e0).  keys, c (normalised), rhs, z: device, sorted order.
+ * Converged when ||P (rhs - (H - e0) z)||_2 <= tol; HCI_ERR_NOT_CONVERGED
+ * after maxit iterations (z holds the last iterate).  iters: host out (may
+ * be NULL).  Synchronises. */
+hci_status hci_zvector(hci_ctx* ctx, const uint64_t* keys, int64_t nV, const double* c, double e0, const double* rhs,
+                       double* z, double tol, int maxit, int* iters);
+
+/* Relaxed density matrices of E_var + E2 (Sec. III.A, Eq. lambda) at a
+ * fixed V and a fixed set of screened pairs: with d, g = dE2/dc and
+ * Gamma^dd, Gamma^dc from hci_pt2 and z from hci_zvector(rhs = g),
+ *   Gamma = (1 - |d|^2) Gamma(c) + Gamma^dd + Gamma^dc + (Gamma^dc)^T
+ *           - 1/4 [Gamma(z + c) - Gamma(z - c)]
+ * (and the same combination of the 1-RDMs), whose contraction with the
+ * derivatives of h and (pq|rs) is d(E_var + E2); hci_rotate_backward maps
+ * it to dE/dkappa.  c: the normalised lowest eigenvector on V, e0 its
+ * energy.  e2: host out.  rdm1, rdm2: device, spin-summed order of
+ * hci_rdm12.  Synchronises. */
+hci_status hci_relaxed_rdm12(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV, double e0,
+                             int64_t max_pairs, double zv_tol, int zv_maxit, double* e2, double* rdm1,
+                             double* rdm2);
 
 /* Spin-summed variational RDMs (Sec. IV, Gamma^{c,c}; accumulated over the
  * connections of V):

@@ -27,7 +27,7 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
-           "hci_solve_batch", "hci_pt2"]
+           "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -67,7 +67,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_sigma.argtypes = [V, V, I64, V, V, I]
     L.hci_davidson.argtypes = [V, V, I64, V, P(D), D, I, P(I)]
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
-    L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V]
+    L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V, V]
+    L.hci_zvector.argtypes = [V, V, I64, V, D, V, V, D, I, P(I)]
+    L.hci_relaxed_rdm12.argtypes = [V, D, V, V, I64, D, I64, D, I, P(D), V, V]
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
@@ -181,9 +183,10 @@ def hci_davidson(ctx, keys, c0=None, tol=1e-10, maxit=400, allow_unconverged=Fal
     return e.value, c, it.value
 
 
-def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None):
+def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None, grad=False):
     """Screened second-order Epstein-Nesbet correction; returns (E2, |C(eps2)|),
-    and with norb given also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
+    and with norb given also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc), and with
+    grad also dE2/dc (appended last)."""
     L = load()
     e2 = ctypes.c_double(0.0)
     n_ext = ctypes.c_int64(0)
@@ -191,11 +194,37 @@ def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None):
     if norb is not None:
         shapes = [(norb, norb), (norb,) * 4, (norb, norb), (norb,) * 4]
         rd = [torch.empty(sh, dtype=torch.float64, device=keys.device) for sh in shapes]
+    g = torch.empty(keys.shape[0], dtype=torch.float64, device=keys.device) if grad else None
     _check(L.hci_pt2(ctx, float(eps2), _ptr(keys), _ptr(c), keys.shape[0], float(e0), int(max_pairs),
-                     ctypes.byref(e2), ctypes.byref(n_ext), *[_ptr(x) if x is not None else None for x in rd]), ctx)
-    if norb is None:
-        return e2.value, n_ext.value
-    return e2.value, n_ext.value, tuple(rd)
+                     ctypes.byref(e2), ctypes.byref(n_ext), *[_ptr(x) if x is not None else None for x in rd],
+                     _ptr(g) if g is not None else None), ctx)
+    out = (e2.value, n_ext.value)
+    if norb is not None:
+        out = out + (tuple(rd),)
+    if grad:
+        out = out + (g,)
+    return out
+
+
+def hci_zvector(ctx, keys, c, e0, rhs, tol=1e-10, maxit=500):
+    """z with (H - e0) z = P rhs, z orthogonal to c; returns (z, iterations)."""
+    L = load()
+    z = torch.empty_like(c)
+    it = ctypes.c_int(0)
+    _check(L.hci_zvector(ctx, _ptr(keys), keys.shape[0], _ptr(c), float(e0), _ptr(rhs), _ptr(z), float(tol),
+                         int(maxit), ctypes.byref(it)), ctx)
+    return z, it.value
+
+
+def hci_relaxed_rdm12(ctx, keys, c, e0, eps2, norb, max_pairs=0, zv_tol=1e-10, zv_maxit=500):
+    """Relaxed density matrices of E_var + E2; returns (E2, rdm1, rdm2)."""
+    L = load()
+    e2 = ctypes.c_double(0.0)
+    r1 = torch.empty((norb, norb), dtype=torch.float64, device=keys.device)
+    r2 = torch.empty((norb,) * 4, dtype=torch.float64, device=keys.device)
+    _check(L.hci_relaxed_rdm12(ctx, float(eps2), _ptr(keys), _ptr(c), keys.shape[0], float(e0), int(max_pairs),
+                               float(zv_tol), int(zv_maxit), ctypes.byref(e2), _ptr(r1), _ptr(r2)), ctx)
+    return e2.value, r1, r2
 
 
 def hci_rdm12(ctx, keys, c, norb):

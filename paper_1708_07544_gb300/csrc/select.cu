@@ -44,7 +44,8 @@ struct WalkArgs {
   // term H_ai c_i, emitted only when |H_ai c_i| > eps1 and the target's hash
   // class is `part` of `npart`
   double* vals;
-  int32_t* srcs;         // perturbative mode with density matrices: source determinant of each pair
+  int32_t* srcs;         // perturbative mode with sources: source determinant of each pair; vals then
+                         // holds the element H_ai instead of the term H_ai c_i
   int npart, part;
   const double* eri;
 };
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_exec(WalkArgs A, int64_
       const int e = k0 + lane;
       bool emit = false;
       ulonglong2 key = k;
-      double term = 0.0;
+      double term = 0.0, elem = 0.0;
       if (e < w.w) {
         const uint16_t tt = tg[e];
         const int r = tt & 0xff, s2 = tt >> 8;
@@ -255,10 +256,11 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_walk_exec(WalkArgs A, int64_
             v = ph * (A.eri[((sp * n + r) * n + sq) * n + s2] - A.eri[((sp * n + s2) * n + sq) * n + r]);
           }
           term = v * ci;
+          elem = v;
           emit = pt_keep(A, key, term);
         }
       }
-      warp_emit(emit, key, term, w.x, A);
+      warp_emit(emit, key, A.srcs ? elem : term, w.x, A);
     }
   }
 }
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
       int t = base + lane;
       bool emit = false;
       ulonglong2 key = k;
-      double term = 0.0;
+      double term = 0.0, elem = 0.0;
       if (t < P) {
         int spin = t < Pa ? 0 : 1;
         int u = spin == 0 ? t : t - Pa;
@@ -356,7 +358,8 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
             for (uint64_t mm = rs & ~s; mm; mm &= mm - 1) v -= js[__ffsll((long long)mm) - 1];
             for (uint64_t mm = o & ~ro; mm; mm &= mm - 1) v += jo[__ffsll((long long)mm) - 1];
             for (uint64_t mm = ro & ~o; mm; mm &= mm - 1) v -= jo[__ffsll((long long)mm) - 1];
-            term = exc_phase(s, p, r) * v * A.c[i];
+            elem = exc_phase(s, p, r) * v;
+            term = elem * A.c[i];
             emit = true;
           }
         } else if (A.accept_all || (s_bound[p * n + r] * absc > A.eps1 &&
@@ -370,7 +373,8 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
             if ((o >> x) & 1ull) v += jo[x];
           }
           emit = fabs(v) * absc > A.eps1;
-          term = exc_phase(s, p, r) * v * A.c[i];
+          elem = exc_phase(s, p, r) * v;
+          term = elem * A.c[i];
         }
         if (emit) {
           uint64_t ns = s ^ (1ull << p) ^ (1ull << r);
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
           if (A.vals) emit = pt_keep(A, key, term);
         }
       }
-      warp_emit(emit, key, term, (int)i, A);
+      warp_emit(emit, key, A.srcs ? elem : term, (int)i, A);
     }
   }
 }
@@ -668,7 +672,8 @@ __device__ __forceinline__ double pt2_diag(const double* s_ref, int n, ulonglong
 __global__ void k_pt2_terms(const ulonglong2* __restrict__ t, const double* __restrict__ v, int64_t m,
                             const ulonglong2* __restrict__ V, int64_t nV, int n, const double* __restrict__ ref,
                             uint64_t ra, uint64_t rb, double e0, double* __restrict__ contrib,
-                            int64_t* __restrict__ ext, double* __restrict__ dpair) {
+                            int64_t* __restrict__ ext, double* __restrict__ dpair, const double* __restrict__ cvec,
+                            const int32_t* __restrict__ src) {
   extern __shared__ double s_ref[];
   const int nref = 1 + 2 * n + 4 * n * n;
   for (int u = threadIdx.x; u < nref; u += blockDim.x) s_ref[u] = ref[u];
@@ -683,7 +688,7 @@ __global__ void k_pt2_terms(const ulonglong2* __restrict__ t, const double* __re
       int64_t end = i + 1;
       if (!(pos < nV && key_eq(V[pos], key))) {
         double num = 0.0;
-        for (end = i; end < m && key_eq(t[end], key); ++end) num += v[end];
+        for (end = i; end < m && key_eq(t[end], key); ++end) num += src ? v[end] * cvec[src[end]] : v[end];
         da = num / (e0 - pt2_diag(s_ref, n, key, ra, rb));
         cv = num * da;
         e = 1;
@@ -697,6 +702,13 @@ __global__ void k_pt2_terms(const ulonglong2* __restrict__ t, const double* __re
     contrib[i] = cv;
     ext[i] = e;
   }
+}
+
+// dE2/dc_i = 2 sum over the screened pairs of d_a H_ai (the pairs fixed)
+__global__ void k_pt2_grad(const int32_t* __restrict__ src, const double* __restrict__ elem,
+                           const double* __restrict__ d, int64_t m, double* __restrict__ g) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+    if (d[j] != 0.0) atomicAdd(&g[src[j]], 2.0 * d[j] * elem[j]);
 }
 
 constexpr int PT2_SUM_BLOCKS = 1024;
@@ -729,7 +741,7 @@ __global__ void k_sum_parts_d(const double* __restrict__ part, int np, double* _
 
 extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV,
                               double e0, int64_t max_pairs, double* e2, int64_t* n_ext, double* rdm1_dd,
-                              double* rdm2_dd, double* rdm1_dc, double* rdm2_dc) {
+                              double* rdm2_dd, double* rdm1_dc, double* rdm2_dc, double* grad_c) {
   if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_pt2: null context");
   if (!e2) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: e2 is NULL");
   *e2 = 0.0;
@@ -739,6 +751,8 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
   const int nrdm = (rdm1_dd != nullptr) + (rdm2_dd != nullptr) + (rdm1_dc != nullptr) + (rdm2_dc != nullptr);
   if (nrdm != 0 && nrdm != 4) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: give all four density matrices or none");
   const bool want_rdm = nrdm == 4;
+  const bool want_src = want_rdm || grad_c != nullptr;
+  if (grad_c && nV > 0) HCI_CUDA(ctx, cudaMemsetAsync(grad_c, 0, (size_t)nV * 8, ctx->st));
   if (want_rdm) {
     const size_t n2 = (size_t)ctx->n * ctx->n;
     HCI_CUDA(ctx, cudaMemsetAsync(rdm1_dd, 0, n2 * 8, ctx->st));
@@ -795,7 +809,7 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
       A.out = bp<ulonglong2>(ctx->s_cand);
       A.vals = bp<double>(ctx->p2_vals);
       A.cap = (int64_t)std::min(ctx->s_cand.bytes / 16, ctx->p2_vals.bytes / 8);
-      if (want_rdm) {
+      if (want_src) {
         HCI_TRY(ensure_buf(ctx, ctx->p2_src, (size_t)A.cap * 4));
         A.srcs = bp<int32_t>(ctx->p2_src);
       }
@@ -813,7 +827,7 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
     int32_t* src = nullptr;
     int32_t* src2 = nullptr;
     double* dpair = nullptr;
-    if (want_rdm) {
+    if (want_src) {
       HCI_TRY(ensure_buf(ctx, ctx->p2_src2, (size_t)m * 4));
       HCI_TRY(ensure_buf(ctx, ctx->p2_d, (size_t)m * 8));
       src = bp<int32_t>(ctx->p2_src);
@@ -830,8 +844,11 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
     HCI_CUDA(ctx, cudaFuncSetAttribute(k_pt2_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HCI_LAUNCH(k_pt2_terms, grid_for(m, 256), 256, sm, st)(bp<ulonglong2>(ctx->s_cand), bp<double>(ctx->p2_vals), m,
                                                           A.keys, nV, n, ref, A.ref_a, A.ref_b, e0, contrib, ext,
-                                                          dpair);
+                                                          dpair, c, src);
+    if (grad_c)
+      HCI_LAUNCH(k_pt2_grad, grid_for(m, 256), 256, 0, st)(src, bp<double>(ctx->p2_vals), dpair, m, grad_c);
     if (want_rdm) HCI_TRY(pt2_rdm_pairs(ctx, A.keys, c, bp<ulonglong2>(ctx->s_cand), src, dpair, m));
+    HCI_CUDA(ctx, cudaGetLastError());
     HCI_LAUNCH(k_sum_slices_d, PT2_SUM_BLOCKS, 256, 0, st)(contrib, m, part);
     HCI_LAUNCH(k_sum_parts_d, 1, 32, 0, st)(part, PT2_SUM_BLOCKS, dsum);
     int64_t* cnt_dev = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);

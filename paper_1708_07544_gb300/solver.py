@@ -56,6 +56,13 @@ class HCISolver:
         also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
         return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs, self.norb if rdms else None)
 
+    def zvector(self, keys, c, e0, rhs, tol=1e-10, maxit=500):
+        return _abi.hci_zvector(self.ctx, keys, c, e0, rhs, tol, maxit)
+
+    def relaxed_rdm12(self, keys, c, e0, eps2, max_pairs=0, zv_tol=1e-10, zv_maxit=500):
+        """(E2, rdm1, rdm2): the density of E_var + E2 (Sec. III.A, Eq. lambda)."""
+        return _abi.hci_relaxed_rdm12(self.ctx, keys, c, e0, eps2, self.norb, max_pairs, zv_tol, zv_maxit)
+
     def solve(self, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24):
         keys, c, e, it = _abi.hci_solve(self.ctx, eps1, max_iter, dav_tol, dav_maxit, cap)
         return {"keys": keys, "c": c, "E": e, "iters": it}
