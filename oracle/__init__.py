@@ -15,7 +15,8 @@ What each function follows:
                      on a fixed V (a library eigensolver stands in for
                      Davidson: the result is the same lowest eigenpair).
 * ``hci``         -- the variational stage V^{mu+1} = V^mu + C^mu(eps1)
-                     (Sec. II.A, Fig. 1) iterated until C^mu is empty.
+                     (Sec. II.A, Fig. 1) iterated until C^mu is empty;
+                     ``hci_roots`` the same for several lowest states.
 * ``rdm12``       -- the variational RDMs by their definition (Sec. IV).
 * ``pt2``         -- the screened Epstein-Nesbet correction E2(eps2),
                      Eq. (pt_hci) of Sec. II.B, by enumerating every single
@@ -261,6 +262,41 @@ def ground_state(inst, keys, v0=None, H=None):
             e, c = float(w[0]), v[:, 0]
     c = c / np.linalg.norm(c)
     return e, fix_phase(c)
+
+
+def lowest_states(inst, keys, nroots):
+    """The nroots lowest eigenpairs of H restricted to V (ascending; each
+    vector with the phase of fix_phase)."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    H = hamiltonian(inst, keys)
+    if len(keys) <= 2500:
+        w, v = np.linalg.eigh(H.toarray())
+    else:
+        w, v = spla.eigsh(H, k=nroots, which="SA", tol=0, ncv=min(len(keys), max(40, 4 * nroots)))
+        order = np.argsort(w)
+        w, v = w[order], v[:, order]
+    return w[:nroots].astype(float), np.stack([fix_phase(v[:, r] / np.linalg.norm(v[:, r])) for r in range(nroots)])
+
+
+def hci_roots(inst, eps1, nroots, max_iter=30):
+    """Variational HCI for the nroots lowest states: a determinant enters when
+    max_r |H_ai c_i^(r)| > eps1 for some D_i, i.e. the selection of the
+    single-state loop with c_i replaced by max_r |c_i^(r)|; V^0 = {aufbau}
+    (one state) and from the first selection on, all nroots states."""
+    P = Problem.of(inst)
+    keys = aufbau(P.nalpha, P.nbeta)
+    ceff = np.array([1.0])
+    es, cs = None, None
+    for mu in range(max_iter):
+        new, _, _ = select(P, keys, ceff, eps1)
+        if len(new) == 0:
+            break
+        keys, _ = merge(keys, np.zeros(len(keys)), new)
+        if len(keys) < nroots:
+            raise ValueError("space smaller than the number of roots")
+        es, cs = lowest_states(P, keys, nroots)
+        ceff = np.abs(cs).max(axis=0)
+    return {"keys": keys, "c": cs, "E": es}
 
 
 def merge(keys, c, new_keys):

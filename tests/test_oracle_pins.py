@@ -223,3 +223,19 @@ def test_golden_polyene8():
     assert len(res["keys"]) == int(vals["nV_eps1e-4"])
     assert abs(res["E"] - vals["E_eps1e-4"]) < 1e-9
     assert abs(oracle.hci(inst, 0.0)["E"] - vals["E_fci"]) < 1e-9
+
+
+def test_hci_roots_at_eps_zero_is_fci_spectrum():
+    """Several roots: HCI(eps1 = 0) reaches the whole sector and its lowest
+    states are the lowest Jordan-Wigner FCI eigenvalues."""
+    inst = hi.random_tiny(5, 2, 2, 81)
+    keys_j, Hj = fci_jw.sector_matrix(inst.h, inst.eri, inst.e_core, 2, 2)
+    w = np.linalg.eigvalsh(Hj)
+    res = oracle.hci_roots(inst, 0.0, 3)
+    assert len(res["keys"]) == len(keys_j)
+    assert np.abs(res["E"] - w[:3]).max() < 1e-10
+    # the states are orthonormal eigenvectors on the final space
+    H = oracle.hamiltonian(inst, res["keys"]).toarray()
+    C = res["c"]
+    assert np.abs(C @ C.T - np.eye(3)).max() < 1e-10
+    assert np.abs(C @ H @ C.T - np.diag(res["E"])).max() < 1e-10
