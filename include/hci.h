@@ -171,6 +171,27 @@ hci_status hci_relaxed_rdm12(hci_ctx* ctx, double eps2, const uint64_t* keys, co
                              int64_t max_pairs, double zv_tol, int zv_maxit, double* e2, double* rdm1,
                              double* rdm2);
 
+/* The nroots lowest eigenpairs on V (ascending), one after the other by
+ * Davidson deflated against the converged lower ones (each start vector and
+ * correction kept orthogonal to them).  c_inout: device [nroots][nV], start
+ * vectors on entry (zero => unit vector at the lowest diagonal element, made
+ * orthogonal), the normalised eigenvectors on exit (phase as hci_davidson).
+ * energies: host [nroots].  iters: host out, total iterations (may be NULL).
+ * 1 <= nroots <= min(nV, 32).  Synchronises. */
+hci_status hci_davidson_roots(hci_ctx* ctx, const uint64_t* keys, int64_t nV, int nroots, double* c_inout,
+                              double* energies, double tol, int maxit, int* iters);
+
+/* Variational HCI for the nroots lowest states (Sec. II.A): D_a enters when
+ * max_r |H_ai c_i^(r)| > eps1, i.e. the selection with c_i replaced by
+ * max_r |c_i^(r)|; V^0 = {aufbau}, then select, merge (every state padded
+ * with zeros) and hci_davidson_roots until the selection is empty.
+ * keys_out: device [cap][2]; c_out: device [nroots][nV] (NULL allowed);
+ * nV_out, energies [nroots], iters: host out.  HCI_ERR_CAPACITY when nV >
+ * cap (nV_out holds the size). */
+hci_status hci_solve_roots(hci_ctx* ctx, int nroots, double eps1, int max_iter, double dav_tol, int dav_maxit,
+                           uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out, double* energies,
+                           int* iters);
+
 /* Spin-summed variational RDMs (Sec. IV, Gamma^{c,c}; accumulated over the
  * connections of V):
  *   rdm1[p*n+q]            = sum_s <a+_ps a_qs>

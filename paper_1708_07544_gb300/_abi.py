@@ -11,6 +11,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -27,7 +29,8 @@ _NAMES = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "CUDA", 5
 EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hci_select", "hci_merge",
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
-           "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12"]
+           "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12", "hci_davidson_roots",
+           "hci_solve_roots"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -69,6 +72,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
     L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V, V]
     L.hci_zvector.argtypes = [V, V, I64, V, D, V, V, D, I, P(I)]
+    L.hci_davidson_roots.argtypes = [V, V, I64, I, V, V, D, I, P(I)]
+    L.hci_solve_roots.argtypes = [V, I, D, I, D, I, V, V, I64, P(I64), V, P(I)]
     L.hci_relaxed_rdm12.argtypes = [V, D, V, V, I64, D, I64, D, I, P(D), V, V]
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
@@ -204,6 +209,34 @@ def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None, grad=False):
     if grad:
         out = out + (g,)
     return out
+
+
+def hci_davidson_roots(ctx, keys, nroots, c0=None, tol=1e-10, maxit=400):
+    """(energies [nroots], c [nroots, nV], total iterations)."""
+    L = load()
+    nV = keys.shape[0]
+    c = torch.zeros((nroots, nV), dtype=torch.float64, device=keys.device) if c0 is None else c0.clone().contiguous()
+    e = (ctypes.c_double * nroots)()
+    it = ctypes.c_int(0)
+    _check(L.hci_davidson_roots(ctx, _ptr(keys), nV, int(nroots), _ptr(c), e, float(tol), int(maxit),
+                                ctypes.byref(it)), ctx)
+    return np.array(e[:]), c, it.value
+
+
+def hci_solve_roots(ctx, nroots, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 22, device=None):
+    """Multi-state variational HCI: (keys [nV, 2] int64, c [nroots, nV], energies, selections)."""
+    L = load()
+    dev = device if device is not None else torch.device("cuda")
+    keys = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+    c = torch.empty((nroots, cap), dtype=torch.float64, device=dev)
+    nv = ctypes.c_int64(0)
+    e = (ctypes.c_double * nroots)()
+    it = ctypes.c_int(0)
+    _check(L.hci_solve_roots(ctx, int(nroots), float(eps1), int(max_iter), float(dav_tol), int(dav_maxit),
+                             _ptr(keys), _ptr(c), cap, ctypes.byref(nv), e, ctypes.byref(it)), ctx)
+    n = nv.value
+    cflat = c.reshape(-1)[: nroots * n].reshape(nroots, n).clone()
+    return keys[:n].clone(), cflat, np.array(e[:]), it.value
 
 
 def hci_zvector(ctx, keys, c, e0, rhs, tol=1e-10, maxit=500):

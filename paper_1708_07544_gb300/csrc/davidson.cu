@@ -277,6 +277,19 @@ __global__ void __launch_bounds__(DBLOCK) k_olsen(const DavDev* __restrict__ d, 
   }
 }
 
+// v[i] += a * (a hash of i mapped to [-1, 1)): a start component in every
+// symmetry sector (deflated roots need not share the lowest diagonal
+// determinant's symmetry)
+__global__ void k_add_hash(double* __restrict__ v, int64_t n, double a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t x = (uint64_t)i + 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    v[i] += a * ((double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
 // t -= sum_j dots_j V_j
 __global__ void k_orth(const double* __restrict__ V, int64_t ld, int k, const DavDev* __restrict__ d,
                        double* __restrict__ t, int64_t n) {
@@ -384,11 +397,13 @@ struct Dav {
 
 }  // namespace
 
-extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout, double* energy,
-                                   double tol, int maxit, int* iters) {
-  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_davidson: null context");
-  if (nV <= 0 || !keys || !c_inout || !energy)
-    return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson: empty space or null pointer");
+// The Davidson loop; with m > 0 locked vectors L (orthonormal, internal
+// order, leading dimension (nV + 31) & ~31) the start vector and every
+// correction are kept orthogonal to them, so the iteration converges to the
+// lowest eigenpair of H in their complement (the next root when L holds the
+// lower ones).
+static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout, double* energy,
+                                double tol, int maxit, int* iters, const double* L, int m) {
   if (iters) *iters = 0;
   HCI_TRY(graph_ensure(ctx, keys, nV));
   prof_tic(ctx, HCI_PH_DAVIDSON);
@@ -422,7 +437,27 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
   if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) {
     HCI_CUDA(ctx, cudaMemsetAsync(D.V, 0, (size_t)nV * 8, st));
     HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(D.V, diag, nV);
+    if (m > 0) HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(D.V, nV, 1e-2 / std::sqrt((double)nV));
   } else {
+    HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.V, nV, 1.0 / std::sqrt(nrm2));
+  }
+  if (m > 0) {
+    // start orthogonal to the locked vectors (else the unit vector at the
+    // lowest diagonal element, made orthogonal)
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      for (int pass = 0; pass < 2; ++pass) {
+        HCI_TRY(D.dots(L, m, D.V, D.d->dots));
+        HCI_LAUNCH(k_orth, D.nblk, DBLOCK, 0, st)(L, D.ld, m, D.d, D.V, nV);
+      }
+      HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
+      HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+      HCI_CUDA(ctx, cudaStreamSynchronize(st));
+      if (nrm2 > 1e-20) break;
+      if (attempt == 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson_roots: no start vector outside the roots");
+      HCI_CUDA(ctx, cudaMemsetAsync(D.V, 0, (size_t)nV * 8, st));
+      HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(D.V, diag, nV);
+      HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(D.V, nV, 1e-2 / std::sqrt((double)nV));
+    }
     HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.V, nV, 1.0 / std::sqrt(nrm2));
   }
   HCI_TRY(D.sigma(0));
@@ -464,6 +499,10 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
     for (int pass = 0; pass < 2; ++pass) {
       HCI_TRY(D.dots(D.V, k, D.t, D.d->dots));
       HCI_LAUNCH(k_orth, D.nblk, DBLOCK, 0, st)(D.V, D.ld, k, D.d, D.t, nV);
+      if (m > 0) {
+        HCI_TRY(D.dots(L, m, D.t, D.d->dots));
+        HCI_LAUNCH(k_orth, D.nblk, DBLOCK, 0, st)(L, D.ld, m, D.d, D.t, nV);
+      }
     }
     HCI_TRY(D.dots(D.t, 1, D.t, &D.d->nrm2));
     HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
@@ -496,5 +535,38 @@ extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t n
   if (!converged && rn > tol)
     return hci_fail(ctx, HCI_ERR_NOT_CONVERGED, "hci_davidson: residual %.3e > tol %.3e after %d iterations", rn, tol,
                     it);
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout, double* energy,
+                                   double tol, int maxit, int* iters) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_davidson: null context");
+  if (nV <= 0 || !keys || !c_inout || !energy)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson: empty space or null pointer");
+  return davidson_core(ctx, keys, nV, c_inout, energy, tol, maxit, iters, nullptr, 0);
+}
+
+extern "C" hci_status hci_davidson_roots(hci_ctx* ctx, const uint64_t* keys, int64_t nV, int nroots, double* c_inout,
+                                         double* energies, double tol, int maxit, int* iters) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_davidson_roots: null context");
+  if (nV <= 0 || !keys || !c_inout || !energies)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson_roots: empty space or null pointer");
+  if (nroots < 1 || nroots > nV || nroots > LDG)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson_roots: nroots must lie in [1, min(nV, %d)]", LDG);
+  if (iters) *iters = 0;
+  HCI_TRY(graph_ensure(ctx, keys, nV));
+  const int64_t ld = (nV + 31) & ~(int64_t)31;
+  HCI_TRY(ensure_buf(ctx, ctx->d_lock, (size_t)ld * nroots * 8));
+  double* L = bp<double>(ctx->d_lock);
+  int total = 0;
+  for (int r = 0; r < nroots; ++r) {
+    int it = 0;
+    hci_status s = davidson_core(ctx, keys, nV, c_inout + (int64_t)r * nV, &energies[r], tol, maxit, &it, L, r);
+    total += it;
+    if (iters) *iters = total;
+    if (s != HCI_OK) return s;
+    HCI_TRY(to_internal(ctx, c_inout + (int64_t)r * nV, L + (int64_t)r * ld, 1));
+  }
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
   return HCI_OK;
 }

@@ -89,7 +89,7 @@ struct hci_ctx {
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
   IncScratch inc;
   bool incremental = true;
-  DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel;
+  DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
   int64_t last_candidates = 0;
   int64_t st_counts[HCI_ST_COUNT] = {};
   Prof prof;

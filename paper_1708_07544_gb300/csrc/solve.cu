@@ -13,6 +13,16 @@
 #include "hci_internal.cuh"
 
 namespace {
+// c_eff[i] = max_r |c_r[i]|: the multi-state criterion max_r |H_ai c_i^(r)|
+// is the single-state one with c_i replaced by c_eff[i]
+__global__ void k_ceff(const double* __restrict__ c, int nroots, int64_t nV, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nV; i += (int64_t)gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int r = 0; r < nroots; ++r) m = fmax(m, fabs(c[(int64_t)r * nV + i]));
+    out[i] = m;
+  }
+}
+
 __global__ void k_aufbau(int na, int nb, ulonglong2* keys, double* c) {
   uint64_t a = na == 64 ? ~0ull : ((1ull << na) - 1ull);
   uint64_t b = nb == 64 ? ~0ull : ((1ull << nb) - 1ull);
@@ -106,6 +116,81 @@ extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double 
   free_buf(st, kr);
   free_buf(st, cr);
   if (ce != cudaSuccess) return hci_fail(ctx, HCI_ERR_CUDA, "hci_solve: %s", cudaGetErrorString(ce));
+  return HCI_OK;
+}
+
+// Variational HCI for the nroots lowest states (Sec. II.A with the
+// selection over all states): V^0 = {aufbau}, first selection from c = [1],
+// then select with c_eff = max_r |c_r|, merge (every state padded with
+// zeros), and the nroots lowest eigenpairs by deflated Davidson.
+extern "C" hci_status hci_solve_roots(hci_ctx* ctx, int nroots, double eps1, int max_iter, double dav_tol,
+                                      int dav_maxit, uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out,
+                                      double* energies, int* iters) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_solve_roots: null context");
+  if (!nV_out || !energies || nroots < 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: bad arguments");
+  if (max_iter < 1 || dav_maxit < 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: bad iteration limits");
+  *nV_out = 0;
+  if (iters) *iters = 0;
+  cudaStream_t st = ctx->st;
+  HCI_TRY(hci_build_lists(ctx));
+  DevBuf kb[2], cb[2], nk, ce;
+  auto cleanup = [&]() {
+    for (int i = 0; i < 2; ++i) { free_buf(st, kb[i]); free_buf(st, cb[i]); }
+    free_buf(st, nk);
+    free_buf(st, ce);
+  };
+  hci_status s;
+  if ((s = ensure_buf(ctx, kb[0], 16)) != HCI_OK || (s = ensure_buf(ctx, ce, 8)) != HCI_OK) { cleanup(); return s; }
+  HCI_LAUNCH(k_aufbau, 1, 1, 0, st)(ctx->na, ctx->nb, bp<ulonglong2>(kb[0]), bp<double>(ce));
+  int cur = 0;
+  int64_t nV = 1;
+  int mu = 0;
+  for (; mu < max_iter; ++mu) {
+    if (mu > 0)
+      HCI_LAUNCH(k_ceff, grid_for(nV, 256), 256, 0, st)(bp<double>(cb[cur]), nroots, nV, bp<double>(ce));
+    int64_t ncap = nk.bytes / 16, nn = 0;
+    s = hci_select(ctx, eps1, bp<uint64_t>(kb[cur]), bp<double>(ce), nV, bp<uint64_t>(nk), ncap, &nn);
+    if (s == HCI_ERR_CAPACITY) {
+      if ((s = ensure_buf(ctx, nk, (size_t)(nn + 1024) * 16)) != HCI_OK) { cleanup(); return s; }
+      s = hci_select(ctx, eps1, bp<uint64_t>(kb[cur]), bp<double>(ce), nV, bp<uint64_t>(nk), nk.bytes / 16, &nn);
+    }
+    if (s != HCI_OK) { cleanup(); return s; }
+    if (nn == 0) break;
+    const int nxt = cur ^ 1;
+    const int64_t nV2 = nV + nn;
+    if ((s = ensure_buf(ctx, kb[nxt], (size_t)nV2 * 16)) != HCI_OK ||
+        (s = ensure_buf(ctx, cb[nxt], (size_t)nV2 * nroots * 8)) != HCI_OK ||
+        (s = ensure_buf(ctx, ce, (size_t)nV2 * 8)) != HCI_OK) {
+      cleanup();
+      return s;
+    }
+    for (int r = 0; r < nroots; ++r) {
+      const double* cr = mu > 0 ? bp<double>(cb[cur]) + (int64_t)r * nV : nullptr;
+      s = hci_merge(ctx, bp<uint64_t>(kb[cur]), cr, nV, bp<uint64_t>(nk), nn, bp<uint64_t>(kb[nxt]),
+                    bp<double>(cb[nxt]) + (int64_t)r * nV2);
+      if (s != HCI_OK) { cleanup(); return s; }
+    }
+    cur = nxt;
+    nV = nV2;
+    if (nV < nroots) { cleanup(); return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: space smaller than nroots"); }
+    s = hci_davidson_roots(ctx, bp<uint64_t>(kb[cur]), nV, nroots, bp<double>(cb[cur]), energies, dav_tol, dav_maxit,
+                           nullptr);
+    if (s != HCI_OK) { cleanup(); return s; }
+  }
+  if (iters) *iters = mu;
+  *nV_out = nV;
+  if (mu == 0) { cleanup(); return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: the first selection is empty"); }
+  if (nV > cap) {
+    cleanup();
+    return hci_fail(ctx, HCI_ERR_CAPACITY, "hci_solve_roots: %lld determinants exceed cap %lld", (long long)nV,
+                    (long long)cap);
+  }
+  cudaError_t e = cudaSuccess;
+  if (keys_out) e = cudaMemcpyAsync(keys_out, kb[cur].p, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && c_out) e = cudaMemcpyAsync(c_out, cb[cur].p, (size_t)nV * nroots * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return hci_fail(ctx, HCI_ERR_CUDA, "hci_solve_roots: %s", cudaGetErrorString(e));
   return HCI_OK;
 }
 

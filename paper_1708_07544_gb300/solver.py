@@ -56,6 +56,13 @@ class HCISolver:
         also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
         return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs, self.norb if rdms else None)
 
+    def davidson_roots(self, keys, nroots, c0=None, tol=1e-10, maxit=400):
+        return _abi.hci_davidson_roots(self.ctx, keys, nroots, c0, tol, maxit)
+
+    def solve_roots(self, nroots, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 22):
+        keys, c, e, it = _abi.hci_solve_roots(self.ctx, nroots, eps1, max_iter, dav_tol, dav_maxit, cap)
+        return {"keys": keys, "c": c, "E": e, "iters": it}
+
     def zvector(self, keys, c, e0, rhs, tol=1e-10, maxit=500):
         return _abi.hci_zvector(self.ctx, keys, c, e0, rhs, tol, maxit)
 

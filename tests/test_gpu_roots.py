@@ -1,0 +1,78 @@
+"""Several lowest states: deflated Davidson against the oracle's
+eigensolver (energies within 1e-9, orthonormal eigenvectors with
+residuals below the tolerance), and the multi-state HCI loop (selection
+with max_r |H_ai c_i^(r)|) against the oracle's: the same determinant set
+and energies within 1e-9, and the full space at eps1 = 0.
+"""
+import numpy as np
+import pytest
+
+import hci_inputs as hi
+import oracle
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1708_07544_gb300 import build
+
+    build.build()
+    import paper_1708_07544_gb300 as p
+
+    return p
+
+
+def dev_keys(keys):
+    k = np.ascontiguousarray(np.asarray(keys, np.uint64).reshape(-1, 2))
+    return torch.from_numpy(k.view(np.int64)).cuda()
+
+
+def host_keys(t):
+    return t.cpu().numpy().view(np.uint64).reshape(-1, 2)
+
+
+def solver(pkg, inst):
+    return pkg.HCISolver(inst.norb, inst.nalpha, inst.nbeta, torch.tensor(inst.h).cuda(),
+                         torch.tensor(inst.eri).cuda(), inst.e_core)
+
+
+@pytest.mark.parametrize("name,make,nv,nroots", [
+    ("tiny6", lambda: hi.random_tiny(6, 3, 3, 91), 300, 4),
+    ("df12", lambda: hi.df_12o(), 2500, 3),
+    ("polyene8_open", lambda: hi.Instance("p8o", 8, 5, 3, hi.ppp_polyene(8).h, hi.ppp_polyene(8).eri, 0.3), 600, 3),
+])
+def test_davidson_roots_match_oracle(pkg, name, make, nv, nroots):
+    inst = make()
+    keys = hi.random_det_keys(inst.norb, inst.nalpha, inst.nbeta, nv, seed=nv + 91)
+    w, _ = oracle.lowest_states(inst, keys, nroots)
+    H = oracle.hamiltonian(inst, keys)
+    with solver(pkg, inst) as s:
+        e, c, it = s.davidson_roots(dev_keys(keys), nroots, tol=1e-10)
+    C = c.cpu().numpy()
+    assert np.abs(e - w).max() < 1e-9
+    assert np.abs(C @ C.T - np.eye(nroots)).max() < 1e-9
+    for r in range(nroots):
+        assert np.linalg.norm(H @ C[r] - e[r] * C[r]) < 1e-9
+
+
+def test_solve_roots_matches_oracle(pkg):
+    inst = hi.ppp_polyene(8)
+    ref = oracle.hci_roots(inst, 1e-3, 3)
+    with solver(pkg, inst) as s:
+        out = s.solve_roots(3, 1e-3, dav_tol=1e-10)
+    got = {tuple(x) for x in host_keys(out["keys"]).tolist()}
+    want = {tuple(x) for x in np.asarray(ref["keys"]).tolist()}
+    assert got == want
+    assert np.abs(out["E"] - ref["E"]).max() < 1e-9
+
+
+def test_solve_roots_eps_zero_is_full_space(pkg):
+    inst = hi.random_tiny(6, 3, 2, 93)
+    w = np.linalg.eigvalsh(oracle.hamiltonian(inst, oracle.hci(inst, 0.0)["keys"]).toarray())
+    with solver(pkg, inst) as s:
+        out = s.solve_roots(3, 0.0, dav_tol=1e-10)
+    assert out["keys"].shape[0] == 20 * 15
+    assert np.abs(out["E"] - w[:3]).max() < 1e-9
