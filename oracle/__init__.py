@@ -24,6 +24,13 @@ What each function follows:
                      kept; pinned against numerators taken from the
                      Jordan-Wigner FCI matrix); ``pt2_rdm`` its density
                      matrices Gamma^dd and Gamma^dc by their definition.
+* ``pt2_semistochastic`` -- Eq. (semistoc): E2^D(eps2_det) plus the mean
+                     over samples of E2^S(eps2) - E2^S(eps2_det), each
+                     sample the unbiased multinomial estimator of the cited
+                     semistochastic HCI work (``pt2_sampled``; pinned by its
+                     exact expectation over every draw sequence), the draws
+                     made by ``philox4x64`` (pinned against numpy's Philox)
+                     and an exact integer inverse CDF (``sample_draws``).
 * ``rotate`` / ``gradient`` -- vHCISCF gradient Eq. (vdedk2): the
                      derivative of the rotated integrals contracted with
                      the RDMs, chained through U = exp(kappa) (Sec. III.B).
@@ -72,6 +79,7 @@ def _lib():
         L.orc_rdm12.argtypes = [ctypes.c_int, P, i64, P, P, P]
         L.orc_pt2.argtypes = [ctypes.c_int, P, P, d, P, P, i64, d, d, P, P]
         L.orc_pt2_rdm.argtypes = [ctypes.c_int, P, P, d, P, P, i64, d, d, P, P, P, P]
+        L.orc_pt2_sampled.argtypes = [ctypes.c_int, P, P, d, P, i64, P, P, P, i64, i64, d, d, d, P]
         L.orc_num_threads.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -176,6 +184,107 @@ def pt2_rdm(inst, keys, c, eps2, e0):
     _lib().orc_pt2_rdm(n, _p(P.h), _p(P.eri), P.e_core, _p(keys), _p(c), len(keys), float(eps2), float(e0),
                        *[_p(x) for x in out])
     return tuple(out)
+
+
+# ----------------------------------------------------------------------------
+# semistochastic second-order correction (Sec. II.B, Eq. semistoc)
+# ----------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+
+
+def philox4x64(ctr, key, rounds=10):
+    """Philox4x64-R counter-based generator (Salmon, Moraes, Dror, Shaw,
+    SC'11), from its published definition: each round multiplies words 0
+    and 2 by two fixed odd constants into 128-bit products and mixes the
+    halves with words 1 and 3 and the key; the key is bumped by two Weyl
+    constants between rounds.  ctr: 4 words, key: 2 words (ints < 2^64)."""
+    c0, c1, c2, c3 = (int(x) & _M64 for x in ctr)
+    k0, k1 = (int(x) & _M64 for x in key)
+    for r in range(rounds):
+        if r:
+            k0 = (k0 + 0x9E3779B97F4A7C15) & _M64
+            k1 = (k1 + 0xBB67AE8584CAA73B) & _M64
+        p0 = 0xD2E7470EE14C6C93 * c0
+        p1 = 0xCA5A826395121157 * c2
+        c0, c1, c2, c3 = ((p1 >> 64) ^ c1 ^ k0, p1 & _M64, (p0 >> 64) ^ c3 ^ k1, p0 & _M64)
+    return c0, c1, c2, c3
+
+
+def sample_weights(c):
+    """Integer sampling weights W_i proportional to |c_i| (reading: p_i =
+    |c_i| / sum_j |c_j| to 2^-40 relative): W_i = ceil(|c_i| 2^(40 - E))
+    with 2^(E-1) <= max|c| < 2^E, so every non-zero c_i has W_i >= 1 and
+    the weights and their prefix sums are exact integers in any order.
+    Returns (W as Python ints, total)."""
+    a = np.abs(np.asarray(c, np.float64))
+    if a.size == 0 or a.max() == 0.0:
+        return [0] * a.size, 0
+    e = np.frexp(a.max())[1]
+    W = [int(np.ceil(np.ldexp(x, 40 - int(e)))) for x in a]
+    return W, sum(W)
+
+
+def sample_draws(c, n_draws, n_samples, seed):
+    """Draw k of sample s: r = first word of philox4x64((k, s, 0, 0),
+    (seed, 0)), u = floor(r * total / 2^64) in [0, total), and the drawn
+    index is the first i whose inclusive prefix sum of W exceeds u, so D_i
+    is drawn with probability W_i / total.  Returns an int64 array
+    (n_samples, n_draws)."""
+    W, total = sample_weights(c)
+    cum = np.cumsum(np.array(W, dtype=object))
+    out = np.zeros((n_samples, n_draws), np.int64)
+    for s in range(n_samples):
+        for k in range(n_draws):
+            r = philox4x64((k, s, 0, 0), (int(seed), 0))[0]
+            u = (r * total) >> 64
+            lo, hi = 0, len(W)
+            while lo < hi:
+                mid = (lo + hi) // 2
+                if cum[mid] > u:
+                    hi = mid
+                else:
+                    lo = mid + 1
+            out[s, k] = lo
+    return out
+
+
+def pt2_sampled(inst, keys, c, idx, counts, p, n_draws, eps2, eps2_det, e0):
+    """One sample of the stochastic correction: the distinct drawn
+    determinants idx (into V), drawn counts[j] times out of n_draws with
+    probability p[idx[j]].  Returns (E2^S(eps2), E2^S(eps2_det)), the
+    unbiased estimates of E2 with each screen (orc_pt2_sampled)."""
+    P = Problem.of(inst)
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    idx = _c(idx, np.int64)
+    f = _c(np.asarray(counts, np.float64) / np.asarray(p, np.float64)[idx], np.float64)
+    sk = _c(keys[idx], np.uint64)
+    sc = _c(c[idx], np.float64)
+    out = np.zeros(2)
+    _lib().orc_pt2_sampled(P.norb, _p(P.h), _p(P.eri), P.e_core, _p(keys), len(keys), _p(sk), _p(sc), _p(f),
+                           len(idx), int(n_draws), float(eps2), float(eps2_det), float(e0), _p(out))
+    return float(out[0]), float(out[1])
+
+
+def pt2_semistochastic(inst, keys, c, e0, eps2, eps2_det, n_draws, n_samples, seed):
+    """Eq. (semistoc): E2 ~ E2^D(eps2_det) + mean_s [E2^S_s(eps2) -
+    E2^S_s(eps2_det)], both stochastic terms of a sample from the same
+    draws; the error is the standard error of that mean.  Returns a dict
+    with estimate, error, e2_det, samples (n_samples x 2) and draws."""
+    keys = _c(keys, np.uint64).reshape(-1, 2)
+    c = _c(c, np.float64)
+    e2d, _ = pt2(inst, keys, c, eps2_det, e0)
+    W, total = sample_weights(c)
+    p = np.array([w / total for w in W]) if total else np.zeros(len(W))
+    draws = sample_draws(c, n_draws, n_samples, seed)
+    samples = np.zeros((n_samples, 2))
+    for s in range(n_samples):
+        idx, cnt = np.unique(draws[s], return_counts=True)
+        samples[s] = pt2_sampled(inst, keys, c, idx, cnt, p, n_draws, eps2, eps2_det, e0)
+    diff = samples[:, 0] - samples[:, 1]
+    err = float(np.std(diff, ddof=1) / np.sqrt(n_samples)) if n_samples > 1 else 0.0
+    return {"estimate": e2d + float(diff.mean()), "error": err, "e2_det": e2d, "samples": samples,
+            "draws": draws}
 
 
 def select(inst, keys, c, eps1, band=1e-12, sources=None):

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <unordered_map>
 #include <vector>
 #ifdef _OPENMP
@@ -372,6 +373,55 @@ void orc_pt2(int n, const double* h, const double* eri, double ecore, const uint
   for (auto& kv : all) sum += kv.second;
   *e2 = sum;
   *n_ext = (int64_t)all.size();
+}
+
+// One sample of the stochastic second-order correction (Sec. II.B, the
+// unbiased multinomial estimator of the cited semistochastic HCI work,
+// Eq. semistoc).  The sample is n_draws determinants drawn from V with
+// replacement, D_j with probability p_j; the distinct ones are given with
+// f_j = w_j / p_j (w_j = times drawn).  For every target D_a outside V, over
+// the sampled pairs kept by a screen (|H_aj c_j| > eps), with x_j = H_aj c_j:
+//   S = sum_j f_j x_j,  T = sum_j (f_j x_j)^2,  U = sum_j f_j x_j^2,
+//   e_a = (S^2 - T + (N_d - 1) U) / (N_d (N_d - 1) (e0 - H_aa)),
+// which is the estimator's [(sum_j w_j x_j / p_j)^2 + sum_j (w_j (N_d - 1) /
+// p_j - w_j^2 / p_j^2) x_j^2] / (N_d (N_d - 1) (e0 - H_aa)) with its terms
+// grouped so that a target reached from one sampled determinant has
+// S^2 - T = 0 exactly.  Its expectation over the draws is E2 with the same
+// screen.  out[0] uses eps2, out[1] eps2_det (>= eps2).  Targets are summed
+// in ascending key order.
+void orc_pt2_sampled(int n, const double* h, const double* eri, double ecore, const uint64_t* keys, int64_t nV,
+                     const uint64_t* src_keys, const double* src_c, const double* src_f, int64_t nsrc,
+                     int64_t n_draws, double eps2, double eps2_det, double e0, double* out) {
+  Ham H{n, h, eri, ecore};
+  Index idx(keys, nV);
+  struct Acc { double s[2], t[2], u[2]; };
+  std::map<Key, Acc> acc;
+  for (int64_t j = 0; j < nsrc; ++j) {
+    const double cj = src_c[j], fj = src_f[j];
+    for_each_excitation(H, src_keys[2 * j], src_keys[2 * j + 1], [&](uint64_t a, uint64_t b, double v) {
+      const double x = v * cj;
+      if (!(std::fabs(x) > eps2)) return;
+      if (idx.find(a, b) >= 0) return;
+      Acc& r = acc.try_emplace(Key{a, b}, Acc{{0, 0}, {0, 0}, {0, 0}}).first->second;
+      for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !(std::fabs(x) > eps2_det)) break;
+        r.s[k] += fj * x;
+        r.t[k] += (fj * x) * (fj * x);
+        r.u[k] += fj * x * x;
+      }
+    });
+  }
+  const double nd = (double)n_draws;
+  double e[2] = {0.0, 0.0};
+  for (auto& kv : acc) {
+    const double den = nd * (nd - 1.0) * (e0 - diag_element(H, kv.first.a, kv.first.b));
+    for (int k = 0; k < 2; ++k) {
+      const Acc& r = kv.second;
+      e[k] += (r.s[k] * r.s[k] - r.t[k] + (nd - 1.0) * r.u[k]) / den;
+    }
+  }
+  out[0] = e[0];
+  out[1] = e[1];
 }
 
 // Density matrices of the perturbative correction (Sec. V, Computational
