@@ -146,6 +146,32 @@ hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double
                    int64_t max_pairs, double* e2, int64_t* n_ext, double* rdm1_dd, double* rdm2_dd,
                    double* rdm1_dc, double* rdm2_dc, double* grad_c);
 
+/* Semistochastic second-order correction (Sec. II.B, Eq. semistoc):
+ *   E2(eps2) ~ E2^D(eps2_det) + mean_s [E2^S_s(eps2) - E2^S_s(eps2_det)],
+ * E2^D the deterministic hci_pt2 value, and both stochastic terms of a
+ * sample s evaluated on the same draws: n_draws determinants of V drawn
+ * with replacement, D_i with probability p_i = W_i / sum W, W_i =
+ * ceil(|c_i| 2^(40 - E)) with 2^(E-1) <= max|c| < 2^E (p_i proportional to
+ * |c_i| to 2^-40).  Draw k of sample s takes the first word r of
+ * Philox4x64-10 (Salmon et al., SC'11) at counter (k, s, 0, 0) and key
+ * (seed, 0), u = floor(r sum W / 2^64), and the index i with
+ * W_0 + .. + W_{i-1} <= u < W_0 + .. + W_i.  Each sample's estimate is the
+ * unbiased multinomial estimator of the cited semistochastic HCI work: over
+ * the targets D_a outside V of the drawn determinants' pairs kept by the
+ * screen (|H_aj c_j| > eps), with x_j = H_aj c_j, f_j = w_j / p_j (w_j =
+ * times drawn), S = sum f_j x_j, T = sum (f_j x_j)^2, U = sum f_j x_j^2:
+ *   E2^S = sum_a (S^2 - T + (N_d - 1) U) / (N_d (N_d - 1) (e0 - H_aa)).
+ * keys, c, e0, max_pairs: as hci_pt2 (keys strictly ascending, nV <= 2^22).
+ * eps2 <= eps2_det.  n_draws >= 2, n_samples >= 1, n_draws * n_samples <
+ * 2^31.  result: host [3] = {estimate, its standard error over the samples
+ * (0 for one sample), E2^D(eps2_det)}.  sample_e2: host [n_samples][2] =
+ * {E2^S(eps2), E2^S(eps2_det)} per sample, or NULL.  draws: device int32
+ * [n_samples][n_draws], the drawn indices into V, or NULL.  nV = 0 or
+ * c = 0 give zeros.  Synchronises.  Builds the heat-bath lists if needed. */
+hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, const double* c, int64_t nV, double e0,
+                              double eps2, double eps2_det, int64_t n_draws, int n_samples, uint64_t seed,
+                              int64_t max_pairs, double* result, double* sample_e2, int32_t* draws);
+
 /* The z-vector equation of the HCISCF gradient (Sec. III.A, Eq. lagc): z
  * with (H - e0) z = P rhs on V and z orthogonal to c (P = 1 - c c^T), by
  * preconditioned conjugate gradients in the complement of c (H - e0 is

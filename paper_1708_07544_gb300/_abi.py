@@ -30,7 +30,7 @@ EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hc
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
            "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12", "hci_davidson_roots",
-           "hci_solve_roots"]
+           "hci_solve_roots", "hci_pt2_stochastic"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -71,6 +71,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_davidson.argtypes = [V, V, I64, V, P(D), D, I, P(I)]
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
     L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V, V]
+    L.hci_pt2_stochastic.argtypes = [V, V, V, I64, D, D, D, I64, I, ctypes.c_uint64, I64, V, V, V]
     L.hci_zvector.argtypes = [V, V, I64, V, D, V, V, D, I, P(I)]
     L.hci_davidson_roots.argtypes = [V, V, I64, I, V, V, D, I, P(I)]
     L.hci_solve_roots.argtypes = [V, I, D, I, D, I, V, V, I64, P(I64), V, P(I)]
@@ -209,6 +210,20 @@ def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None, grad=False):
     if grad:
         out = out + (g,)
     return out
+
+
+def hci_pt2_stochastic(ctx, keys, c, e0, eps2, eps2_det, n_draws, n_samples, seed=0, max_pairs=0):
+    """Semistochastic E2 (Eq. semistoc): dict with estimate, error, e2_det,
+    samples [n_samples, 2] (E2^S(eps2), E2^S(eps2_det)) and draws
+    [n_samples, n_draws] (device int32 indices into V)."""
+    L = load()
+    res = (ctypes.c_double * 3)()
+    smp = np.zeros((int(n_samples), 2))
+    draws = torch.empty((int(n_samples), int(n_draws)), dtype=torch.int32, device=keys.device)
+    _check(L.hci_pt2_stochastic(ctx, _ptr(keys), _ptr(c), keys.shape[0], float(e0), float(eps2), float(eps2_det),
+                                int(n_draws), int(n_samples), int(seed), int(max_pairs), res,
+                                smp.ctypes.data_as(ctypes.c_void_p), _ptr(draws)), ctx)
+    return {"estimate": res[0], "error": res[1], "e2_det": res[2], "samples": smp, "draws": draws}
 
 
 def hci_davidson_roots(ctx, keys, nroots, c0=None, tol=1e-10, maxit=400):

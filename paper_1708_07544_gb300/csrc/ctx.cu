@@ -290,7 +290,8 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->inc.roff, &ctx->inc.ctl, &ctx->inc.left, &ctx->inc.samp,
                     &ctx->p2_vals, &ctx->p2_vals2, &ctx->p2_ref,
                     &ctx->p2_src, &ctx->p2_src2, &ctx->p2_d, &ctx->p2_dd,
-                    &ctx->d_zv, &ctx->d_rel, &ctx->d_lock};
+                    &ctx->d_zv, &ctx->d_rel, &ctx->d_lock, &ctx->ss_w, &ctx->ss_draw,
+                    &ctx->ss_draw2, &ctx->ss_run, &ctx->ss_src};
   for (DevBuf* b : bufs) free_buf(st, *b);
   prof_release(ctx);
   cudaStreamSynchronize(st);

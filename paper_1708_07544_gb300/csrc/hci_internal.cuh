@@ -85,6 +85,7 @@ struct hci_ctx {
   // scratch
   DevBuf s_cand, s_cand2, s_flags, s_scan, s_misc, s_counter, s_hist, s_walkstat, s_items, s_rdmw, s_rdmh;
   DevBuf p2_vals, p2_vals2, p2_ref, p2_src, p2_src2, p2_d, p2_dd;   // perturbative correction
+  DevBuf ss_w, ss_draw, ss_draw2, ss_run, ss_src;                 // sampled perturbative correction
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
   IncScratch inc;

@@ -3,6 +3,8 @@
 // behind an upper-bound screen, sort-based deduplication against V, and the
 // sorted merge V^{mu+1} = V^mu + C^mu.
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "hci_internal.cuh"
 
@@ -739,6 +741,34 @@ __global__ void k_sum_parts_d(const double* __restrict__ part, int np, double* _
 
 }  // namespace
 
+// Walk arguments of the perturbative modes: sources keys/c (nV of them),
+// terms kept when |H_ai c_i| > eps (every single and double when eps < 0).
+static hci_status pt_walk_args(hci_ctx* ctx, WalkArgs& A, const uint64_t* keys, const double* c, int64_t nV,
+                               double eps) {
+  Lists& L = ctx->lists;
+  A = WalkArgs{};
+  A.n = ctx->n; A.na = ctx->na; A.nb = ctx->nb;
+  A.keys = reinterpret_cast<const ulonglong2*>(keys);
+  A.c = c; A.nV = nV; A.eps1 = eps; A.accept_all = eps <= 0.0 ? 1 : 0;
+  A.opp_mag = bp<double>(L.opp_mag); A.opp_tgt = bp<uint16_t>(L.opp_tgt); A.Lo = L.len_opp;
+  A.same_mag = bp<double>(L.same_mag); A.same_tgt = bp<uint16_t>(L.same_tgt); A.Ls = L.len_same;
+  A.max_dbl = L.max_opp > L.max_same ? L.max_opp : L.max_same;
+  A.h = bp<double>(ctx->h); A.jk_same = bp<double>(ctx->jk_same); A.j_opp = bp<double>(ctx->j_opp);
+  A.single_bound = bp<double>(L.single_bound); A.max_single = L.max_single;
+  A.list_max = bp<double>(L.list_max);
+  A.f_ref = bp<double>(L.f_ref);
+  A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
+  A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
+  A.eri = bp<double>(ctx->eri);
+  A.srcs = nullptr;
+  A.vals = nullptr;
+  A.npart = 1;
+  A.part = 0;
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  A.counter = bp<unsigned long long>(ctx->s_counter);
+  return HCI_OK;
+}
+
 extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double* c, int64_t nV,
                               double e0, int64_t max_pairs, double* e2, int64_t* n_ext, double* rdm1_dd,
                               double* rdm2_dd, double* rdm1_dc, double* rdm2_dc, double* grad_c) {
@@ -768,28 +798,12 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
   if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2: keys are not strictly ascending");
   cudaStream_t st = ctx->st;
   const int n = ctx->n;
-  Lists& L = ctx->lists;
   WalkArgs A;
-  A.n = n; A.na = ctx->na; A.nb = ctx->nb;
-  A.keys = reinterpret_cast<const ulonglong2*>(keys);
-  A.c = c; A.nV = nV; A.eps1 = eps2; A.accept_all = eps2 <= 0.0 ? 1 : 0;
-  A.opp_mag = bp<double>(L.opp_mag); A.opp_tgt = bp<uint16_t>(L.opp_tgt); A.Lo = L.len_opp;
-  A.same_mag = bp<double>(L.same_mag); A.same_tgt = bp<uint16_t>(L.same_tgt); A.Ls = L.len_same;
-  A.max_dbl = L.max_opp > L.max_same ? L.max_opp : L.max_same;
-  A.h = bp<double>(ctx->h); A.jk_same = bp<double>(ctx->jk_same); A.j_opp = bp<double>(ctx->j_opp);
-  A.single_bound = bp<double>(L.single_bound); A.max_single = L.max_single;
-  A.list_max = bp<double>(L.list_max);
-  A.f_ref = bp<double>(L.f_ref);
-  A.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
-  A.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
-  A.eri = bp<double>(ctx->eri);
-  A.srcs = nullptr;
-  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
-  A.counter = bp<unsigned long long>(ctx->s_counter);
+  HCI_TRY(pt_walk_args(ctx, A, keys, c, nV, eps2));
   if (want_rdm) HCI_TRY(pt2_rdm_begin(ctx));
   // aufbau reference of the diagonal elements
   const size_t nref = 1 + 2 * (size_t)n + 4 * (size_t)n * n;
-  HCI_TRY(ensure_buf(ctx, ctx->p2_ref, nref * 8 + (PT2_SUM_BLOCKS + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, ctx->p2_ref, nref * 8 + (PT2_SUM_BLOCKS + 2) * 8));
   double* ref = bp<double>(ctx->p2_ref);
   double* part = ref + nref;
   double* dsum = part + PT2_SUM_BLOCKS;
@@ -887,5 +901,359 @@ extern "C" hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, c
   }
   *e2 = acc;
   if (n_ext) *n_ext = next_total;
+  return HCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Semistochastic second-order correction (Sec. II.B, Eq. semistoc):
+// E2 ~ E2^D(eps2_det) + mean over samples of [E2^S(eps2) - E2^S(eps2_det)],
+// both stochastic terms of a sample taken from the same draws.  A sample is
+// n_draws determinants of V drawn with replacement, D_i with probability
+// p_i = W_i / sum W (integer weights W_i proportional to |c_i|); the drawn
+// determinants are walked like V in the deterministic correction, and every
+// target outside V contributes the unbiased multinomial estimate of the
+// cited semistochastic HCI work, grouped as
+//   (S^2 - T + (N_d - 1) U) / (N_d (N_d - 1) (E0 - H_aa)),
+// S = sum_j f_j x_j, T = sum_j (f_j x_j)^2, U = sum_j f_j x_j^2,
+// x_j = H_aj c_j, f_j = w_j / p_j (w_j = times D_j was drawn).
+// Draw k of sample s uses the first word r of Philox4x64-10 at counter
+// (k, s, 0, 0) and key (seed, 0): u = floor(r sum W / 2^64), and the drawn
+// index is the i with prefix_{i-1} <= u < prefix_i of the inclusive prefix
+// sums of W.  Weights, prefix sums and the draw are exact integer
+// arithmetic, so the draws do not depend on the summation order.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 64x64->128 multiplications by fixed odd constants, the halves mixed with
+// the other two words and the key; the key is bumped by two Weyl
+// constants between rounds.
+__device__ __forceinline__ uint64_t philox4x64_first(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                     uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B97F4A7C15ull;
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+    const uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+    const uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return c0;
+}
+
+// largest |c_i| (bit pattern of a non-negative double orders like the value)
+__global__ void k_abs_max(const double* __restrict__ c, int64_t n, unsigned long long* __restrict__ mx) {
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(c[i]));
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+// W_i = ceil(|c_i| 2^(40 - E)), 2^(E-1) <= max|c| < 2^E: W_i >= 1 iff c_i != 0, sum W < 2^63 for n < 2^22
+__global__ void k_ss_weights(const double* __restrict__ c, int64_t n, const unsigned long long* __restrict__ mx,
+                             int64_t* __restrict__ W) {
+  int e = 0;
+  frexp(__longlong_as_double((long long)*mx), &e);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    W[i] = (int64_t)ceil(ldexp(fabs(c[i]), 40 - e));
+}
+
+// draws: key (x = sample, y = drawn index) for the sort, and the index alone
+__global__ void k_ss_draw(const int64_t* __restrict__ excl, int64_t nV,
+                          const int64_t* __restrict__ total, uint64_t seed, int64_t nd, int64_t m,
+                          ulonglong2* __restrict__ out, int32_t* __restrict__ draws) {
+  const uint64_t tot = (uint64_t)*total;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / nd, k = t - s * nd;
+    const uint64_t r = philox4x64_first((uint64_t)k, (uint64_t)s, 0ull, 0ull, seed, 0ull);
+    const uint64_t u = __umul64hi(r, tot);
+    // the i with excl[i] <= u < excl[i] + W[i] is the last i with
+    // excl[i] <= u (a zero weight shares its start with the next entry, and
+    // the last entry ends at the total > u, so that i has W[i] > 0)
+    int64_t lo = 0, hi = nV;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((uint64_t)excl[mid] <= u) lo = mid + 1;
+      else hi = mid;
+    }
+    const int64_t i = lo - 1;
+    out[t] = make_ulonglong2((unsigned long long)s, (unsigned long long)i);
+    if (draws) draws[t] = (int32_t)i;
+  }
+}
+
+__global__ void k_run_first(const ulonglong2* __restrict__ k, int64_t m, int64_t* __restrict__ flag) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+    flag[t] = (t == 0 || !key_eq(k[t], k[t - 1])) ? 1 : 0;
+}
+
+// distinct (sample, index) runs of the sorted draws: index, sample, first position
+__global__ void k_ss_compact(const ulonglong2* __restrict__ k, int64_t m, const int64_t* __restrict__ flag,
+                             const int64_t* __restrict__ pos, int32_t* __restrict__ d_idx, int32_t* __restrict__ d_s,
+                             int64_t* __restrict__ d_start) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+    if (flag[t]) {
+      const int64_t j = pos[t];
+      d_idx[j] = (int32_t)k[t].y;
+      d_s[j] = (int32_t)k[t].x;
+      d_start[j] = t;
+    }
+}
+
+// seg[s] = first distinct run of sample s (s = 0..ns)
+__global__ void k_ss_seg(const int32_t* __restrict__ d_s, int64_t nd, int ns, int64_t* __restrict__ seg) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= ns; s += gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = nd;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (d_s[mid] < s) lo = mid + 1;
+      else hi = mid;
+    }
+    seg[s] = lo;
+  }
+}
+
+// the sources of one sample: key, c, f = w / p with p = W_i / sum W
+__global__ void k_ss_gather(int64_t j0, int64_t j1, int64_t ndist, int64_t m, const int32_t* __restrict__ d_idx,
+                            const int64_t* __restrict__ d_start, const ulonglong2* __restrict__ keys,
+                            const double* __restrict__ c, const int64_t* __restrict__ W,
+                            const int64_t* __restrict__ total, ulonglong2* __restrict__ sk, double* __restrict__ sc,
+                            double* __restrict__ sf) {
+  const double tot = (double)*total;
+  for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < j1;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = (j + 1 < ndist ? d_start[j + 1] : m) - d_start[j];
+    const int32_t i = d_idx[j];
+    const double p = (double)W[i] / tot;
+    sk[j - j0] = keys[i];
+    sc[j - j0] = c[i];
+    sf[j - j0] = (double)w / p;
+  }
+}
+
+// On the first pair of every run of equal targets (sorted; element H_aj and
+// source j on each pair): targets in V give 0, the others their estimate
+// with the eps2 screen (every emitted pair) and with eps2_det.
+__global__ void k_ss_terms(const ulonglong2* __restrict__ t, const double* __restrict__ v,
+                           const int32_t* __restrict__ src, int64_t m, const ulonglong2* __restrict__ V, int64_t nV,
+                           const double* __restrict__ sc, const double* __restrict__ sf, double eps2_det,
+                           double nd, int n, const double* __restrict__ ref, uint64_t ra, uint64_t rb, double e0,
+                           double* __restrict__ out_t, double* __restrict__ out_d) {
+  extern __shared__ double s_ref[];
+  const int nref = 1 + 2 * n + 4 * n * n;
+  for (int u = threadIdx.x; u < nref; u += blockDim.x) s_ref[u] = ref[u];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double et = 0.0, ed = 0.0;
+    const ulonglong2 key = t[i];
+    if (i == 0 || !key_eq(key, t[i - 1])) {
+      const int64_t pos = lower_bound(V, nV, key);
+      if (!(pos < nV && key_eq(V[pos], key))) {
+        double S[2] = {0.0, 0.0}, T[2] = {0.0, 0.0}, U[2] = {0.0, 0.0};
+        for (int64_t e = i; e < m && key_eq(t[e], key); ++e) {
+          const int32_t j = src[e];
+          const double x = v[e] * sc[j], f = sf[j];
+          for (int k = 0; k < 2; ++k) {
+            if (k == 1 && !(fabs(x) > eps2_det)) break;
+            S[k] += f * x;
+            T[k] += (f * x) * (f * x);
+            U[k] += f * x * x;
+          }
+        }
+        const double den = nd * (nd - 1.0) * (e0 - pt2_diag(s_ref, n, key, ra, rb));
+        et = (S[0] * S[0] - T[0] + (nd - 1.0) * U[0]) / den;
+        ed = (S[1] * S[1] - T[1] + (nd - 1.0) * U[1]) / den;
+      }
+    }
+    out_t[i] = et;
+    out_d[i] = ed;
+  }
+}
+
+}  // namespace
+
+extern "C" hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, const double* c, int64_t nV, double e0,
+                                         double eps2, double eps2_det, int64_t n_draws, int n_samples,
+                                         uint64_t seed, int64_t max_pairs, double* result, double* sample_e2,
+                                         int32_t* draws) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_pt2_stochastic: null context");
+  if (!result) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: result is NULL");
+  result[0] = result[1] = result[2] = 0.0;
+  if (nV < 0 || max_pairs < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: negative size");
+  if (n_draws < 2 || n_samples < 1)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: need n_draws >= 2 and n_samples >= 1");
+  if (n_draws * (int64_t)n_samples > INT32_MAX)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: n_draws * n_samples exceeds 2^31 - 1");
+  if (!(eps2 <= eps2_det)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: eps2 must not exceed eps2_det");
+  if (nV > ((int64_t)1 << 22))
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: more than 2^22 determinants");
+  if (sample_e2)
+    for (int s = 0; s < 2 * n_samples; ++s) sample_e2[s] = 0.0;
+  if (nV == 0) return HCI_OK;
+  if (!keys || !c) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: null keys or c");
+  // deterministic part (also checks the keys and builds the lists)
+  double e2d = 0.0;
+  HCI_TRY(hci_pt2(ctx, eps2_det, keys, c, nV, e0, max_pairs, &e2d, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr));
+  cudaStream_t st = ctx->st;
+  const int n = ctx->n;
+  const int64_t nd = n_draws, m = nd * n_samples;
+  // weights, their exclusive prefix sums and total
+  HCI_TRY(ensure_buf(ctx, ctx->ss_w, (size_t)(2 * nV + 2) * 8));
+  int64_t* W = bp<int64_t>(ctx->ss_w);
+  int64_t* excl = W + nV;
+  int64_t* total = excl + nV;
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(total + 1);
+  HCI_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
+  HCI_LAUNCH(k_abs_max, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx);
+  HCI_LAUNCH(k_ss_weights, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx, W);
+  HCI_TRY(scan_i64(ctx, W, excl, nV, total));
+  int64_t tot_h = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&tot_h, total, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  if (tot_h == 0) {   // c = 0: every estimate is 0
+    result[2] = e2d;
+    result[0] = e2d;
+    if (draws) HCI_CUDA(ctx, cudaMemsetAsync(draws, 0, (size_t)m * 4, st));
+    return HCI_OK;
+  }
+  // draws, sorted by (sample, index), and their distinct runs
+  HCI_TRY(ensure_buf(ctx, ctx->ss_draw, (size_t)m * 16));
+  HCI_TRY(ensure_buf(ctx, ctx->ss_draw2, (size_t)m * 16));
+  ulonglong2* dk = bp<ulonglong2>(ctx->ss_draw);
+  HCI_LAUNCH(k_ss_draw, grid_for(m, 256, 152 * 8), 256, 0, st)(excl, nV, total, seed, nd, m, dk, draws);
+  int sbits = 1, ibits = 1;
+  while (sbits < 32 && ((int64_t)1 << sbits) < n_samples) ++sbits;
+  while (ibits < 32 && ((int64_t)1 << ibits) < nV) ++ibits;
+  HCI_TRY(sort_keys(ctx, bp<uint64_t>(ctx->ss_draw), bp<uint64_t>(ctx->ss_draw2), m, sbits, ibits));
+  HCI_TRY(ensure_buf(ctx, ctx->ss_run, (size_t)m * (8 + 8 + 8 + 4 + 4) + (size_t)(n_samples + 1) * 8));
+  int64_t* flag = bp<int64_t>(ctx->ss_run);
+  int64_t* pos = flag + m;
+  int64_t* d_start = pos + m;
+  int32_t* d_idx = reinterpret_cast<int32_t*>(d_start + m);
+  int32_t* d_s = d_idx + m;
+  int64_t* seg = reinterpret_cast<int64_t*>(d_s + m);
+  int64_t* ndist_dev = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 48);
+  HCI_LAUNCH(k_run_first, grid_for(m, 256, 152 * 8), 256, 0, st)(dk, m, flag);
+  HCI_TRY(scan_i64(ctx, flag, pos, m, ndist_dev));
+  HCI_LAUNCH(k_ss_compact, grid_for(m, 256, 152 * 8), 256, 0, st)(dk, m, flag, pos, d_idx, d_s, d_start);
+  int64_t ndist = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&ndist, ndist_dev, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  HCI_LAUNCH(k_ss_seg, 1, 256, 0, st)(d_s, ndist, n_samples, seg);
+  std::vector<int64_t> seg_h((size_t)n_samples + 1);
+  HCI_CUDA(ctx, cudaMemcpyAsync(seg_h.data(), seg, (size_t)(n_samples + 1) * 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  int64_t maxsrc = 0;
+  for (int s = 0; s < n_samples; ++s) maxsrc = std::max(maxsrc, seg_h[s + 1] - seg_h[s]);
+  HCI_TRY(ensure_buf(ctx, ctx->ss_src, (size_t)maxsrc * 32));
+  ulonglong2* sk = bp<ulonglong2>(ctx->ss_src);
+  double* sc = reinterpret_cast<double*>(sk + maxsrc);
+  double* sf = sc + maxsrc;
+  // the reference of the diagonal elements (written by hci_pt2 above)
+  WalkArgs A;
+  HCI_TRY(pt_walk_args(ctx, A, reinterpret_cast<const uint64_t*>(sk), sc, 0, eps2));
+  const size_t nref = 1 + 2 * (size_t)n + 4 * (size_t)n * n;
+  double* ref = bp<double>(ctx->p2_ref);
+  double* part = ref + nref;
+  double* dsum = part + PT2_SUM_BLOCKS;
+  const int64_t per = max_pairs > 0 ? max_pairs : ((int64_t)1 << 28);
+  const ulonglong2* Vk = reinterpret_cast<const ulonglong2*>(keys);
+  const size_t smref = nref * 8;
+  HCI_CUDA(ctx, cudaFuncSetAttribute(k_ss_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smref));
+  HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)4096 * 16));
+  HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)4096 * 8));
+  std::vector<double> est((size_t)n_samples * 2, 0.0);
+  // one hash class of one sample's targets: walk (again with a larger
+  // buffer if it was too small), sort, estimate, sum
+  auto run_class = [&](int s, int npart, int pc, int64_t* m_out) -> hci_status {
+    A.npart = npart;
+    A.part = pc;
+    int64_t mp = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      A.out = bp<ulonglong2>(ctx->s_cand);
+      A.vals = bp<double>(ctx->p2_vals);
+      A.cap = (int64_t)std::min(ctx->s_cand.bytes / 16, ctx->p2_vals.bytes / 8);
+      HCI_TRY(ensure_buf(ctx, ctx->p2_src, (size_t)A.cap * 4));
+      A.srcs = bp<int32_t>(ctx->p2_src);
+      HCI_TRY(run_walk(ctx, A, &mp));
+      if (mp <= A.cap || (npart == 1 && mp > per)) break;
+      HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)(mp + mp / 8 + 4096) * 16));
+      HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)(mp + mp / 8 + 4096) * 8));
+    }
+    *m_out = mp;
+    if (npart == 1 && mp > per) return HCI_OK;
+    if (mp > A.cap) return hci_fail(ctx, HCI_ERR_CUDA, "hci_pt2_stochastic: pair count changed between walks");
+    if (mp == 0) return HCI_OK;
+    HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)mp * 16));
+    HCI_TRY(ensure_buf(ctx, ctx->p2_vals2, (size_t)mp * 8));
+    HCI_TRY(ensure_buf(ctx, ctx->p2_src2, (size_t)mp * 4));
+    HCI_TRY(ensure_buf(ctx, ctx->p2_d, (size_t)mp * 8));
+    HCI_TRY(sort_pairs(ctx, bp<uint64_t>(ctx->s_cand), bp<uint64_t>(ctx->s_cand2), bp<double>(ctx->p2_vals),
+                       bp<double>(ctx->p2_vals2), bp<int32_t>(ctx->p2_src), bp<int32_t>(ctx->p2_src2), mp, n, n));
+    double* ct = bp<double>(ctx->p2_vals2);
+    double* cd = bp<double>(ctx->p2_d);
+    HCI_LAUNCH(k_ss_terms, grid_for(mp, 256), 256, smref, st)(bp<ulonglong2>(ctx->s_cand), bp<double>(ctx->p2_vals),
+                                                              bp<int32_t>(ctx->p2_src), mp, Vk, nV, sc, sf, eps2_det,
+                                                              (double)nd, n, ref, A.ref_a, A.ref_b, e0, ct, cd);
+    HCI_LAUNCH(k_sum_slices_d, PT2_SUM_BLOCKS, 256, 0, st)(ct, mp, part);
+    HCI_LAUNCH(k_sum_parts_d, 1, 32, 0, st)(part, PT2_SUM_BLOCKS, dsum);
+    HCI_LAUNCH(k_sum_slices_d, PT2_SUM_BLOCKS, 256, 0, st)(cd, mp, part);
+    HCI_LAUNCH(k_sum_parts_d, 1, 32, 0, st)(part, PT2_SUM_BLOCKS, dsum + 1);
+    HCI_CUDA(ctx, cudaGetLastError());
+    double hs[2] = {0.0, 0.0};
+    HCI_CUDA(ctx, cudaMemcpyAsync(hs, dsum, 16, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    est[2 * (size_t)s] += hs[0];
+    est[2 * (size_t)s + 1] += hs[1];
+    return HCI_OK;
+  };
+  for (int s = 0; s < n_samples; ++s) {
+    const int64_t j0 = seg_h[s], j1 = seg_h[s + 1];
+    if (j1 <= j0) continue;
+    HCI_LAUNCH(k_ss_gather, grid_for(j1 - j0, 256), 256, 0, st)(j0, j1, ndist, m, d_idx, d_start, Vk, c, W, total,
+                                                                sk, sc, sf);
+    A.nV = j1 - j0;
+    int64_t tot_pairs = 0;
+    HCI_TRY(run_class(s, 1, 0, &tot_pairs));
+    if (tot_pairs > per) {
+      const int64_t np64 = (tot_pairs + per - 1) / per;
+      if (np64 > (1 << 20))
+        return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: max_pairs too small for %lld pairs",
+                        (long long)tot_pairs);
+      const int npart = (int)np64;
+      const int64_t cap = tot_pairs / npart + tot_pairs / (8 * (int64_t)npart) + 4096;
+      HCI_TRY(ensure_buf(ctx, ctx->s_cand, (size_t)cap * 16));
+      HCI_TRY(ensure_buf(ctx, ctx->p2_vals, (size_t)cap * 8));
+      for (int pc = 0; pc < npart; ++pc) {
+        int64_t mp = 0;
+        HCI_TRY(run_class(s, npart, pc, &mp));
+      }
+    }
+  }
+  // Eq. (semistoc): E2^D plus the mean difference, and its standard error
+  double mean = 0.0;
+  for (int s = 0; s < n_samples; ++s) mean += est[2 * (size_t)s] - est[2 * (size_t)s + 1];
+  mean /= n_samples;
+  double var = 0.0;
+  for (int s = 0; s < n_samples; ++s) {
+    const double d = est[2 * (size_t)s] - est[2 * (size_t)s + 1] - mean;
+    var += d * d;
+  }
+  result[0] = e2d + mean;
+  result[1] = n_samples > 1 ? std::sqrt(var / (n_samples - 1) / n_samples) : 0.0;
+  result[2] = e2d;
+  if (sample_e2)
+    for (size_t u = 0; u < est.size(); ++u) sample_e2[u] = est[u];
   return HCI_OK;
 }

@@ -56,6 +56,11 @@ class HCISolver:
         also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
         return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs, self.norb if rdms else None)
 
+    def pt2_semistochastic(self, keys, c, e0, eps2, eps2_det, n_draws, n_samples, seed=0, max_pairs=0):
+        """E2(eps2) ~ E2^D(eps2_det) + mean of E2^S(eps2) - E2^S(eps2_det)
+        over n_samples samples of n_draws determinants (Eq. semistoc)."""
+        return _abi.hci_pt2_stochastic(self.ctx, keys, c, e0, eps2, eps2_det, n_draws, n_samples, seed, max_pairs)
+
     def davidson_roots(self, keys, nroots, c0=None, tol=1e-10, maxit=400):
         return _abi.hci_davidson_roots(self.ctx, keys, nroots, c0, tol, maxit)
 
