@@ -219,8 +219,8 @@ def sample_weights(c):
     a = np.abs(np.asarray(c, np.float64))
     if a.size == 0 or a.max() == 0.0:
         return [0] * a.size, 0
-    e = np.frexp(a.max())[1]
-    W = [int(np.ceil(np.ldexp(x, 40 - int(e)))) for x in a]
+    e = int(np.frexp(a.max())[1])
+    W = [int(x) for x in np.ceil(np.ldexp(a, 40 - e))]
     return W, sum(W)
 
 
@@ -231,20 +231,13 @@ def sample_draws(c, n_draws, n_samples, seed):
     is drawn with probability W_i / total.  Returns an int64 array
     (n_samples, n_draws)."""
     W, total = sample_weights(c)
-    cum = np.cumsum(np.array(W, dtype=object))
+    cum = np.cumsum(np.array(W, dtype=np.int64))      # exact: total < 2^63
     out = np.zeros((n_samples, n_draws), np.int64)
     for s in range(n_samples):
         for k in range(n_draws):
             r = philox4x64((k, s, 0, 0), (int(seed), 0))[0]
             u = (r * total) >> 64
-            lo, hi = 0, len(W)
-            while lo < hi:
-                mid = (lo + hi) // 2
-                if cum[mid] > u:
-                    hi = mid
-                else:
-                    lo = mid + 1
-            out[s, k] = lo
+            out[s, k] = int(np.searchsorted(cum, np.int64(u), side="right"))
     return out
 
 

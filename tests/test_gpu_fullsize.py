@@ -119,6 +119,22 @@ def test_df44_bench_configuration(pkg):
         assert np.trace(r1dd) > 0.0 and abs(np.trace(r1dc)) < 1e-10
         assert abs(np.einsum("pprr->", r2dd) - (N - 1) * np.trace(r1dd)) < 1e-8 * N * N * np.trace(r1dd)
         assert np.abs(r1dd - r1dd.T).max() < 1e-12
+        # semistochastic E2(1e-5) from E2^D(3e-5) (Eq. semistoc): within five
+        # standard errors of the deterministic value; one sample of 200
+        # draws against the oracle on the same draws
+        keys_h = out["keys"].cpu().numpy().view(np.uint64).reshape(-1, 2)
+        c_h = out["c"].cpu().numpy()
+        r = s.pt2_semistochastic(out["keys"], out["c"], out["E"], 1e-5, 3e-5, 1000, 12, seed=11)
+        assert abs(r["e2_det"] - e2l) <= 1e-12 * abs(e2l)
+        assert r["error"] > 0.0 and abs(r["estimate"] - e2) < 5 * r["error"]
+        one = s.pt2_semistochastic(out["keys"], out["c"], out["E"], 1e-5, 3e-5, 200, 1, seed=12)
+        d = oracle.sample_draws(c_h, 200, 1, 12)
+        assert np.array_equal(one["draws"].cpu().numpy(), d)
+        W, tot = oracle.sample_weights(c_h)
+        p = np.array(W, np.float64) / float(tot)
+        idx, cnt = np.unique(d[0], return_counts=True)
+        want = oracle.pt2_sampled(R, keys_h, c_h, idx, cnt, p, 200, 1e-5, 3e-5, out["E"])
+        assert np.abs(one["samples"][0] - want).max() <= 1e-10 * abs(want[0])
     finally:
         s.close()
     # backward through the rotation against the oracle's chain rule on the same RDMs
