@@ -321,9 +321,11 @@ def gpu_arm(args):
         # semistochastic E2 at a tighter eps2 (Eq. semistoc): E2^D at the
         # paper's eps2 plus the sampled difference down to PT2_SS_EPS2
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("pt2_ss")
         t0 = time.perf_counter()
         ss = s.pt2_semistochastic(keys, c, last["E"], PT2_SS_EPS2, PT2_EPS2, PT2_SS_DRAWS, PT2_SS_SAMPLES, seed=1708)
         t_ss = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
         pt2 = {"eps2": PT2_EPS2, "E2": e2v, "E_var_plus_E2": last["E"] + e2v, "targets": n_ext,
                "seconds": round(statistics.median(ts), 4), "seconds_with_rdms": round(t_rdm, 4),
                "relaxed_rdm_seconds": round(t_rel, 4), "reps": args.pt2_reps,
