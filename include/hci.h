@@ -200,8 +200,11 @@ hci_status hci_relaxed_rdm12(hci_ctx* ctx, double eps2, const uint64_t* keys, co
 /* The nroots lowest eigenpairs on V (ascending), one after the other by
  * Davidson deflated against the converged lower ones (each start vector and
  * correction kept orthogonal to them).  c_inout: device [nroots][nV], start
- * vectors on entry (zero => unit vector at the lowest diagonal element, made
- * orthogonal), the normalised eigenvectors on exit (phase as hci_davidson).
+ * vectors on entry (zero => unit vector at the lowest diagonal element, for
+ * roots above the first plus 1e-2/sqrt(nV) times a fixed hash of each index
+ * mapped to [-1, 1), so that no symmetry sector is missing from the start;
+ * then made orthogonal), the normalised eigenvectors on exit (phase as
+ * hci_davidson).
  * energies: host [nroots].  iters: host out, total iterations (may be NULL).
  * 1 <= nroots <= min(nV, 32).  Synchronises. */
 hci_status hci_davidson_roots(hci_ctx* ctx, const uint64_t* keys, int64_t nV, int nroots, double* c_inout,
@@ -211,7 +214,8 @@ hci_status hci_davidson_roots(hci_ctx* ctx, const uint64_t* keys, int64_t nV, in
  * max_r |H_ai c_i^(r)| > eps1, i.e. the selection with c_i replaced by
  * max_r |c_i^(r)|; V^0 = {aufbau}, then select, merge (every state padded
  * with zeros) and hci_davidson_roots until the selection is empty.
- * keys_out: device [cap][2]; c_out: device [nroots][nV] (NULL allowed);
+ * keys_out: device [cap][2]; c_out: device with room for nroots * cap
+ * doubles, written densely as [nroots][nV] (NULL allowed);
  * nV_out, energies [nroots], iters: host out.  HCI_ERR_CAPACITY when nV >
  * cap (nV_out holds the size). */
 hci_status hci_solve_roots(hci_ctx* ctx, int nroots, double eps1, int max_iter, double dav_tol, int dav_maxit,
