@@ -30,11 +30,13 @@ EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hc
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
            "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12", "hci_davidson_roots",
-           "hci_solve_roots", "hci_pt2_stochastic"]
+           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
-         "select_sources", "candidates", "graph_builds", "walk_entries", "singles_exact", "rows_refilled"]
+         "select_sources", "candidates", "graph_builds", "walk_entries", "singles_exact", "rows_refilled",
+         "sigma_direct"]
+SIGMA_AUTO, SIGMA_STORED, SIGMA_DIRECT = 0, 1, 2
 
 
 class HCIError(RuntimeError):
@@ -71,6 +73,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_davidson.argtypes = [V, V, I64, V, P(D), D, I, P(I)]
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
     L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V, V]
+    L.hci_set_sigma_mode.argtypes = [V, I, I64]
     L.hci_pt2_stochastic.argtypes = [V, V, V, I64, D, D, D, I64, I, ctypes.c_uint64, I64, V, V, V]
     L.hci_zvector.argtypes = [V, V, I64, V, D, V, V, D, I, P(I)]
     L.hci_davidson_roots.argtypes = [V, V, I64, I, V, V, D, I, P(I)]
@@ -210,6 +213,12 @@ def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None, grad=False):
     if grad:
         out = out + (g,)
     return out
+
+
+def hci_set_sigma_mode(ctx, mode, graph_budget=0):
+    """Stored connections (SIGMA_STORED), searched again per traversal
+    (SIGMA_DIRECT), or stored while they fit graph_budget bytes (SIGMA_AUTO)."""
+    _check(load().hci_set_sigma_mode(ctx, int(mode), int(graph_budget)), ctx)
 
 
 def hci_pt2_stochastic(ctx, keys, c, e0, eps2, eps2_det, n_draws, n_samples, seed=0, max_pairs=0):

@@ -357,6 +357,18 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
   return HCI_OK;
 }
 
+extern "C" hci_status hci_set_sigma_mode(hci_ctx* ctx, int mode, int64_t graph_budget) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_set_sigma_mode: null context");
+  if (mode != HCI_SIGMA_AUTO && mode != HCI_SIGMA_STORED && mode != HCI_SIGMA_DIRECT)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_set_sigma_mode: unknown mode %d", mode);
+  if (graph_budget < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_set_sigma_mode: negative budget");
+  ctx->sigma_mode = mode;
+  ctx->graph_budget = graph_budget;
+  ctx->direct_fallback = false;
+  ctx->graph.valid = false;
+  return HCI_OK;
+}
+
 extern "C" hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout) {
   if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_stats: null context");
   if (nout < 0 || (nout > 0 && !out)) return HCI_ERR_INVALID;
@@ -364,6 +376,7 @@ extern "C" hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout) {
   for (int k = 0; k < HCI_ST_COUNT; ++k) v[k] = ctx->st_counts[k];
   v[HCI_ST_GRAPH_NNZ] = ctx->graph.valid ? ctx->graph.nnz : 0;
   v[HCI_ST_LAST_CANDIDATES] = ctx->last_candidates;
+  v[HCI_ST_SIGMA_DIRECT] = ctx->graph.valid && ctx->graph.direct ? 1 : 0;
   for (int k = 0; k < nout && k < HCI_ST_COUNT; ++k) out[k] = v[k];
   for (int k = HCI_ST_COUNT; k < nout; ++k) out[k] = 0;
   return HCI_OK;

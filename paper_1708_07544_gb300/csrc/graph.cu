@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "hci_internal.cuh"
+#include "rdm_acc.cuh"
 
 namespace {
 
@@ -245,6 +246,12 @@ struct GraphArgs {
   const int32_t* s2i;      // sorted position -> internal id (columns are stored as internal ids)
   unsigned long long* queue;
   HamView H;
+  // direct traversals (no stored rows), vectors by sorted position
+  const double* dc;             // input vector
+  double* dsig;                 // sigma: output
+  const double* ddiag;          // sigma: diagonal elements
+  unsigned long long* dnnz;     // sigma: connections visited (may be null)
+  RdmAcc R;                     // RDMs: accumulators
 };
 
 // A group of size m is scanned when that is cheaper than L binary searches.
@@ -255,16 +262,31 @@ __device__ __forceinline__ bool use_lookup(int64_t m, int L) {
 
 // Row search modes: count only, fill at a known offset, or staged fill
 // (into the warp's scratch, capped at scr_cap entries, still counting past it).
-constexpr int ROWS_COUNT = 0, ROWS_FILL = 1, ROWS_STAGED = 2;
+// Direct traversals evaluate each connection as it is found: ROWS_SIGMA adds
+// H_ij c_j into the row's sum, ROWS_RDM accumulates <D_i| op |D_j> c_i c_j
+// for j > i (the other orientation is added as the transpose).
+constexpr int ROWS_COUNT = 0, ROWS_FILL = 1, ROWS_STAGED = 2, ROWS_SIGMA = 3, ROWS_RDM = 4;
+
+// per-row state of the direct traversals: row (sorted position), c_i, partial sum
+struct RowAcc {
+  int64_t i;
+  double ci;
+  double acc;
+};
 
 template <int MODE>
 __device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t j, bool ok, int64_t& w,
-                                      int32_t* out) {
+                                      int32_t* out, RowAcc& ra) {
   const int lane = threadIdx.x & 31;
   unsigned m = __ballot_sync(0xffffffffu, ok);
-  if (MODE != ROWS_COUNT && ok) {
+  if ((MODE == ROWS_FILL || MODE == ROWS_STAGED) && ok) {
     int64_t pos = w + __popc(m & ((1u << lane) - 1u));
     if (MODE == ROWS_FILL || pos < A.scr_cap) out[pos] = A.s2i[j];
+  }
+  if (MODE == ROWS_SIGMA && ok) ra.acc = fma(connection_el(A.H, ki, A.V[j]), A.dc[j], ra.acc);
+  if (MODE == ROWS_RDM && ok && j > ra.i) {
+    const double cc = ra.ci * A.dc[j];
+    if (cc != 0.0) rdm_accumulate(A.R, A.n, ki, A.V[j], cc);
   }
   w += __popc(m);
 }
@@ -278,7 +300,7 @@ __device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t
 template <int MODE, bool BETA>
 __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, int g, int64_t& w, int32_t* out,
                                            int64_t* s_start, int64_t* s_pref, int64_t* s_size, const int* occ_o,
-                                           const int* vir_o, int nocc_o, int nvir_o) {
+                                           const int* vir_o, int nocc_o, int nvir_o, RowAcc& ra) {
   const int lane = threadIdx.x & 31;
   const int64_t* ptr = BETA ? A.bnbr_ptr : A.anbr_ptr;
   const int32_t* nbr = BETA ? A.bnbr : A.anbr;
@@ -325,7 +347,7 @@ __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, in
         else { j = pos; other = A.vb[pos]; }
         ok = __popcll(mine ^ other) == 2;
       }
-      visit<MODE>(A, ki, j, ok, w, out);
+      visit<MODE>(A, ki, j, ok, w, out, ra);
     }
     unsigned lk = __ballot_sync(0xffffffffu, look);
     while (lk) {
@@ -350,7 +372,7 @@ __device__ __forceinline__ void mixed_side(const GraphArgs& A, ulonglong2 ki, in
             if (x == want) { ok = true; j = BETA ? A.permb[st2 + lo] : st2 + lo; }
           }
         }
-        visit<MODE>(A, ki, j, ok, w, out);
+        visit<MODE>(A, ki, j, ok, w, out, ra);
       }
     }
     __syncwarp();
@@ -400,6 +422,7 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
     int32_t* out = MODE == ROWS_FILL ? A.col
                    : MODE == ROWS_STAGED ? A.scr + (int64_t)(blockIdx.x * G_WARPS + wid) * A.scr_cap
                                          : nullptr;
+    RowAcc ra{i, (MODE == ROWS_SIGMA || MODE == ROWS_RDM) ? A.dc[i] : 0.0, 0.0};
     // (A) same alpha string
     {
       const int g = A.ia[i];
@@ -416,8 +439,8 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
           const int d = __popcll(ki.y ^ x2);
           ok2 = d == 2 || d == 4;
         }
-        visit<MODE>(A, ki, j, ok, w, out);
-        if (j0 + 32 < e) visit<MODE>(A, ki, j2, ok2, w, out);
+        visit<MODE>(A, ki, j, ok, w, out, ra);
+        if (j0 + 32 < e) visit<MODE>(A, ki, j2, ok2, w, out, ra);
       }
     }
     // (B) same beta string
@@ -438,10 +461,10 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
           ok2 = d == 2 || d == 4;
         }
         const int64_t j = (MODE != ROWS_COUNT && ok) ? (int64_t)A.permb[k] : -1;
-        visit<MODE>(A, ki, j, ok, w, out);
+        visit<MODE>(A, ki, j, ok, w, out, ra);
         if (k0 + 32 < e) {
           const int64_t j2 = (MODE != ROWS_COUNT && ok2) ? (int64_t)A.permb[k2] : -1;
-          visit<MODE>(A, ki, j2, ok2, w, out);
+          visit<MODE>(A, ki, j2, ok2, w, out, ra);
         }
       }
     }
@@ -451,14 +474,22 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
       if (A.costa[ga_i] <= A.costb[gb_i]) {
         const int no = occ_vir_lists(ki.y, A.n, s_occ[wid], s_vir[wid]);
         mixed_side<MODE, false>(A, ki, ga_i, w, out, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid],
-                                s_vir[wid], no, A.n - no);
+                                s_vir[wid], no, A.n - no, ra);
       } else {
         const int no = occ_vir_lists(ki.x, A.n, s_occ[wid], s_vir[wid]);
         mixed_side<MODE, true>(A, ki, gb_i, w, out, s_start[wid], s_pref[wid], s_size[wid], s_occ[wid],
-                               s_vir[wid], no, A.n - no);
+                               s_vir[wid], no, A.n - no, ra);
       }
     }
     if (MODE == ROWS_COUNT && lane == 0) A.rowcnt[q] = w;
+    if (MODE == ROWS_SIGMA) {
+      double a = ra.acc;
+      for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) {
+        A.dsig[i] = fma(A.ddiag[i], ra.ci, a);
+        if (A.dnnz) atomicAdd(A.dnnz, (unsigned long long)w);
+      }
+    }
     if (MODE == ROWS_STAGED) {
       __syncwarp();
       int64_t base = -1;
@@ -973,6 +1004,8 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
 // Group structures of the space in G.keys (nV determinants): alpha groups,
 // beta-major order and beta groups, single-excitation neighbour lists of the
 // distinct alpha and beta strings, and the (C) search cost per string.
+static void space_args(hci_ctx* ctx, int64_t nV, GraphArgs& A);
+
 static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   Graph& G = ctx->graph;
   prof_tic(ctx, HCI_PH_GRAPH_SPACE);
@@ -1058,7 +1091,16 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
                                                  Lside[s], bp<int64_t>(*costs[s]));
   }
   HCI_CUDA(ctx, cudaGetLastError());
-  A.V = V;
+  space_args(ctx, nV, A);
+  prof_toc(ctx, HCI_PH_GRAPH_SPACE);
+  return HCI_OK;
+}
+
+// Traversal arguments of the space built by build_space (pointers only).
+static void space_args(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
+  const int n = ctx->n;
+  A = GraphArgs{};
+  A.V = bp<ulonglong2>(ctx->graph.keys);
   A.bk = bp<ulonglong2>(ctx->g_bkeys);
   A.nV = nV;
   A.n = n; A.na = ctx->na; A.nb = ctx->nb;
@@ -1084,8 +1126,8 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   A.nrows = nV;
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr; A.rowcnt = nullptr;
   A.scr = nullptr; A.scr_cap = 0; A.stage = nullptr; A.stage_cap = 0; A.rowoff = nullptr; A.stage_ctl = nullptr;
-  prof_toc(ctx, HCI_PH_GRAPH_SPACE);
-  return HCI_OK;
+  A.s2i = bp<int32_t>(ctx->graph.s2i);
+  A.dc = nullptr; A.dsig = nullptr; A.ddiag = nullptr; A.dnnz = nullptr;
 }
 
 // Count the entries of the rows listed in A (A.rowlist / A.nrows) into cnt.
@@ -1226,6 +1268,9 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   const int64_t nnz = read_i64(ctx, dtot, &st);
   HCI_TRY(st);
   const int64_t cap = used + used / 4 + 1024;
+  if (ctx->graph_budget > 0 && cap * 12 > ctx->graph_budget)
+    return hci_fail(ctx, HCI_ERR_NOMEM, "graph: a pool of %lld bytes exceeds the budget of %lld", (long long)(cap * 12),
+                    (long long)ctx->graph_budget);
   HCI_TRY(ensure_buf(ctx, G.col, (size_t)cap * 4));
   HCI_TRY(ensure_buf(ctx, G.val, (size_t)cap * 8));
   HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val)));
@@ -1384,6 +1429,10 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   int64_t base = G.pool_used;
   if (repack) {
     const int64_t cap = total + total / 4 + 1024;
+    // the old pool stays alive while the new one is filled
+    if (ctx->graph_budget > 0 && (cap + G.pool_cap) * 12 > ctx->graph_budget)
+      return hci_fail(ctx, HCI_ERR_NOMEM, "graph: repacking into %lld bytes exceeds the budget of %lld",
+                      (long long)(cap * 12), (long long)ctx->graph_budget);
     HCI_TRY(ensure_buf(ctx, S.col_old, (size_t)cap * 4));
     HCI_TRY(ensure_buf(ctx, S.val_old, (size_t)cap * 8));
     col_dst = bp<int32_t>(S.col_old);
@@ -1433,6 +1482,47 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   return HCI_OK;
 }
 
+// Direct form: the space's search structures and diagonal only (internal
+// ids = sorted positions); every traversal searches the rows again.
+static hci_status graph_build_direct(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
+  Graph& G = ctx->graph;
+  G.valid = false;
+  if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 indices");
+  prof_tic(ctx, HCI_PH_GRAPH);
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  HCI_TRY(ensure_buf(ctx, G.keys_int, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys_int.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  HCI_TRY(ensure_buf(ctx, G.s2i, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, G.i2s, (size_t)nV * 4));
+  HCI_LAUNCH(k_iota, grid_for(nV, 256), 256, 0, ctx->st)(bp<int32_t>(G.s2i), bp<int32_t>(G.i2s), nV);
+  GraphArgs A;
+  HCI_TRY(build_space(ctx, nV, A));
+  HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
+  HCI_TRY(compute_diag(ctx, nV, bp<ulonglong2>(G.keys_int), bp<double>(G.diag)));
+  prof_toc(ctx, HCI_PH_GRAPH);
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  G.nV = nV;
+  G.nnz = -1;   // counted by the first direct sigma
+  G.direct = true;
+  ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
+  G.valid = true;
+  return HCI_OK;
+}
+
+// the stored rows and the incremental scratch, released before a direct build
+static void release_stored(hci_ctx* ctx) {
+  Graph& G = ctx->graph;
+  IncScratch& S = ctx->inc;
+  DevBuf* bufs[] = {&G.rowptr, &G.rowstart, &G.rowlen, &G.rowcap, &G.col, &G.val, &S.col_old, &S.val_old,
+                    &S.colN, &S.valN, &S.T, &S.T2, &S.scr, &S.stage};
+  for (DevBuf* b : bufs) free_buf(ctx->st, *b);
+  G.pool_used = G.pool_cap = 0;
+  G.nnz = 0;
+  cudaStreamSynchronize(ctx->st);
+}
+
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   uint64_t hsh = 0;
   HCI_TRY(hash_keys(ctx, keys, nV, &hsh));
@@ -1440,19 +1530,83 @@ hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   int ok = 0;
   HCI_TRY(check_sorted(ctx, keys, nV, &ok));
   if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "keys are not strictly ascending");
-  bool done = false;
-  if (ctx->graph.valid && ctx->incremental) {
+  const bool direct = ctx->sigma_mode == HCI_SIGMA_DIRECT || (ctx->sigma_mode == HCI_SIGMA_AUTO && ctx->direct_fallback);
+  if (!direct) {
+    hci_status s = HCI_OK;
+    bool done = false;
+    if (ctx->graph.valid && !ctx->graph.direct && ctx->incremental) {
+      ctx->graph.valid = false;
+      s = graph_extend(ctx, keys, nV, &done);
+    }
+    if (s == HCI_OK && !done) {
+      ctx->graph.direct = false;
+      s = graph_build(ctx, keys, nV);
+    }
+    if (s == HCI_OK) {
+      ctx->graph.hash = hsh;
+      ctx->graph.valid = true;
+      return HCI_OK;
+    }
+    if (s != HCI_ERR_NOMEM || ctx->sigma_mode != HCI_SIGMA_AUTO) return s;
+    // the connections do not fit: search them again in every traversal
     ctx->graph.valid = false;
-    HCI_TRY(graph_extend(ctx, keys, nV, &done));
+    ctx->direct_fallback = true;
+    release_stored(ctx);
   }
-  if (!done) HCI_TRY(graph_build(ctx, keys, nV));
+  HCI_TRY(graph_build_direct(ctx, keys, nV));
   ctx->graph.hash = hsh;
   ctx->graph.valid = true;
   return HCI_OK;
 }
 
+// H c of a direct graph: every row's connections searched and evaluated
+static hci_status sigma_direct(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
+  Graph& G = ctx->graph;
+  GraphArgs A;
+  space_args(ctx, G.nV, A);
+  A.ddiag = bp<double>(G.diag);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 56);
+  for (int v = 0; v < nvec; ++v) {
+    A.dc = c + (int64_t)v * G.nV;
+    A.dsig = sigma + (int64_t)v * G.nV;
+    A.dnnz = G.nnz < 0 ? cnt : nullptr;
+    if (A.dnnz) HCI_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8, ctx->st));
+    HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
+    HCI_LAUNCH(k_rows<ROWS_SIGMA>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
+    HCI_CUDA(ctx, cudaGetLastError());
+    if (A.dnnz) {
+      unsigned long long h = 0;
+      HCI_CUDA(ctx, cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, ctx->st));
+      HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+      G.nnz = (int64_t)h;
+    }
+  }
+  return HCI_OK;
+}
+
+hci_status direct_rdm(hci_ctx* ctx, const double* c, const RdmAcc& R) {
+  Graph& G = ctx->graph;
+  GraphArgs A;
+  space_args(ctx, G.nV, A);
+  A.dc = c;
+  A.R = R;
+  HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
+  HCI_LAUNCH(k_rows<ROWS_RDM>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_CUDA(ctx, cudaGetLastError());
+  return HCI_OK;
+}
+
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
   Graph& G = ctx->graph;
+  if (G.direct) {
+    prof_tic(ctx, HCI_PH_SIGMA);
+    HCI_TRY(sigma_direct(ctx, c, sigma, nvec));
+    ctx->st_counts[HCI_ST_SIGMA_CALLS] += nvec;
+    ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;
+    ctx->st_counts[HCI_ST_SIGMA_NNZ] += G.nnz * nvec;
+    prof_toc(ctx, HCI_PH_SIGMA);
+    return HCI_OK;
+  }
   prof_tic(ctx, HCI_PH_SIGMA);
   ctx->st_counts[HCI_ST_SIGMA_CALLS] += nvec;
   ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;

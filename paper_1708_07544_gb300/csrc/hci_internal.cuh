@@ -42,6 +42,7 @@ struct Graph {
   DevBuf keys;               // copy of the space's keys [nV][2], sorted
   DevBuf keys_int;           // the same keys by internal id (insertion order)
   DevBuf s2i, i2s;           // int32 maps sorted position <-> internal id
+  bool direct = false;       // no stored rows: every traversal searches and evaluates the connections again
 };
 
 struct Lists {
@@ -90,6 +91,9 @@ struct hci_ctx {
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
   IncScratch inc;
   bool incremental = true;
+  int sigma_mode = HCI_SIGMA_AUTO;
+  int64_t graph_budget = 0;  // bytes the stored connection pool may take (0: device memory)
+  bool direct_fallback = false;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
   int64_t last_candidates = 0;
   int64_t st_counts[HCI_ST_COUNT] = {};
@@ -162,6 +166,9 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 // sigma on vectors in internal order (rows/columns of the cached graph)
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec);
+struct RdmAcc;
+// off-diagonal RDM contributions of a direct graph (one orientation per pair)
+hci_status direct_rdm(hci_ctx* ctx, const double* c, const RdmAcc& R);
 // density matrices of the perturbative correction (rdm.cu)
 hci_status pt2_rdm_begin(hci_ctx* ctx);
 hci_status pt2_rdm_pairs(hci_ctx* ctx, const ulonglong2* V, const double* c, const ulonglong2* tgt, const int32_t* src,

@@ -19,85 +19,12 @@
 // occupation correlation M[sp][tq] = sum_i c_i^2 n_sp(i) n_tq(i), folded over
 // the alpha and beta string groups of the graph.
 #include "hci_internal.cuh"
+#include "rdm_acc.cuh"
 
 namespace {
 
 constexpr int R_WARPS = 8;
 
-__device__ __forceinline__ void add2(double* r2, int n, int p, int q, int r, int s, double v) {
-  atomicAdd(&r2[(((int64_t)p * n + q) * n + r) * n + s], v);
-}
-
-// One orientation of every connected pair (column id above the row id): the
-// other orientation contributes the transpose (p,q,r,s) -> (q,p,s,r), added
-// in k_rdm_finish.  Doubles go to Hh (n^4).  A single a -> b of spin S in
-// D_j with weight w adds w to S1[S][b][a]; its spectator terms
-// sum w n_k(D_j) are split into the aufbau occupation (expanded in
-// k_rdm_finish) plus the orbitals where D_j's strings differ from the
-// aufbau ones, accumulated in Dt[b][a][k] (both spins) and Dx[b][a][k]
-// (same spin, for the exchange terms).
-struct RdmAcc {
-  double* Hh;
-  double* S1;
-  double* Dt;
-  double* Dx;
-  uint64_t ref_a, ref_b;
-};
-
-// <ki| op |kj> of one connected pair (a single or double excitation apart)
-// with weight cc, accumulated into R (doubles into Hh, singles into S1 / Dt /
-// Dx as described above)
-__device__ __forceinline__ void rdm_accumulate(const RdmAcc& R, int n, ulonglong2 ki, ulonglong2 kj, double cc) {
-  const uint64_t xa = ki.x ^ kj.x, xb = ki.y ^ kj.y;
-  const int da = __popcll(xa), db = __popcll(xb);
-  if (da + db == 2) {
-    // single a -> b in spin S
-    const int S = da == 2 ? 0 : 1;
-    const uint64_t sj = S == 0 ? kj.x : kj.y, oj = S == 0 ? kj.y : kj.x;
-    const uint64_t x = S == 0 ? xa : xb;
-    const int a = __ffsll((long long)(sj & x)) - 1;
-    const int bb = __ffsll((long long)(x & ~sj)) - 1;
-    const double w = cc * exc_phase(sj, a, bb);
-    atomicAdd(&R.S1[((int64_t)S * n + bb) * n + a], w);
-    const uint64_t rs = S == 0 ? R.ref_a : R.ref_b, ro = S == 0 ? R.ref_b : R.ref_a;
-    double* dt = R.Dt + ((int64_t)bb * n + a) * n;
-    double* dx = R.Dx + ((int64_t)bb * n + a) * n;
-    for (uint64_t m = sj & ~rs; m; m &= m - 1) {
-      const int kk = __ffsll((long long)m) - 1;
-      atomicAdd(dt + kk, w);
-      atomicAdd(dx + kk, w);
-    }
-    for (uint64_t m = rs & ~sj; m; m &= m - 1) {
-      const int kk = __ffsll((long long)m) - 1;
-      atomicAdd(dt + kk, -w);
-      atomicAdd(dx + kk, -w);
-    }
-    for (uint64_t m = oj & ~ro; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, w);
-    for (uint64_t m = ro & ~oj; m; m &= m - 1) atomicAdd(dt + __ffsll((long long)m) - 1, -w);
-  } else if (da == 4 || db == 4) {
-    const uint64_t sj = da == 4 ? kj.x : kj.y;
-    const uint64_t x = da == 4 ? xa : xb;
-    uint64_t holes = sj & x, parts = x & ~sj;
-    const int a = __ffsll((long long)holes) - 1; holes &= holes - 1;
-    const int bh = __ffsll((long long)holes) - 1;
-    const int cp = __ffsll((long long)parts) - 1; parts &= parts - 1;
-    const int d = __ffsll((long long)parts) - 1;
-    const double s1 = exc_phase(sj, a, cp);
-    const uint64_t t = sj ^ (1ull << a) ^ (1ull << cp);
-    const double w = cc * s1 * exc_phase(t, bh, d);
-    add2(R.Hh, n, cp, a, d, bh, w);
-    add2(R.Hh, n, d, bh, cp, a, w);
-    add2(R.Hh, n, cp, bh, d, a, -w);
-    add2(R.Hh, n, d, a, cp, bh, -w);
-  } else {
-    // alpha a -> c, beta b -> d
-    const int a = __ffsll((long long)(kj.x & xa)) - 1, cp = __ffsll((long long)(ki.x & xa)) - 1;
-    const int bh = __ffsll((long long)(kj.y & xb)) - 1, d = __ffsll((long long)(ki.y & xb)) - 1;
-    const double w = cc * exc_phase(kj.x, a, cp) * exc_phase(kj.y, bh, d);
-    add2(R.Hh, n, cp, a, d, bh, w);
-    add2(R.Hh, n, d, bh, cp, a, w);
-  }
-}
 
 __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulonglong2* __restrict__ V, int64_t nV,
                                                               const double* __restrict__ c,
@@ -501,10 +428,13 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   R.Dx = R.Dt + n3;
   R.ref_a = ctx->na == 64 ? ~0ull : ((1ull << ctx->na) - 1ull);
   R.ref_b = ctx->nb == 64 ? ~0ull : ((1ull << ctx->nb) - 1ull);
-  HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
-                                                         bp<int64_t>(ctx->graph.rowptr),
-                                                         bp<int64_t>(ctx->graph.rowstart),
-                                                         bp<int32_t>(ctx->graph.col), R, queue);
+  if (ctx->graph.direct)
+    HCI_TRY(direct_rdm(ctx, ci, R));   // connections searched again, one orientation each
+  else
+    HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
+                                                           bp<int64_t>(ctx->graph.rowptr),
+                                                           bp<int64_t>(ctx->graph.rowstart),
+                                                           bp<int32_t>(ctx->graph.col), R, queue);
   HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, rdm1, rdm2, 1);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);

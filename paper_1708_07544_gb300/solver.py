@@ -56,6 +56,10 @@ class HCISolver:
         also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
         return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs, self.norb if rdms else None)
 
+    def set_sigma_mode(self, mode, graph_budget=0):
+        """_abi.SIGMA_AUTO / SIGMA_STORED / SIGMA_DIRECT (see hci_set_sigma_mode)."""
+        _abi.hci_set_sigma_mode(self.ctx, mode, graph_budget)
+
     def pt2_semistochastic(self, keys, c, e0, eps2, eps2_det, n_draws, n_samples, seed=0, max_pairs=0):
         """E2(eps2) ~ E2^D(eps2_det) + mean of E2^S(eps2) - E2^S(eps2_det)
         over n_samples samples of n_draws determinants (Eq. semistoc)."""
