@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--sigma-reps", type=int, default=20)
     ap.add_argument("--fwd-bwd-reps", type=int, default=2)
     ap.add_argument("--pt2-reps", type=int, default=2)
+    ap.add_argument("--direct-reps", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1, help="also time the 64-instance batched solve")
     return ap.parse_args()
 
@@ -333,6 +334,30 @@ def gpu_arm(args):
                                   "n_samples": PT2_SS_SAMPLES, "E2": ss["estimate"], "error": ss["error"],
                                   "E2_det": ss["e2_det"], "seconds": round(t_ss, 4)}}
     s.close()
+    # the same H c with the connections searched and evaluated again in every
+    # product (no stored graph; the form for spaces whose connections exceed
+    # device memory): its first call builds the search structures
+    direct = {}
+    if args.direct_reps > 0:
+        sd = pkg.HCISolver(n, inst.nalpha, inst.nbeta, h2, e2, inst.e_core)
+        sd.set_sigma_mode(_abi.SIGMA_DIRECT)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sd_sig = sd.sigma(keys, c)
+        torch.cuda.synchronize()
+        t_first = time.perf_counter() - t0
+        td = []
+        for _ in range(args.direct_reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sd_sig = sd.sigma(keys, c)
+            torch.cuda.synchronize()
+            td.append(time.perf_counter() - t0)
+        dev_max = float((sd_sig - sig).abs().max().item())
+        st_d = sd.stats()
+        sd.close()
+        direct = {"sigma_ms": round(1e3 * statistics.median(td), 3), "first_call_ms": round(1e3 * t_first, 3),
+                  "connections": st_d["graph_nnz"], "max_abs_diff_vs_stored": dev_max, "reps": args.direct_reps}
     sig_ms = tm["sigma"][0] / max(tm["sigma"][1], 1)
     nnz = st["graph_nnz"]
     nV = int(keys.shape[0])
@@ -434,6 +459,7 @@ def gpu_arm(args):
                              "bytes_per_launch": sig_bytes},
             "fwd_bwd": fb,
             "pt2": pt2,
+            "sigma_direct": direct,
             "batch": batch,
             "e2e": {"value": round(aggregate_seconds(e2e_step, world), 6), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
