@@ -167,8 +167,8 @@ hci_status hci_set_sigma_mode(hci_ctx* ctx, int mode, int64_t graph_budget);
  * E2^D the deterministic hci_pt2 value, and both stochastic terms of a
  * sample s evaluated on the same draws: n_draws determinants of V drawn
  * with replacement, D_i with probability p_i = W_i / sum W, W_i =
- * ceil(|c_i| 2^(40 - E)) with 2^(E-1) <= max|c| < 2^E (p_i proportional to
- * |c_i| to 2^-40).  Draw k of sample s takes the first word r of
+ * ceil(|c_i| 2^(B - E)) with 2^(E-1) <= max|c| < 2^E, B = 40 for nV <= 2^22
+ * and 62 - ceil(log2 nV) above (p_i proportional to |c_i| to 2^-B).  Draw k of sample s takes the first word r of
  * Philox4x64-10 (Salmon et al., SC'11) at counter (k, s, 0, 0) and key
  * (seed, 0), u = floor(r sum W / 2^64), and the index i with
  * W_0 + .. + W_{i-1} <= u < W_0 + .. + W_i.  Each sample's estimate is the
@@ -177,7 +177,7 @@ hci_status hci_set_sigma_mode(hci_ctx* ctx, int mode, int64_t graph_budget);
  * screen (|H_aj c_j| > eps), with x_j = H_aj c_j, f_j = w_j / p_j (w_j =
  * times drawn), S = sum f_j x_j, T = sum (f_j x_j)^2, U = sum f_j x_j^2:
  *   E2^S = sum_a (S^2 - T + (N_d - 1) U) / (N_d (N_d - 1) (e0 - H_aa)).
- * keys, c, e0, max_pairs: as hci_pt2 (keys strictly ascending, nV <= 2^22).
+ * keys, c, e0, max_pairs: as hci_pt2 (keys strictly ascending, nV < 2^31).
  * eps2 <= eps2_det.  n_draws >= 2, n_samples >= 1, n_draws * n_samples <
  * 2^31.  result: host [3] = {estimate, its standard error over the samples
  * (0 for one sample), E2^D(eps2_det)}.  sample_e2: host [n_samples][2] =

@@ -212,15 +212,20 @@ def philox4x64(ctr, key, rounds=10):
 
 def sample_weights(c):
     """Integer sampling weights W_i proportional to |c_i| (reading: p_i =
-    |c_i| / sum_j |c_j| to 2^-40 relative): W_i = ceil(|c_i| 2^(40 - E))
-    with 2^(E-1) <= max|c| < 2^E, so every non-zero c_i has W_i >= 1 and
-    the weights and their prefix sums are exact integers in any order.
-    Returns (W as Python ints, total)."""
+    |c_i| / sum_j |c_j| to 2^-B relative): W_i = ceil(|c_i| 2^(B - E))
+    with 2^(E-1) <= max|c| < 2^E, B = 40 for up to 2^22 determinants and
+    62 - ceil(log2 n) above (so that the sum stays below 2^62); every
+    non-zero c_i has W_i >= 1 and the weights and their prefix sums are
+    exact integers in any order.  Returns (W as Python ints, total)."""
     a = np.abs(np.asarray(c, np.float64))
     if a.size == 0 or a.max() == 0.0:
         return [0] * a.size, 0
+    lg = 0
+    while (1 << lg) < a.size:
+        lg += 1
+    B = 40 if lg <= 22 else 62 - lg
     e = int(np.frexp(a.max())[1])
-    W = [int(x) for x in np.ceil(np.ldexp(a, 40 - e))]
+    W = [int(x) for x in np.ceil(np.ldexp(a, B - e))]
     return W, sum(W)
 
 

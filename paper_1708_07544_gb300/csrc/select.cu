@@ -959,13 +959,13 @@ __global__ void k_abs_max(const double* __restrict__ c, int64_t n, unsigned long
   if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
 }
 
-// W_i = ceil(|c_i| 2^(40 - E)), 2^(E-1) <= max|c| < 2^E: W_i >= 1 iff c_i != 0, sum W < 2^63 for n < 2^22
+// W_i = ceil(|c_i| 2^(B - E)), 2^(E-1) <= max|c| < 2^E: W_i >= 1 iff c_i != 0, W_i <= 2^B, sum W <= 2^62
 __global__ void k_ss_weights(const double* __restrict__ c, int64_t n, const unsigned long long* __restrict__ mx,
-                             int64_t* __restrict__ W) {
+                             int B, int64_t* __restrict__ W) {
   int e = 0;
   frexp(__longlong_as_double((long long)*mx), &e);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    W[i] = (int64_t)ceil(ldexp(fabs(c[i]), 40 - e));
+    W[i] = (int64_t)ceil(ldexp(fabs(c[i]), B - e));
 }
 
 // draws: key (x = sample, y = drawn index) for the sort, and the index alone
@@ -1095,8 +1095,7 @@ extern "C" hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, con
   if (n_draws * (int64_t)n_samples > INT32_MAX)
     return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: n_draws * n_samples exceeds 2^31 - 1");
   if (!(eps2 <= eps2_det)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: eps2 must not exceed eps2_det");
-  if (nV > ((int64_t)1 << 22))
-    return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: more than 2^22 determinants");
+  if (nV > INT32_MAX) return hci_fail(ctx, HCI_ERR_INVALID, "hci_pt2_stochastic: more than 2^31 - 1 determinants");
   if (sample_e2)
     for (int s = 0; s < 2 * n_samples; ++s) sample_e2[s] = 0.0;
   if (nV == 0) return HCI_OK;
@@ -1116,7 +1115,11 @@ extern "C" hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, con
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(total + 1);
   HCI_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
   HCI_LAUNCH(k_abs_max, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx);
-  HCI_LAUNCH(k_ss_weights, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx, W);
+  // weight scale 2^B: 2^40, or less so that nV 2^B <= 2^62
+  int lg = 0;
+  while (((int64_t)1 << lg) < nV) ++lg;
+  const int B = lg <= 22 ? 40 : 62 - lg;
+  HCI_LAUNCH(k_ss_weights, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx, B, W);
   HCI_TRY(scan_i64(ctx, W, excl, nV, total));
   int64_t tot_h = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&tot_h, total, 8, cudaMemcpyDeviceToHost, st));

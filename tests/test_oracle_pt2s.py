@@ -62,6 +62,19 @@ def test_weights_proportional_to_abs_c():
     assert np.abs(W / W.max() - a / a.max()).max() < 2.0**-38
 
 
+def test_weights_above_2_22_determinants_keep_the_sum_below_2_62():
+    n = (1 << 22) + 5                      # ceil(log2 n) = 23: scale 2^39
+    c = np.full(n, 1e-3)
+    c[0] = -0.9
+    c[7] = 0.0
+    W, total = oracle.sample_weights(c)
+    assert total < 2**62
+    W = np.array(W, dtype=np.float64)
+    assert 2.0**38 <= W.max() <= 2.0**39 and W[7] == 0.0 and W[W > 0].min() >= 1.0
+    a = np.abs(c)
+    assert np.abs(W / W.max() - a / a.max()).max() < 2.0**-37
+
+
 def _expectation(inst, keys, c, e0, nd, eps2, eps2d):
     W, total = oracle.sample_weights(c)
     p = np.array([w / total for w in W])
