@@ -315,6 +315,8 @@ hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, co
 /* Work counters of this context (instrumentation; the paper reports only
  * wall times per HCISCF iteration, Sec. V).  out[k] for k < nout:
  *   HCI_ST_GRAPH_NNZ        off-diagonal connections of the cached graph
+ *                           (direct form: counted by its first product, 0
+ *                           before)
  *   HCI_ST_LAST_CANDIDATES  candidates emitted by the last selection
  *   HCI_ST_SIGMA_CALLS      H c products so far (one per vector)
  *   HCI_ST_SIGMA_ROWS       rows processed by them

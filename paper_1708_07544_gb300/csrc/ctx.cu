@@ -374,7 +374,7 @@ extern "C" hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout) {
   if (nout < 0 || (nout > 0 && !out)) return HCI_ERR_INVALID;
   int64_t v[HCI_ST_COUNT];
   for (int k = 0; k < HCI_ST_COUNT; ++k) v[k] = ctx->st_counts[k];
-  v[HCI_ST_GRAPH_NNZ] = ctx->graph.valid ? ctx->graph.nnz : 0;
+  v[HCI_ST_GRAPH_NNZ] = ctx->graph.valid && ctx->graph.nnz > 0 ? ctx->graph.nnz : 0;
   v[HCI_ST_LAST_CANDIDATES] = ctx->last_candidates;
   v[HCI_ST_SIGMA_DIRECT] = ctx->graph.valid && ctx->graph.direct ? 1 : 0;
   for (int k = 0; k < nout && k < HCI_ST_COUNT; ++k) out[k] = v[k];
