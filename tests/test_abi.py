@@ -55,3 +55,25 @@ def test_product_path_has_no_oracle_import():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "hci_oracle" not in src and "orc_" not in src, f
+
+
+def _enum_values():
+    txt = open(os.path.join(ROOT, "include", "hci.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(HCI_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+
+
+def test_binding_constants_match_header():
+    from paper_1708_07544_gb300 import _abi
+
+    ev = _enum_values()
+    assert ev["HCI_ST_COUNT"] == len(_abi.STATS)
+    for i, name in enumerate(_abi.STATS):
+        assert ev["HCI_ST_" + name.upper()] == i, name
+    assert (ev["HCI_SIGMA_AUTO"], ev["HCI_SIGMA_STORED"], ev["HCI_SIGMA_DIRECT"]) == \
+        (_abi.SIGMA_AUTO, _abi.SIGMA_STORED, _abi.SIGMA_DIRECT)
+    assert ev["HCI_PH_COUNT"] == len(_abi.PHASES)
+    for i, name in enumerate(_abi.PHASES):
+        assert ev["HCI_PH_" + name.upper()] == i, name
+    for name in ["INVALID", "CAPACITY", "NOT_CONVERGED", "CUDA", "NOMEM"]:
+        assert ev["HCI_ERR_" + name] == getattr(_abi, "HCI_ERR_" + name), name
