@@ -186,6 +186,33 @@ def pt2_rdm(inst, keys, c, eps2, e0):
     return tuple(out)
 
 
+def spin_square(norb, keys, c):
+    """<S^2> of the state sum_i c_i |D_i> (the spin of the states Sec. VI
+    compares): S^2 = S_- S_+ + S_z (S_z + 1), with ||S_+ c||^2 evaluated by
+    applying S_+ = sum_p a+_{p alpha} a_{p beta} to every determinant (alpha
+    block then beta block, ascending: the sign of a+_{p alpha} a_{p beta} is
+    (-1)^(n_alpha + #beta below p + #alpha below p)).  Small spaces only."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    c = np.asarray(c, np.float64)
+    if len(keys) == 0:
+        return 0.0
+    na = bin(int(keys[0, 0])).count("1")
+    nb = bin(int(keys[0, 1])).count("1")
+    out = {}
+    for (ka, kb), ci in zip(keys.tolist(), c.tolist()):
+        if ci == 0.0:
+            continue
+        for p in range(norb):
+            if not (kb >> p) & 1 or (ka >> p) & 1:
+                continue
+            below = (1 << p) - 1
+            sgn = -1.0 if (na + bin(kb & below).count("1") + bin(ka & below).count("1")) % 2 else 1.0
+            t = (ka | (1 << p), kb & ~(1 << p))
+            out[t] = out.get(t, 0.0) + sgn * ci
+    sz = 0.5 * (na - nb)
+    return float(sum(v * v for v in out.values()) + sz * (sz + 1.0) * float(c @ c))
+
+
 # ----------------------------------------------------------------------------
 # semistochastic second-order correction (Sec. II.B, Eq. semistoc)
 # ----------------------------------------------------------------------------
