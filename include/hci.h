@@ -213,6 +213,14 @@ hci_status hci_relaxed_rdm12(hci_ctx* ctx, double eps2, const uint64_t* keys, co
                              int64_t max_pairs, double zv_tol, int zv_maxit, double* e2, double* rdm1,
                              double* rdm2);
 
+/* <S^2> of a state from its spin-summed 2-RDM (rdm2 as hci_rdm12 writes it,
+ * device [n][n][n][n]): -N (N - 4) / 4 - 1/2 sum_pq rdm2[p,q,q,p], which
+ * follows from S^2 = S_z^2 + (S_+ S_- + S_- S_+) / 2 and the definition of
+ * rdm2.  Tells the spin of the states of several roots (the paper's singlet
+ * and triplet states, Sec. VI) apart within one S_z sector.  s2: host out.
+ * Synchronises. */
+hci_status hci_spin_square(hci_ctx* ctx, const double* rdm2, double* s2);
+
 /* The nroots lowest eigenpairs on V (ascending), one after the other by
  * Davidson deflated against the converged lower ones (each start vector and
  * correction kept orthogonal to them).  c_inout: device [nroots][nV], start

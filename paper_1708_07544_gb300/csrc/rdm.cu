@@ -442,6 +442,38 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   return HCI_OK;
 }
 
+namespace {
+// <S^2> = -N (N - 4) / 4 - 1/2 sum_pq rdm2[p,q,q,p], from S^2 = S_z^2 +
+// (S_+ S_- + S_- S_+) / 2 written with the spin-summed 2-RDM of hci_rdm12
+__global__ void k_spin_square(const double* __restrict__ rdm2, int n, int nelec, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int p = t / n, q = t % n;
+    s += rdm2[(((int64_t)p * n + q) * n + q) * n + p];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = -0.25 * nelec * (nelec - 4.0) - 0.5 * red[0];
+}
+}  // namespace
+
+extern "C" hci_status hci_spin_square(hci_ctx* ctx, const double* rdm2, double* s2) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_spin_square: null context");
+  if (!rdm2 || !s2) return hci_fail(ctx, HCI_ERR_INVALID, "hci_spin_square: null pointer");
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  double* d = reinterpret_cast<double*>(bp<char>(ctx->s_counter) + 32);
+  HCI_LAUNCH(k_spin_square, 1, 256, 0, ctx->st)(rdm2, ctx->n, ctx->na + ctx->nb, d);
+  HCI_CUDA(ctx, cudaGetLastError());
+  HCI_CUDA(ctx, cudaMemcpyAsync(s2, d, 8, cudaMemcpyDeviceToHost, ctx->st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  return HCI_OK;
+}
+
 // Density matrices of the perturbative correction, accumulated over the
 // hash classes of hci_pt2: begin (clear), pairs (once per class), finish.
 static RdmAcc pt2_acc(hci_ctx* ctx) {

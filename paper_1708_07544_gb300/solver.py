@@ -56,6 +56,10 @@ class HCISolver:
         also (rdm1_dd, rdm2_dd, rdm1_dc, rdm2_dc)."""
         return _abi.hci_pt2(self.ctx, keys, c, eps2, e0, max_pairs, self.norb if rdms else None)
 
+    def spin_square(self, rdm2):
+        """<S^2> of the state whose spin-summed 2-RDM is rdm2 (hci_rdm12)."""
+        return _abi.hci_spin_square(self.ctx, rdm2)
+
     def set_sigma_mode(self, mode, graph_budget=0):
         """_abi.SIGMA_AUTO / SIGMA_STORED / SIGMA_DIRECT (see hci_set_sigma_mode)."""
         _abi.hci_set_sigma_mode(self.ctx, mode, graph_budget)

@@ -76,3 +76,25 @@ def test_solve_roots_eps_zero_is_full_space(pkg):
         out = s.solve_roots(3, 0.0, dav_tol=1e-10)
     assert out["keys"].shape[0] == 20 * 15
     assert np.abs(out["E"] - w[:3]).max() < 1e-9
+
+
+@pytest.mark.parametrize("nalpha,nbeta", [(4, 4), (5, 3)])
+def test_spin_square_of_roots(pkg, nalpha, nbeta):
+    """<S^2> from each root's 2-RDM (hci_spin_square) against the oracle's
+    S_+ evaluation on the CI vector; at eps1 = 0 the roots are eigenstates
+    of S^2 (integer S), and S_z = 1 leaves S >= 1."""
+    p8 = hi.ppp_polyene(8)
+    inst = hi.Instance("p8", 8, nalpha, nbeta, p8.h, p8.eri, p8.e_core)
+    with solver(pkg, inst) as s:
+        out = s.solve_roots(4, 0.0, dav_tol=1e-10)
+        keys = out["keys"]
+        kh = host_keys(keys)
+        for r in range(4):
+            cr = out["c"][r].contiguous()
+            _, r2 = s.rdm12(keys, cr)
+            s2 = s.spin_square(r2)
+            want = oracle.spin_square(8, kh, cr.cpu().numpy())
+            assert abs(s2 - want) < 1e-8, (r, s2, want)
+            S = 0.5 * (np.sqrt(1.0 + 4.0 * s2) - 1.0)
+            assert abs(S - round(S)) < 1e-6, (r, s2)
+            assert S > 0.5 * (nalpha - nbeta) - 1e-6
