@@ -237,7 +237,9 @@ hci_status hci_davidson_roots(hci_ctx* ctx, const uint64_t* keys, int64_t nV, in
 /* Variational HCI for the nroots lowest states (Sec. II.A): D_a enters when
  * max_r |H_ai c_i^(r)| > eps1, i.e. the selection with c_i replaced by
  * max_r |c_i^(r)|; V^0 = {aufbau}, then select, merge (every state padded
- * with zeros) and hci_davidson_roots until the selection is empty.
+ * with zeros) and hci_davidson_roots (all states of V while it holds fewer
+ * than nroots determinants) until the selection is empty; HCI_ERR_INVALID
+ * when the final V is smaller than nroots.
  * keys_out: device [cap][2]; c_out: device with room for nroots * cap
  * doubles, written densely as [nroots][nV] (NULL allowed);
  * nV_out, energies [nroots], iters: host out.  HCI_ERR_CAPACITY when nV >

@@ -416,7 +416,9 @@ def hci_roots(inst, eps1, nroots, max_iter=30):
     """Variational HCI for the nroots lowest states: a determinant enters when
     max_r |H_ai c_i^(r)| > eps1 for some D_i, i.e. the selection of the
     single-state loop with c_i replaced by max_r |c_i^(r)|; V^0 = {aufbau}
-    (one state) and from the first selection on, all nroots states."""
+    (one state), then after each merge the nroots lowest states, or all of
+    them while V holds fewer determinants (reading: the paper is silent;
+    the space must reach nroots determinants by the end)."""
     P = Problem.of(inst)
     keys = aufbau(P.nalpha, P.nbeta)
     ceff = np.array([1.0])
@@ -426,10 +428,10 @@ def hci_roots(inst, eps1, nroots, max_iter=30):
         if len(new) == 0:
             break
         keys, _ = merge(keys, np.zeros(len(keys)), new)
-        if len(keys) < nroots:
-            raise ValueError("space smaller than the number of roots")
-        es, cs = lowest_states(P, keys, nroots)
+        es, cs = lowest_states(P, keys, min(nroots, len(keys)))
         ceff = np.abs(cs).max(axis=0)
+    if len(keys) < nroots:
+        raise ValueError("space smaller than the number of roots")
     return {"keys": keys, "c": cs, "E": es}
 
 

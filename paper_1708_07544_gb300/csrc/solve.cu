@@ -172,14 +172,21 @@ extern "C" hci_status hci_solve_roots(hci_ctx* ctx, int nroots, double eps1, int
     }
     cur = nxt;
     nV = nV2;
-    if (nV < nroots) { cleanup(); return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: space smaller than nroots"); }
-    s = hci_davidson_roots(ctx, bp<uint64_t>(kb[cur]), nV, nroots, bp<double>(cb[cur]), energies, dav_tol, dav_maxit,
+    // while V holds fewer determinants than roots: all of its states (the
+    // other rows of c stay zero)
+    const int nr = nV < nroots ? (int)nV : nroots;
+    s = hci_davidson_roots(ctx, bp<uint64_t>(kb[cur]), nV, nr, bp<double>(cb[cur]), energies, dav_tol, dav_maxit,
                            nullptr);
     if (s != HCI_OK) { cleanup(); return s; }
   }
   if (iters) *iters = mu;
   *nV_out = nV;
   if (mu == 0) { cleanup(); return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: the first selection is empty"); }
+  if (nV < nroots) {
+    cleanup();
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_roots: the space ends with %lld < nroots determinants",
+                    (long long)nV);
+  }
   if (nV > cap) {
     cleanup();
     return hci_fail(ctx, HCI_ERR_CAPACITY, "hci_solve_roots: %lld determinants exceed cap %lld", (long long)nV,

@@ -69,6 +69,20 @@ def test_solve_roots_matches_oracle(pkg):
     assert np.abs(out["E"] - ref["E"]).max() < 1e-9
 
 
+@pytest.mark.parametrize("eps1", [1.0, 0.7])
+def test_solve_roots_growing_from_fewer_determinants_than_roots(pkg, eps1):
+    """The first selection leaves 3 determinants for 4 roots: the loop
+    solves for the states V holds until it has grown (eps1 = 1.0 ends with
+    exactly 4 determinants, 0.7 with 11)."""
+    inst = hi.random_tiny(6, 3, 3, 91)
+    ref = oracle.hci_roots(inst, eps1, 4)
+    with solver(pkg, inst) as s:
+        out = s.solve_roots(4, eps1, dav_tol=1e-10)
+    got = {tuple(x) for x in host_keys(out["keys"]).tolist()}
+    assert got == {tuple(x) for x in np.asarray(ref["keys"]).tolist()}
+    assert np.abs(out["E"] - ref["E"]).max() < 1e-9
+
+
 def test_solve_roots_eps_zero_is_full_space(pkg):
     inst = hi.random_tiny(6, 3, 2, 93)
     w = np.linalg.eigvalsh(oracle.hamiltonian(inst, oracle.hci(inst, 0.0)["keys"]).toarray())
