@@ -50,3 +50,30 @@ def test_batch_reports_a_failing_instance(pkg):
     with pytest.raises(pkg.HCIError) as ei:
         pkg.hci_solve_batch(lst, 1e-4, nstreams=2)
     assert "instance 1" in str(ei.value)
+
+
+def test_batch_matches_oracle(pkg):
+    """Three instances of the uneven batch (norb 10, 17 and 24) solved
+    concurrently: energies within 1e-9 Ha, space sizes equal and RDMs within
+    1e-8 of the oracle's HCI (Sec. II.A) and RDMs (Sec. IV); the selected
+    sets of the same instances (single-instance solves, which the batch
+    reproduces above) equal the oracle's."""
+    import oracle
+
+    allb = hi.df_batch(64)
+    insts = [allb[0], allb[7], allb[59]]
+    assert [i.norb for i in insts] == [10, 17, 24]
+    lst = _lst(insts)
+    en, nv, r1, r2 = pkg.hci_solve_batch(lst, 1e-4, dav_tol=1e-10, nstreams=3, want_rdm=True)
+    for k, inst in enumerate(insts):
+        ref = oracle.hci(inst, 1e-4)
+        assert nv[k] == len(ref["keys"]), (k, nv[k], len(ref["keys"]))
+        assert abs(en[k] - ref["E"]) < 1e-9, (k, en[k], ref["E"])
+        w1, w2 = oracle.rdm12(inst.norb, ref["keys"], ref["c"])
+        assert np.abs(r1[k].cpu().numpy() - w1).max() < 1e-8
+        assert np.abs(r2[k].cpu().numpy() - w2).max() < 1e-8
+        n, na, nb, h, eri, ec = lst[k]
+        with pkg.HCISolver(n, na, nb, h, eri, ec) as s:
+            out = s.solve(1e-4, dav_tol=1e-10)
+        got = out["keys"].cpu().numpy().view(np.uint64).reshape(-1, 2)
+        assert np.array_equal(got, ref["keys"])

@@ -45,7 +45,7 @@ def solve(pkg, inst, eps1, kap):
     k = torch.tensor(kap).cuda()
     _, h2, e2 = pkg.hci_rotate(k, h, eri)
     s = pkg.HCISolver(inst.norb, inst.nalpha, inst.nbeta, h2, e2, inst.e_core)
-    out = s.solve(eps1, dav_tol=1e-9, cap=1 << 22)
+    out = s.solve(eps1, dav_tol=1e-10, cap=1 << 22)
     R, _ = oracle.rotate(inst, kap)
     return s, out, R, (h, eri, k)
 
