@@ -266,8 +266,22 @@ hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, in
                      uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV, double* energy,
                      int* iters);
 
-/* Many independent active spaces of uneven size (BASELINE batching
- * workload; the paper solves one space per orbital iteration, Sec. III): each
+/* The variational stage resumed from a saved state (checkpoint and resume of
+ * the selection loop of Sec. II.A: V^{mu+1} = V^mu + C^mu depends only on
+ * V^mu and c^mu): keys0 (device [nV0][2], strictly ascending) and c0
+ * (device [nV0], the state on that space, e.g. a step of an earlier solve
+ * written to disk) stand for V^mu, c^mu; the next selection is made from
+ * them as they are, then select / merge / Davidson as in hci_solve until the
+ * selection is empty or max_iter more selections.  When the first selection
+ * is already empty the state's energy comes from Davidson on (keys0, c0).
+ * Outputs as hci_solve; iters counts the selections made here.  Synchronises. */
+hci_status hci_solve_from(hci_ctx* ctx, const uint64_t* keys0, const double* c0, int64_t nV0, double eps1,
+                          int max_iter, double dav_tol, int dav_maxit, uint64_t* keys_out, double* c_out, int64_t cap,
+                          int64_t* nV, double* energy, int* iters);
+
+/* Many independent active spaces of uneven size (a batch of orbital
+ * iterations or of molecules; the paper solves one space per orbital
+ * iteration, Sec. III): each
  * instance k gets its own context and stream, `nstreams` host threads take
  * instances from a shared queue, so uneven instances overlap on the GPU.
  * Arrays of length count: norb, nalpha, nbeta, h[k] / eri[k] (device
@@ -286,6 +300,9 @@ hci_status hci_solve_batch(int count, const int* norb, const int* nalpha, const 
  * orbital parameters kappa; Sec. III.B): U = exp(kappa) for an n x n real
  * kappa (antisymmetric for an orthogonal U), h' = U^T h U,
  * (pq|rs)' = sum_abcd U_ap U_bq U_cr U_ds (ab|cd).
+ * The outputs are made exactly symmetric, as hci_create requires: every
+ * permutation of (pq|rs)' in its 8-fold orbit, and h'_qp, hold the bits of
+ * the orbit's representative (p <= q, r <= s, pq <= rs) and of h'_pq, p < q.
  * All pointers device; U, h_out, eri_out are outputs (n*n, n*n, n^4).
  * stream: cudaStream_t or NULL. */
 hci_status hci_rotate(int norb, const double* kappa, const double* h, const double* eri, double* U,
@@ -315,10 +332,13 @@ hci_status hci_rotate_backward(int norb, const double* kappa, const double* h, c
  * array of about 8 MiB that every GPU loading this library holds until the
  * process exits; norb above 32 is rejected with HCI_ERR_INVALID.
  * The first call on each device looks up the array's device address (with
- * that device current) and caches it, so make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller.  Synchronises the stream. */
+ * that device current) and caches it for the CUDA context that is current;
+ * a call made in another context (after a device reset, or from a context
+ * the caller created) looks the address up again.  Make the first call on a
+ * device, and the first after a reset, before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Synchronises the stream. */
 hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, const double* eri, double* U,
                               double* h_out, double* eri_out, void* stream);
 

@@ -30,7 +30,7 @@ EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hc
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
            "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12", "hci_davidson_roots",
-           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode", "hci_spin_square"]
+           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode", "hci_spin_square", "hci_solve_from"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -81,6 +81,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_solve_roots.argtypes = [V, I, D, I, D, I, V, V, I64, P(I64), V, P(I)]
     L.hci_relaxed_rdm12.argtypes = [V, D, V, V, I64, D, I64, D, I, P(D), V, V]
     L.hci_solve.argtypes = [V, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
+    L.hci_solve_from.argtypes = [V, V, V, I64, D, I, D, I, V, V, I64, P(I64), P(D), P(I)]
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
     L.hci_rotate_noalloc.argtypes = [I, V, V, V, V, V, V, V]
@@ -316,6 +317,33 @@ def hci_solve(ctx, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24,
         c = torch.empty(cap, dtype=torch.float64, device=device)
         st = L.hci_solve(ctx, float(eps1), int(max_iter), float(dav_tol), int(dav_maxit), _ptr(keys), _ptr(c), cap,
                          ctypes.byref(nv), ctypes.byref(e), ctypes.byref(it))
+    _check(st, ctx)
+    n = int(nv.value)
+    return keys[:n], c[:n], e.value, it.value
+
+
+def hci_solve_from(ctx, keys0, c0, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24):
+    """Variational stage resumed from (keys0, c0); returns (keys, c, E, iterations)."""
+    L = load()
+    keys0 = keys0.contiguous()
+    c0 = c0.to(torch.float64).contiguous()
+    nv = ctypes.c_int64(0)
+    e = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    cap = max(cap, keys0.shape[0])
+    dev = keys0.device
+
+    def run(cap):
+        keys = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+        c = torch.empty(cap, dtype=torch.float64, device=dev)
+        st = L.hci_solve_from(ctx, _ptr(keys0), _ptr(c0), keys0.shape[0], float(eps1), int(max_iter),
+                              float(dav_tol), int(dav_maxit), _ptr(keys), _ptr(c), cap, ctypes.byref(nv),
+                              ctypes.byref(e), ctypes.byref(it))
+        return st, keys, c
+
+    st, keys, c = run(cap)
+    if st == HCI_ERR_CAPACITY:
+        st, keys, c = run(int(nv.value))
     _check(st, ctx)
     n = int(nv.value)
     return keys[:n], c[:n], e.value, it.value

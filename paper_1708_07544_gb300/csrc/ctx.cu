@@ -1,11 +1,22 @@
 // Context lifetime, integral tables and the heat-bath excitation lists.
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 
 #include "hci_internal.cuh"
 
 static thread_local char g_create_err[512] = {0};
+
+int g_hci_nsm = 0;
+
+int64_t hci_fail_alloc_env() {
+  const char* v = getenv("HCI_FAIL_ALLOC_AFTER");
+  if (!v || !*v) return -1;
+  char* end = nullptr;
+  const long long k = strtoll(v, &end, 10);
+  return (end && *end == 0 && k >= 0) ? (int64_t)k : -1;
+}
 
 hci_status hci_fail(hci_ctx* ctx, hci_status code, const char* fmt, ...) {
   char* dst = ctx ? ctx->err : g_create_err;
@@ -18,6 +29,12 @@ hci_status hci_fail(hci_ctx* ctx, hci_status code, const char* fmt, ...) {
 
 hci_status ensure_buf(hci_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes <= b.bytes && b.p) return HCI_OK;
+  if (ctx->fail_alloc_after >= 0) {
+    if (ctx->fail_alloc_after == 0)
+      return hci_fail(ctx, HCI_ERR_NOMEM, "device allocation of %zu bytes refused (injected by HCI_FAIL_ALLOC_AFTER)",
+                      bytes);
+    --ctx->fail_alloc_after;
+  }
   if (b.p) {
     cudaFreeAsync(b.p, ctx->st);
     b.p = nullptr;
@@ -224,6 +241,18 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       uint64_t thr = ~0ull;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
+  ctx->fail_alloc_after = hci_fail_alloc_env();
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0) {
+      ctx->nsm = nsm;
+      g_hci_nsm = nsm;
+    } else {
+      ctx->nsm = hci_nsm();
     }
     cudaGetLastError();
   }

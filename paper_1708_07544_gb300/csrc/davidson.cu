@@ -411,7 +411,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   D.ctx = ctx;
   D.n = nV;
   D.ld = (nV + 31) & ~(int64_t)31;
-  D.nblk = grid_for(nV, DBLOCK, 152 * 8);
+  D.nblk = grid_for(nV, DBLOCK, ctx->nsm * 8);
   HCI_TRY(ensure_buf(ctx, ctx->d_vb, (size_t)D.ld * (MAXSUB + 3) * 8));
   HCI_TRY(ensure_buf(ctx, ctx->d_wb, (size_t)D.ld * MAXSUB * 8));
   HCI_TRY(ensure_buf(ctx, ctx->d_part, (size_t)(D.nblk + 1) * LDG * 8));

@@ -95,6 +95,8 @@ struct hci_ctx {
   int64_t graph_budget = 0;  // bytes the stored connection pool may take (0: device memory)
   bool direct_fallback = false;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
+  int nsm = 0;               // streaming multiprocessors of the context's device (grid sizes)
+  int64_t fail_alloc_after = -1;  // HCI_FAIL_ALLOC_AFTER: allocations left before one is refused (-1: off)
   int64_t last_candidates = 0;
   int64_t st_counts[HCI_ST_COUNT] = {};
   Prof prof;
@@ -136,7 +138,18 @@ void free_buf(cudaStream_t st, DevBuf& b);
 template <class T>
 inline T* bp(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
 
-inline int grid_for(int64_t work, int block, int max_blocks = 152 * 16) {
+// SM count of the device the last context was created on (152 on GB300);
+// grid-stride launches without a context size their grids from it.
+extern int g_hci_nsm;
+inline int hci_nsm() { return g_hci_nsm > 0 ? g_hci_nsm : 152; }
+
+// Host-side fault injection for tests: the value of the environment variable
+// HCI_FAIL_ALLOC_AFTER (k >= 0: the first k allocations succeed, every later
+// one is refused as if the device were out of memory), or -1 when unset.
+int64_t hci_fail_alloc_env();
+
+inline int grid_for(int64_t work, int block, int max_blocks = -1) {
+  if (max_blocks < 0) max_blocks = hci_nsm() * 16;
   int64_t g = (work + block - 1) / block;
   if (g < 1) g = 1;
   if (g > max_blocks) g = max_blocks;

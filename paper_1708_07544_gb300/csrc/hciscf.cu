@@ -223,7 +223,7 @@ extern "C" hci_status hci_relaxed_rdm12(hci_ctx* ctx, double eps2, const uint64_
   for (int p = 0; p < n; ++p) tr += t1[(size_t)p * n + p];
   const int N = ctx->na + ctx->nb;
   const double dd = N > 0 ? tr / N : 0.0;
-  HCI_LAUNCH(k_relaxed_combine, grid_for((int64_t)n4, ZB, 152 * 8), ZB, 0, st)(
+  HCI_LAUNCH(k_relaxed_combine, grid_for((int64_t)n4, ZB, ctx->nsm * 8), ZB, 0, st)(
       n, dd, g[4], g[5], g[0], g[1], g[2], g[3], g[6], g[7], g[8], g[9], rdm1, rdm2);
   HCI_CUDA(ctx, cudaGetLastError());
   HCI_CUDA(ctx, cudaStreamSynchronize(st));

@@ -255,7 +255,7 @@ hci_status hash_keys(hci_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t* ha
   unsigned long long* d = bp<unsigned long long>(ctx->s_counter);
   HCI_CUDA(ctx, cudaMemsetAsync(d, 0, 16, ctx->st));
   if (n > 0)
-    HCI_LAUNCH(k_hash, grid_for(n, 256, 152 * 8), 256, 0, ctx->st)(reinterpret_cast<const ulonglong2*>(keys), n, d);
+    HCI_LAUNCH(k_hash, grid_for(n, 256, ctx->nsm * 8), 256, 0, ctx->st)(reinterpret_cast<const ulonglong2*>(keys), n, d);
   unsigned long long hv[2];
   HCI_CUDA(ctx, cudaMemcpyAsync(hv, d, 16, cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
@@ -268,7 +268,7 @@ hci_status check_sorted(hci_ctx* ctx, const uint64_t* keys, int64_t n, int* ok_h
   int* d = reinterpret_cast<int*>(bp<char>(ctx->s_counter) + 32);
   HCI_CUDA(ctx, cudaMemsetAsync(d, 0, sizeof(int), ctx->st));
   if (n > 1)
-    HCI_LAUNCH(k_check_sorted, grid_for(n, 256, 152 * 8), 256, 0, ctx->st)(reinterpret_cast<const ulonglong2*>(keys), n, d);
+    HCI_LAUNCH(k_check_sorted, grid_for(n, 256, ctx->nsm * 8), 256, 0, ctx->st)(reinterpret_cast<const ulonglong2*>(keys), n, d);
   int bad = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&bad, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));

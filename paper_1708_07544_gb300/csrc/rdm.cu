@@ -431,11 +431,11 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   if (ctx->graph.direct)
     HCI_TRY(direct_rdm(ctx, ci, R));   // connections searched again, one orientation each
   else
-    HCI_LAUNCH(k_rdm_offdiag, 152 * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
+    HCI_LAUNCH(k_rdm_offdiag, ctx->nsm * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
                                                            bp<int64_t>(ctx->graph.rowptr),
                                                            bp<int64_t>(ctx->graph.rowstart),
                                                            bp<int32_t>(ctx->graph.col), R, queue);
-  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, rdm1, rdm2, 1);
+  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, ctx->nsm * 8), 256, 0, st)(n, R, rdm1, rdm2, 1);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
@@ -505,7 +505,7 @@ hci_status pt2_rdm_pairs(hci_ctx* ctx, const ulonglong2* V, const double* c, con
   HCI_LAUNCH(k_rdm_pairs, grid_for(m, 256), 256, 0, ctx->st)(n, V, c, tgt, src, d, m, R);
   const size_t sm = (size_t)(1 + mm + mm * mm) * 8;
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_dd_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  HCI_LAUNCH(k_dd_acc, grid_for(m, 256, 152 * 2), 256, sm, ctx->st)(n, tgt, d, m, R.ref_a, R.ref_b,
+  HCI_LAUNCH(k_dd_acc, grid_for(m, 256, ctx->nsm * 2), 256, sm, ctx->st)(n, tgt, d, m, R.ref_a, R.ref_b,
                                                                      bp<double>(ctx->p2_dd));
   HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
@@ -518,7 +518,7 @@ hci_status pt2_rdm_finish(hci_ctx* ctx, double* r1dd, double* r2dd, double* r1dc
   RdmAcc R = pt2_acc(ctx);
   HCI_CUDA(ctx, cudaMemsetAsync(r1dc, 0, n2 * 8, st));
   HCI_CUDA(ctx, cudaMemsetAsync(r2dc, 0, n4 * 8, st));
-  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, 152 * 8), 256, 0, st)(n, R, r1dc, r2dc, 0);
+  HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, ctx->nsm * 8), 256, 0, st)(n, R, r1dc, r2dc, 0);
   double* acc = bp<double>(ctx->p2_dd);
   double* M = acc + 1 + mm + mm * mm;
   HCI_LAUNCH(k_dd_matrix, grid_for((int64_t)mm * mm, 256), 256, 0, st)(n, acc, R.ref_a, R.ref_b, M);

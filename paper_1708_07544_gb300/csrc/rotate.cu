@@ -14,6 +14,9 @@
 //           exp at kappa^T, read off exp([[k^T, G], [0, k^T]]).
 // FP64 on CUDA cores: double-precision tensor throughput on this part is no
 // higher than the FP64 pipe, and the contraction is a small share of a solve.
+#include <cuda.h>
+
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -125,6 +128,32 @@ __global__ void __launch_bounds__(256) k_qtrans(int n, const double* __restrict_
   }
 }
 
+// The solver reads different permutations of one integral (heat-bath lists,
+// Slater-Condon rules), so every permutation must hold the same bits: each
+// element of the 8-fold orbit of (pq|rs) takes the value of the orbit's
+// representative ((a,b) = sorted (p,q), (c,d) = sorted (r,s), pairs ordered
+// so that (a,b) <= (c,d)), and h_pq = h_qp takes the value of h_min,max.  In
+// place: a representative is only ever rewritten with its own value.
+__global__ void k_sym8(int n, double* __restrict__ eri) {
+  const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(t % n), r = (int)((t / n) % n), q = (int)((t / n2) % n), p = (int)(t / (n2 * n));
+    int a = p < q ? p : q, b = p < q ? q : p, c = r < s ? r : s, d = r < s ? s : r;
+    if (a * n + b > c * n + d) {
+      const int ta = a, tb = b;
+      a = c; b = d; c = ta; d = tb;
+    }
+    const int64_t rep = (((int64_t)a * n + b) * n + c) * n + d;
+    if (rep != t) eri[t] = eri[rep];
+  }
+}
+__global__ void k_symh(int n, double* __restrict__ h) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int p = t / n, q = t % n;
+  if (p > q) h[t] = h[q * n + p];
+}
+
 // partial[b][x][y] = sum_{J in chunk b} A[x][J] B[y][J]  (A, B: n x K)
 constexpr int NT_CH = 64;
 __global__ void __launch_bounds__(256) k_gemm_nt_part(int n, int64_t K, const double* __restrict__ A,
@@ -161,8 +190,11 @@ struct Scratch {
   cudaStream_t st;
   void* ptrs[16];
   int count = 0;
+  int64_t left = hci_fail_alloc_env();   // host-side fault injection (tests)
   double* get(size_t doubles) {
     void* p = nullptr;
+    if (left == 0) return nullptr;
+    if (left > 0) --left;
     if (cudaMallocAsync(&p, doubles * 8 + 64, st) != cudaSuccess) return nullptr;
     ptrs[count++] = p;
     return reinterpret_cast<double*>(p);
@@ -212,6 +244,13 @@ void qtrans(cudaStream_t st, int n, const double* in, const double* M, double* o
   HCI_LAUNCH(k_qtrans, blocks(N3, QT_J), 256, smem, st)(n, in, M, out);
 }
 
+// exact permutational symmetry of the rotated integrals (see k_sym8)
+void symmetrize(cudaStream_t st, int n, double* h, double* eri) {
+  const int64_t n4 = (int64_t)n * n * n * n;
+  HCI_LAUNCH(k_symh, blocks((int64_t)n * n), 256, 0, st)(n, h);
+  HCI_LAUNCH(k_sym8, (unsigned)std::min<int64_t>(blocks(n4), 4096), 256, 0, st)(n, eri);
+}
+
 }  // namespace
 
 extern "C" hci_status hci_rotate(int norb, const double* kappa, const double* h, const double* eri, double* U,
@@ -224,7 +263,9 @@ extern "C" hci_status hci_rotate(int norb, const double* kappa, const double* h,
   Scratch S{st};
   const size_t n2 = (size_t)n * n, n4 = n2 * n2;
   double *w1 = S.get(n2), *w2 = S.get(n2), *w3 = S.get(n2), *ds = S.get(8), *t4 = S.get(n4);
-  if (!w1 || !w2 || !w3 || !ds || !t4) return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate: allocation failed");
+  if (!w1 || !w2 || !w3 || !ds || !t4)
+    return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate: allocation failed%s",
+                    S.left == 0 ? " (injected by HCI_FAIL_ALLOC_AFTER)" : "");
   cudaFuncSetAttribute(k_qtrans, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 * 64 + 64 * QT_J) * 8);
   hci_status s = expm_dev(st, n, kappa, U, w1, w2, w3, ds);
   if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate: matrix exponential failed");
@@ -234,6 +275,7 @@ extern "C" hci_status hci_rotate(int norb, const double* kappa, const double* h,
   qtrans(st, n, t4, U, eri_out);
   qtrans(st, n, eri_out, U, t4);
   qtrans(st, n, t4, U, eri_out);
+  symmetrize(st, n, h_out, eri_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate: %s", cudaGetErrorString(e));
   e = cudaStreamSynchronize(st);
@@ -258,7 +300,8 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
          *b4 = S.get((size_t)m2 * m2), *b5 = S.get((size_t)m2 * m2), *ds = S.get(8);
   double *D = S.get(n4), *t4 = S.get(n4);
   if (!U || !Ut || !I || !w1 || !gU || !b1 || !b2 || !b3 || !b4 || !b5 || !ds || !D || !t4)
-    return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed");
+    return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed%s",
+                    S.left == 0 ? " (injected by HCI_FAIL_ALLOC_AFTER)" : "");
   cudaFuncSetAttribute(k_qtrans, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 * 64 + 64 * QT_J) * 8);
   cudaFuncSetAttribute(k_gemm_nt_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * NT_CH * 8);
   hci_status s = expm_dev(st, n, kappa, U, w1, b1, b2, ds);
@@ -292,7 +335,9 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
     const int64_t K = (int64_t)n * n * n;
     const int nparts = (int)((K + NT_CH - 1) / NT_CH);
     double* part = S.get((size_t)nparts * n2);
-    if (!part) return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed");
+    if (!part)
+      return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed%s",
+                      S.left == 0 ? " (injected by HCI_FAIL_ALLOC_AFTER)" : "");
     HCI_LAUNCH(k_gemm_nt_part, nparts, 256, (size_t)2 * n * NT_CH * 8, st)(n, K, eri, D, part);
     HCI_LAUNCH(k_sum_parts, blocks((int64_t)n2), 256, 0, st)((int)n2, nparts, part, 4.0, gU);
     // dkappa = L_exp(kappa^T, gU)
@@ -331,12 +376,48 @@ constexpr size_t NOALLOC_DOUBLES = NOALLOC_T4 + 3 * NOALLOC_M + 32;   // 8.02 Mi
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
 constexpr int NOALLOC_MAXDEV = 64;
-static double* g_noalloc_ptr[NOALLOC_MAXDEV] = {};
+struct NoallocSlot {
+  unsigned long long ctx_id = 0;   // context the address was looked up in (0: none)
+  double* ptr = nullptr;
+};
+static NoallocSlot g_noalloc_slot[NOALLOC_MAXDEV];
 static std::mutex g_noalloc_mu;
 
-// Device address of the scratch array on the current device.  In host code
+// Identity of the calling thread's current CUDA context (a driver-assigned id
+// that is never reused), 0 when it cannot be read.  The driver entry points
+// are fetched through the runtime, so the library does not link libcuda.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(a);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(b);
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// with cudaGetSymbolAddress (with the device current) once per device and
+// context: the cached address is used again only while the same context is
+// current, so a device reset or another context gets its own look-up.
 hci_status noalloc_scratch(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -344,15 +425,19 @@ hci_status noalloc_scratch(double** out) {
   if (dev < 0 || dev >= NOALLOC_MAXDEV)
     return hci_fail(nullptr, HCI_ERR_INVALID, "hci_rotate_noalloc: device %d outside [0,%d)", dev, NOALLOC_MAXDEV);
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  NoallocSlot& slot = g_noalloc_slot[dev];
+  unsigned long long id = current_context_id();
+  if (!slot.ptr || id == 0 || slot.ctx_id != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: cudaGetSymbolAddress failed: %s",
                       cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = reinterpret_cast<double*>(p);
+    if (id == 0) id = current_context_id();   // the look-up made the primary context current
+    slot.ptr = reinterpret_cast<double*>(p);
+    slot.ctx_id = id;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = slot.ptr;
   return HCI_OK;
 }
 
@@ -387,6 +472,7 @@ extern "C" hci_status hci_rotate_noalloc(int norb, const double* kappa, const do
   qtrans(st, n, t4, U, eri_out);
   qtrans(st, n, eri_out, U, t4);
   qtrans(st, n, t4, U, eri_out);
+  symmetrize(st, n, h_out, eri_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: %s", cudaGetErrorString(e));
   e = cudaStreamSynchronize(st);

@@ -456,7 +456,7 @@ static hci_status run_walk(hci_ctx* ctx, WalkArgs& A, int64_t* total) {
   HCI_CUDA(ctx, cudaMemsetAsync(A.walkstat, 0, 16, ctx->st));
   prof_tic(ctx, HCI_PH_WALK);
   HCI_CUDA(ctx, cudaMemsetAsync(A.counter, 0, 16, ctx->st));
-  const int grid = 152 * 8;
+  const int grid = ctx->nsm * 8;
   const size_t smw = (size_t)(A.n * A.n + A.n * (A.n - 1) / 2) * 8 + HCI_MAXORB * (HCI_MAXORB - 1);
   HCI_CUDA(ctx, cudaFuncSetAttribute(k_walk_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -1114,12 +1114,12 @@ extern "C" hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, con
   int64_t* total = excl + nV;
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(total + 1);
   HCI_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
-  HCI_LAUNCH(k_abs_max, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx);
+  HCI_LAUNCH(k_abs_max, grid_for(nV, 256, ctx->nsm * 8), 256, 0, st)(c, nV, mx);
   // weight scale 2^B: 2^40, or less so that nV 2^B <= 2^62
   int lg = 0;
   while (((int64_t)1 << lg) < nV) ++lg;
   const int B = lg <= 22 ? 40 : 62 - lg;
-  HCI_LAUNCH(k_ss_weights, grid_for(nV, 256, 152 * 8), 256, 0, st)(c, nV, mx, B, W);
+  HCI_LAUNCH(k_ss_weights, grid_for(nV, 256, ctx->nsm * 8), 256, 0, st)(c, nV, mx, B, W);
   HCI_TRY(scan_i64(ctx, W, excl, nV, total));
   int64_t tot_h = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&tot_h, total, 8, cudaMemcpyDeviceToHost, st));
@@ -1134,7 +1134,7 @@ extern "C" hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, con
   HCI_TRY(ensure_buf(ctx, ctx->ss_draw, (size_t)m * 16));
   HCI_TRY(ensure_buf(ctx, ctx->ss_draw2, (size_t)m * 16));
   ulonglong2* dk = bp<ulonglong2>(ctx->ss_draw);
-  HCI_LAUNCH(k_ss_draw, grid_for(m, 256, 152 * 8), 256, 0, st)(excl, nV, total, seed, nd, m, dk, draws);
+  HCI_LAUNCH(k_ss_draw, grid_for(m, 256, ctx->nsm * 8), 256, 0, st)(excl, nV, total, seed, nd, m, dk, draws);
   int sbits = 1, ibits = 1;
   while (sbits < 32 && ((int64_t)1 << sbits) < n_samples) ++sbits;
   while (ibits < 32 && ((int64_t)1 << ibits) < nV) ++ibits;
@@ -1147,9 +1147,9 @@ extern "C" hci_status hci_pt2_stochastic(hci_ctx* ctx, const uint64_t* keys, con
   int32_t* d_s = d_idx + m;
   int64_t* seg = reinterpret_cast<int64_t*>(d_s + m);
   int64_t* ndist_dev = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 48);
-  HCI_LAUNCH(k_run_first, grid_for(m, 256, 152 * 8), 256, 0, st)(dk, m, flag);
+  HCI_LAUNCH(k_run_first, grid_for(m, 256, ctx->nsm * 8), 256, 0, st)(dk, m, flag);
   HCI_TRY(scan_i64(ctx, flag, pos, m, ndist_dev));
-  HCI_LAUNCH(k_ss_compact, grid_for(m, 256, 152 * 8), 256, 0, st)(dk, m, flag, pos, d_idx, d_s, d_start);
+  HCI_LAUNCH(k_ss_compact, grid_for(m, 256, ctx->nsm * 8), 256, 0, st)(dk, m, flag, pos, d_idx, d_s, d_start);
   int64_t ndist = 0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&ndist, ndist_dev, 8, cudaMemcpyDeviceToHost, st));
   HCI_CUDA(ctx, cudaStreamSynchronize(st));

@@ -32,9 +32,13 @@ __global__ void k_aufbau(int na, int nb, ulonglong2* keys, double* c) {
 }  // namespace
 
 // The whole loop; on success the final space and vector are left in
-// keys_res / c_res (owned by the caller, released with free_buf).
+// keys_res / c_res (owned by the caller, released with free_buf).  With
+// keys0 given the loop resumes from (keys0, c0): the first selection is made
+// from that state as it is, and its energy is only computed (by Davidson on
+// it) when that selection is empty.
 static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit, DevBuf& keys_res,
-                             DevBuf& c_res, int64_t* nV_out, double* energy, int* iters) {
+                             DevBuf& c_res, int64_t* nV_out, double* energy, int* iters,
+                             const uint64_t* keys0 = nullptr, const double* c0 = nullptr, int64_t nV0 = 0) {
   cudaStream_t st = ctx->st;
   HCI_TRY(hci_build_lists(ctx));
   DevBuf kb[2], cb[2], nk;
@@ -43,14 +47,28 @@ static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav
     free_buf(st, nk);
   };
   int cur = 0;
-  int64_t nV = 1;
+  int64_t nV = keys0 ? nV0 : 1;
   hci_status s;
-  if ((s = ensure_buf(ctx, kb[0], 16)) != HCI_OK || (s = ensure_buf(ctx, cb[0], 8)) != HCI_OK) { cleanup(); return s; }
-  HCI_LAUNCH(k_aufbau, 1, 1, 0, st)(ctx->na, ctx->nb, bp<ulonglong2>(kb[0]), bp<double>(cb[0]));
+  if ((s = ensure_buf(ctx, kb[0], (size_t)nV * 16)) != HCI_OK || (s = ensure_buf(ctx, cb[0], (size_t)nV * 8)) != HCI_OK) {
+    cleanup();
+    return s;
+  }
   double e = 0.0;
   int dav_it = 0;
-  s = hci_davidson(ctx, bp<uint64_t>(kb[0]), 1, bp<double>(cb[0]), &e, dav_tol, dav_maxit, &dav_it);
-  if (s != HCI_OK) { cleanup(); return s; }
+  bool have_e = false;
+  if (keys0) {
+    cudaError_t ce = cudaMemcpyAsync(kb[0].p, keys0, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(cb[0].p, c0, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st);
+    if (ce != cudaSuccess) {
+      cleanup();
+      return hci_fail(ctx, HCI_ERR_CUDA, "hci_solve_from: %s", cudaGetErrorString(ce));
+    }
+  } else {
+    HCI_LAUNCH(k_aufbau, 1, 1, 0, st)(ctx->na, ctx->nb, bp<ulonglong2>(kb[0]), bp<double>(cb[0]));
+    s = hci_davidson(ctx, bp<uint64_t>(kb[0]), 1, bp<double>(cb[0]), &e, dav_tol, dav_maxit, &dav_it);
+    if (s != HCI_OK) { cleanup(); return s; }
+    have_e = true;
+  }
   int mu = 0;
   for (; mu < max_iter; ++mu) {
     int64_t ncap = nk.bytes / 16;
@@ -63,6 +81,7 @@ static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav
     }
     if (s != HCI_OK) { cleanup(); return s; }
     if (nn == 0) break;
+    have_e = false;
     const int nxt = cur ^ 1;
     const int64_t nV2 = nV + nn;
     if ((s = ensure_buf(ctx, kb[nxt], (size_t)nV2 * 16)) != HCI_OK ||
@@ -77,6 +96,12 @@ static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav
     nV = nV2;
     s = hci_davidson(ctx, bp<uint64_t>(kb[cur]), nV, bp<double>(cb[cur]), &e, dav_tol, dav_maxit, &dav_it);
     if (s != HCI_OK) { cleanup(); return s; }
+    have_e = true;
+  }
+  if (!have_e) {
+    // resumed from a state whose space did not grow: its energy
+    s = hci_davidson(ctx, bp<uint64_t>(kb[cur]), nV, bp<double>(cb[cur]), &e, dav_tol, dav_maxit, &dav_it);
+    if (s != HCI_OK) { cleanup(); return s; }
   }
   if (iters) *iters = mu;
   *nV_out = nV;
@@ -87,26 +112,32 @@ static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav
   return HCI_OK;
 }
 
-extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit,
-                                uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out, double* energy,
-                                int* iters) {
-  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_solve: null context");
-  if (!nV_out || !energy) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve: null output scalar");
-  if (max_iter < 0 || dav_maxit < 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve: bad iteration limits");
+static hci_status solve_entry(const char* name, hci_ctx* ctx, double eps1, int max_iter, double dav_tol,
+                              int dav_maxit, uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out,
+                              double* energy, int* iters, const uint64_t* keys0, const double* c0, int64_t nV0) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "%s: null context", name);
+  if (!nV_out || !energy) return hci_fail(ctx, HCI_ERR_INVALID, "%s: null output scalar", name);
+  if (max_iter < 0 || dav_maxit < 1) return hci_fail(ctx, HCI_ERR_INVALID, "%s: bad iteration limits", name);
   *nV_out = 0;
   if (iters) *iters = 0;
   cudaStream_t st = ctx->st;
+  if (keys0) {
+    if (nV0 < 1 || !c0) return hci_fail(ctx, HCI_ERR_INVALID, "%s: empty start space or null start vector", name);
+    int ok = 0;
+    HCI_TRY(check_sorted(ctx, keys0, nV0, &ok));
+    if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "%s: start keys are not strictly ascending", name);
+  }
   DevBuf kr, cr;
   int64_t nV = 0;
   double e = 0.0;
-  hci_status s = solve_core(ctx, eps1, max_iter, dav_tol, dav_maxit, kr, cr, &nV, &e, iters);
+  hci_status s = solve_core(ctx, eps1, max_iter, dav_tol, dav_maxit, kr, cr, &nV, &e, iters, keys0, c0, nV0);
   if (s != HCI_OK) return s;
   *nV_out = nV;
   *energy = e;
   if (nV > cap) {
     free_buf(st, kr);
     free_buf(st, cr);
-    return hci_fail(ctx, HCI_ERR_CAPACITY, "hci_solve: %lld determinants exceed cap %lld", (long long)nV,
+    return hci_fail(ctx, HCI_ERR_CAPACITY, "%s: %lld determinants exceed cap %lld", name, (long long)nV,
                     (long long)cap);
   }
   cudaError_t ce = cudaSuccess;
@@ -115,8 +146,23 @@ extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double 
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   free_buf(st, kr);
   free_buf(st, cr);
-  if (ce != cudaSuccess) return hci_fail(ctx, HCI_ERR_CUDA, "hci_solve: %s", cudaGetErrorString(ce));
+  if (ce != cudaSuccess) return hci_fail(ctx, HCI_ERR_CUDA, "%s: %s", name, cudaGetErrorString(ce));
   return HCI_OK;
+}
+
+extern "C" hci_status hci_solve(hci_ctx* ctx, double eps1, int max_iter, double dav_tol, int dav_maxit,
+                                uint64_t* keys_out, double* c_out, int64_t cap, int64_t* nV_out, double* energy,
+                                int* iters) {
+  return solve_entry("hci_solve", ctx, eps1, max_iter, dav_tol, dav_maxit, keys_out, c_out, cap, nV_out, energy, iters,
+                     nullptr, nullptr, 0);
+}
+
+extern "C" hci_status hci_solve_from(hci_ctx* ctx, const uint64_t* keys0, const double* c0, int64_t nV0, double eps1,
+                                     int max_iter, double dav_tol, int dav_maxit, uint64_t* keys_out, double* c_out,
+                                     int64_t cap, int64_t* nV_out, double* energy, int* iters) {
+  if (!keys0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_solve_from: null start keys");
+  return solve_entry("hci_solve_from", ctx, eps1, max_iter, dav_tol, dav_maxit, keys_out, c_out, cap, nV_out, energy,
+                     iters, keys0, c0, nV0);
 }
 
 // Variational HCI for the nroots lowest states (Sec. II.A with the

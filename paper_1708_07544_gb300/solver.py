@@ -87,6 +87,11 @@ class HCISolver:
         keys, c, e, it = _abi.hci_solve(self.ctx, eps1, max_iter, dav_tol, dav_maxit, cap)
         return {"keys": keys, "c": c, "E": e, "iters": it}
 
+    def solve_from(self, keys, c, eps1, max_iter=30, dav_tol=1e-10, dav_maxit=400, cap=1 << 24):
+        """The selection loop resumed from a saved state (keys, c)."""
+        keys, c, e, it = _abi.hci_solve_from(self.ctx, keys, c, eps1, max_iter, dav_tol, dav_maxit, cap)
+        return {"keys": keys, "c": c, "E": e, "iters": it}
+
     def stats(self):
         return _abi.hci_stats(self.ctx)
 

@@ -77,3 +77,17 @@ def test_binding_constants_match_header():
         assert ev["HCI_PH_" + name.upper()] == i, name
     for name in ["INVALID", "CAPACITY", "NOT_CONVERGED", "CUDA", "NOMEM"]:
         assert ev["HCI_ERR_" + name] == getattr(_abi, "HCI_ERR_" + name), name
+
+
+def test_create_reports_injected_allocation_failure_without_gpu(lib, monkeypatch):
+    """HCI_FAIL_ALLOC_AFTER=0 refuses the context's first device allocation
+    on the host, before any device call: hci_create returns HCI_ERR_NOMEM
+    with a message that names the injection (no GPU needed)."""
+    import ctypes
+
+    monkeypatch.setenv("HCI_FAIL_ALLOC_AFTER", "0")
+    out = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)          # never dereferenced: the refusal comes first
+    assert lib.hci_create(ctypes.byref(out), 8, 4, 4, dummy, dummy, 0.0, None) == 5
+    assert b"injected" in lib.hci_last_error(None)
+    assert out.value is None
