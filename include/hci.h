@@ -148,18 +148,25 @@ hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double
 
 /* How sigma and the RDMs get the connections of V (Sec. IV builds them by
  * generating every single and double between pairs of V):
- *   HCI_SIGMA_STORED: stored once per space (pooled CSR, int32 column +
- *     FP64 element, ~12 bytes per connection with per-row slack) and
- *     streamed by every H c; extended in place when V grows.
+ *   HCI_SIGMA_STORED: stored once per space with both orientations of every
+ *     connected pair (pooled CSR, int32 column + FP64 element, 12 bytes per
+ *     ordered pair plus per-row slack), streamed by every H c as a pure
+ *     gather; extended in place when V grows.
+ *   HCI_SIGMA_HALF: stored with one orientation per pair (in the row of the
+ *     later-inserted determinant; 12 bytes per pair, no slack: half the
+ *     memory); every H c adds each entry to both of its rows, the second by
+ *     an FP64 atomic add, so sums are taken in a run-dependent order; V's
+ *     growth only appends rows.
  *   HCI_SIGMA_DIRECT: nothing stored; every H c and RDM pass searches the
  *     connections of each row again and evaluates their elements (a few
  *     hundred MB of search structures instead of ~12 bytes per connection,
  *     for spaces whose connections exceed device memory).
- *   HCI_SIGMA_AUTO (default): stored while the pool fits graph_budget bytes
- *     (0: device memory), else direct for the rest of the context's life.
+ *   HCI_SIGMA_AUTO (default): both orientations while the pool fits
+ *     graph_budget bytes (0: device memory), else one orientation while that
+ *     fits, else direct, each fallback for the rest of the context's life.
  * Results agree to rounding order.  Invalidates the cached graph.
  * HCI_ERR_INVALID for an unknown mode or a negative budget. */
-enum { HCI_SIGMA_AUTO = 0, HCI_SIGMA_STORED = 1, HCI_SIGMA_DIRECT = 2 };
+enum { HCI_SIGMA_AUTO = 0, HCI_SIGMA_STORED = 1, HCI_SIGMA_DIRECT = 2, HCI_SIGMA_HALF = 3 };
 hci_status hci_set_sigma_mode(hci_ctx* ctx, int mode, int64_t graph_budget);
 
 /* Semistochastic second-order correction (Sec. II.B, Eq. semistoc):
@@ -360,12 +367,14 @@ hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, co
  *   HCI_ST_ROWS_REFILLED    new graph rows too long for the one-pass search,
  *                           filled by a second search
  *   HCI_ST_SIGMA_DIRECT     1 when the cached graph is direct (connections
- *                           searched again by every traversal), else 0 */
+ *                           searched again by every traversal), else 0
+ *   HCI_ST_GRAPH_HALF       1 when the cached graph stores one orientation
+ *                           of each pair, else 0 */
 enum {
   HCI_ST_GRAPH_NNZ = 0, HCI_ST_LAST_CANDIDATES = 1, HCI_ST_SIGMA_CALLS = 2, HCI_ST_SIGMA_ROWS = 3,
   HCI_ST_SIGMA_NNZ = 4, HCI_ST_SELECT_CALLS = 5, HCI_ST_SELECT_SOURCES = 6, HCI_ST_CANDIDATES = 7,
   HCI_ST_GRAPH_BUILDS = 8, HCI_ST_WALK_ENTRIES = 9, HCI_ST_SINGLES_EXACT = 10, HCI_ST_ROWS_REFILLED = 11,
-  HCI_ST_SIGMA_DIRECT = 12, HCI_ST_COUNT = 13
+  HCI_ST_SIGMA_DIRECT = 12, HCI_ST_GRAPH_HALF = 13, HCI_ST_COUNT = 14
 };
 hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout);
 

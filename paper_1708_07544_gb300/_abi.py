@@ -35,8 +35,8 @@ PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm"
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
          "select_sources", "candidates", "graph_builds", "walk_entries", "singles_exact", "rows_refilled",
-         "sigma_direct"]
-SIGMA_AUTO, SIGMA_STORED, SIGMA_DIRECT = 0, 1, 2
+         "sigma_direct", "graph_half"]
+SIGMA_AUTO, SIGMA_STORED, SIGMA_DIRECT, SIGMA_HALF = 0, 1, 2, 3
 
 
 class HCIError(RuntimeError):

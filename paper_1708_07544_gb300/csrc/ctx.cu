@@ -302,7 +302,7 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->h, &ctx->eri, &ctx->jk_same, &ctx->j_opp, &ctx->lists.opp_mag, &ctx->lists.opp_tgt,
                     &ctx->lists.list_max, &ctx->lists.f_ref, &ctx->s_items,
                     &ctx->lists.same_mag, &ctx->lists.same_tgt, &ctx->lists.single_bound,
-                    &ctx->graph.rowptr, &ctx->graph.col, &ctx->graph.val, &ctx->graph.diag, &ctx->graph.keys,
+                    &ctx->graph.rowptr, &ctx->graph.rowstart, &ctx->graph.diag, &ctx->graph.keys,
                     &ctx->s_cand, &ctx->s_cand2, &ctx->s_flags, &ctx->s_scan, &ctx->s_misc, &ctx->s_counter,
                     &ctx->s_hist, &ctx->g_ua, &ctx->g_ga, &ctx->g_ia, &ctx->g_ub, &ctx->g_gb, &ctx->g_ib,
                     &ctx->g_permb, &ctx->g_bkeys, &ctx->g_bkeys2, &ctx->g_nbr_ptr, &ctx->g_nbr, &ctx->g_cnt,
@@ -310,17 +310,21 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->g_bnbr_ptr, &ctx->g_bnbr, &ctx->g_costa, &ctx->g_costb, &ctx->s_walkstat,
                     &ctx->g_htab, &ctx->g_hval, &ctx->s_rdmw, &ctx->g_posb, &ctx->g_vb, &ctx->g_ba,
                     &ctx->inc.pos_old, &ctx->inc.mark, &ctx->inc.flag, &ctx->inc.newrows, &ctx->inc.rpN,
-                    &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.cnt, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T,
-                    &ctx->inc.T2, &ctx->inc.tstart, &ctx->inc.len, &ctx->inc.keys_old, &ctx->inc.rp_old,
-                    &ctx->inc.col_old, &ctx->inc.val_old, &ctx->inc.len_old, &ctx->inc.cap_old,
-                    &ctx->inc.diag_old, &ctx->graph.rowstart, &ctx->graph.rowlen, &ctx->graph.rowcap,
-                    &ctx->graph.keys_int, &ctx->graph.s2i, &ctx->graph.i2s, &ctx->inc.s2i_old,
-                    &ctx->inc.keys_int_old, &ctx->d_perm, &ctx->s_rdmh, &ctx->inc.scr, &ctx->inc.stage,
+                    &ctx->inc.cnt, &ctx->inc.keys_old, &ctx->inc.s2i_old, &ctx->inc.grow,
+                    &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T, &ctx->inc.T2,
+                    &ctx->inc.tstart, &ctx->inc.len, &ctx->inc.rp_old, &ctx->inc.col_old, &ctx->inc.val_old,
+                    &ctx->inc.len_old, &ctx->inc.cap_old, &ctx->graph.rowlen, &ctx->graph.rowcap,
+                    &ctx->graph.keys_int, &ctx->graph.s2i, &ctx->graph.i2s,
+                    &ctx->d_perm, &ctx->s_rdmh, &ctx->inc.scr, &ctx->inc.stage,
                     &ctx->inc.roff, &ctx->inc.ctl, &ctx->inc.left, &ctx->inc.samp,
                     &ctx->p2_vals, &ctx->p2_vals2, &ctx->p2_ref,
                     &ctx->p2_src, &ctx->p2_src2, &ctx->p2_d, &ctx->p2_dd,
                     &ctx->d_zv, &ctx->d_rel, &ctx->d_lock, &ctx->ss_w, &ctx->ss_draw,
                     &ctx->ss_draw2, &ctx->ss_run, &ctx->ss_src};
+  for (int k = 0; k < GRAPH_MAXSEG; ++k) {
+    free_buf(st, ctx->graph.seg_col[k]);
+    free_buf(st, ctx->graph.seg_val[k]);
+  }
   for (DevBuf* b : bufs) free_buf(st, *b);
   prof_release(ctx);
   cudaStreamSynchronize(st);
@@ -388,12 +392,13 @@ extern "C" hci_status hci_build_lists(hci_ctx* ctx) {
 
 extern "C" hci_status hci_set_sigma_mode(hci_ctx* ctx, int mode, int64_t graph_budget) {
   if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_set_sigma_mode: null context");
-  if (mode != HCI_SIGMA_AUTO && mode != HCI_SIGMA_STORED && mode != HCI_SIGMA_DIRECT)
+  if (mode != HCI_SIGMA_AUTO && mode != HCI_SIGMA_STORED && mode != HCI_SIGMA_DIRECT && mode != HCI_SIGMA_HALF)
     return hci_fail(ctx, HCI_ERR_INVALID, "hci_set_sigma_mode: unknown mode %d", mode);
   if (graph_budget < 0) return hci_fail(ctx, HCI_ERR_INVALID, "hci_set_sigma_mode: negative budget");
   ctx->sigma_mode = mode;
   ctx->graph_budget = graph_budget;
   ctx->direct_fallback = false;
+  ctx->half_fallback = false;
   ctx->graph.valid = false;
   return HCI_OK;
 }
@@ -406,6 +411,7 @@ extern "C" hci_status hci_stats(const hci_ctx* ctx, int64_t* out, int nout) {
   v[HCI_ST_GRAPH_NNZ] = ctx->graph.valid && ctx->graph.nnz > 0 ? ctx->graph.nnz : 0;
   v[HCI_ST_LAST_CANDIDATES] = ctx->last_candidates;
   v[HCI_ST_SIGMA_DIRECT] = ctx->graph.valid && ctx->graph.direct ? 1 : 0;
+  v[HCI_ST_GRAPH_HALF] = ctx->graph.valid && !ctx->graph.direct && ctx->graph.half ? 1 : 0;
   for (int k = 0; k < nout && k < HCI_ST_COUNT; ++k) out[k] = v[k];
   for (int k = HCI_ST_COUNT; k < nout; ++k) out[k] = 0;
   return HCI_OK;

@@ -10,8 +10,16 @@
 //   (B) same beta string, alpha differs by 1 or 2 electrons;
 //   (C) alpha differs by a single (via the single-excitation neighbours of
 //       each distinct alpha string) and beta differs by a single.
-// The three sets are disjoint.  Rows are filled in scan order, so the CSR
-// layout (and the sigma summation order) is deterministic.
+// The three sets are disjoint.  Two stored forms (hci_set_sigma_mode):
+//   both orientations: every row holds all of its connections in a row pool
+//     with slack (12 B per ordered pair); H c is a pure gather over the
+//     rows, and growing the space appends the new rows' transposes to the
+//     old rows in place;
+//   one orientation: each connected pair is stored once, in the row of the
+//     determinant with the larger internal id (ids are insertion order), in
+//     one segment per build or extension (half the memory; growing the
+//     space only appends rows), and H c adds each entry to both of its rows
+//     (a row sum plus an FP64 atomic scatter into the other row).
 #include <algorithm>
 #include <vector>
 
@@ -21,7 +29,8 @@
 namespace {
 
 constexpr int G_WARPS = 8;
-constexpr int ROWS_GRID = 152 * 6;   // blocks of the row search (all resident at 40 registers)
+// blocks of the row search: six per SM, all resident at 40 registers
+inline int rows_grid(const hci_ctx* ctx) { return ctx->nsm * 6; }
 constexpr int64_t ROW_SCR = 32768;   // scratch entries per warp of the staged row search
 constexpr int64_t ROW_SAMPLE = 2048; // rows counted to size the staging buffer
 
@@ -244,6 +253,7 @@ struct GraphArgs {
   int64_t* rowoff;
   unsigned long long* stage_ctl;  // [0] next free staging entry, [1] rows left to the fill pass
   const int32_t* s2i;      // sorted position -> internal id (columns are stored as internal ids)
+  int lower;               // one-orientation form: a row keeps the connections with a smaller id
   unsigned long long* queue;
   HamView H;
   // direct traversals (no stored rows), vectors by sorted position
@@ -262,14 +272,17 @@ __device__ __forceinline__ bool use_lookup(int64_t m, int L) {
 
 // Row search modes: count only, fill at a known offset, or staged fill
 // (into the warp's scratch, capped at scr_cap entries, still counting past it).
-// Direct traversals evaluate each connection as it is found: ROWS_SIGMA adds
-// H_ij c_j into the row's sum, ROWS_RDM accumulates <D_i| op |D_j> c_i c_j
-// for j > i (the other orientation is added as the transpose).
+// With A.lower these three keep only the connections j whose internal id is
+// below the row's (the one-orientation form).  Direct traversals evaluate
+// every connection as it is found: ROWS_SIGMA adds H_ij c_j into the row's
+// sum, ROWS_RDM accumulates <D_i| op |D_j> c_i c_j for j > i (the other
+// orientation is added as the transpose).
 constexpr int ROWS_COUNT = 0, ROWS_FILL = 1, ROWS_STAGED = 2, ROWS_SIGMA = 3, ROWS_RDM = 4;
 
-// per-row state of the direct traversals: row (sorted position), c_i, partial sum
+// per-row state: row (sorted position), its internal id, c_i, partial sum
 struct RowAcc {
   int64_t i;
+  int32_t id;
   double ci;
   double acc;
 };
@@ -278,10 +291,17 @@ template <int MODE>
 __device__ __forceinline__ void visit(const GraphArgs& A, ulonglong2 ki, int64_t j, bool ok, int64_t& w,
                                       int32_t* out, RowAcc& ra) {
   const int lane = threadIdx.x & 31;
+  int32_t id = 0;
+  if (MODE == ROWS_COUNT || MODE == ROWS_FILL || MODE == ROWS_STAGED) {
+    if (ok && (A.lower || MODE != ROWS_COUNT)) {
+      id = A.s2i[j];
+      if (A.lower) ok = id < ra.id;
+    }
+  }
   unsigned m = __ballot_sync(0xffffffffu, ok);
   if ((MODE == ROWS_FILL || MODE == ROWS_STAGED) && ok) {
     int64_t pos = w + __popc(m & ((1u << lane) - 1u));
-    if (MODE == ROWS_FILL || pos < A.scr_cap) out[pos] = A.s2i[j];
+    if (MODE == ROWS_FILL || pos < A.scr_cap) out[pos] = id;
   }
   if (MODE == ROWS_SIGMA && ok) ra.acc = fma(connection_el(A.H, ki, A.V[j]), A.dc[j], ra.acc);
   if (MODE == ROWS_RDM && ok && j > ra.i) {
@@ -422,7 +442,7 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
     int32_t* out = MODE == ROWS_FILL ? A.col
                    : MODE == ROWS_STAGED ? A.scr + (int64_t)(blockIdx.x * G_WARPS + wid) * A.scr_cap
                                          : nullptr;
-    RowAcc ra{i, (MODE == ROWS_SIGMA || MODE == ROWS_RDM) ? A.dc[i] : 0.0, 0.0};
+    RowAcc ra{i, A.s2i[i], (MODE == ROWS_SIGMA || MODE == ROWS_RDM) ? A.dc[i] : 0.0, 0.0};
     // (A) same alpha string
     {
       const int g = A.ia[i];
@@ -460,10 +480,10 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_rows(GraphArgs A) {
           const int d = __popcll(ki.x ^ x2);
           ok2 = d == 2 || d == 4;
         }
-        const int64_t j = (MODE != ROWS_COUNT && ok) ? (int64_t)A.permb[k] : -1;
+        const int64_t j = ok ? (int64_t)A.permb[k] : -1;
         visit<MODE>(A, ki, j, ok, w, out, ra);
         if (k0 + 32 < e) {
-          const int64_t j2 = (MODE != ROWS_COUNT && ok2) ? (int64_t)A.permb[k2] : -1;
+          const int64_t j2 = ok2 ? (int64_t)A.permb[k2] : -1;
           visit<MODE>(A, ki, j2, ok2, w, out, ra);
         }
       }
@@ -657,6 +677,19 @@ __global__ void k_compact_idx(const int64_t* __restrict__ flag, const int64_t* _
                               int32_t* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (flag[i]) out[pos[i]] = (int32_t)i;
+}
+
+// rows of V' appended after the nold rows already stored: row nold + q has
+// rp[q+1] - rp[q] entries starting at offset rp[q] of segment seg, and the
+// prefix continues from base (rp[nrows] = the segment's size); with
+// nold = 0, base = 0 and rp = rowptr this writes the table of a fresh graph
+__global__ void k_append_rows(int64_t nold, int64_t nrows, const int64_t* rp, int64_t base, int seg,
+                              int64_t* rowptr, int64_t* __restrict__ rowstart) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q <= nrows; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = rp[q];
+    rowptr[nold + q] = base + o;
+    if (q < nrows) rowstart[nold + q] = ((int64_t)seg << GRAPH_SEG_SHIFT) | o;
+  }
 }
 
 // per new row: number of entries whose column is an old determinant; also
@@ -895,7 +928,7 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
   }
 }
 
-// sigma = diag .* c + offdiag * c ; one warp per row.  In the single-vector
+// Both-orientation form: sigma = diag .* c + offdiag * c ; one warp per row.  In the single-vector
 // path each warp owns a contiguous range of rows holding an equal share of
 // the connections and keeps four (col, val, c[col]) loads per lane in
 // flight; the CSR stream is read with evict-first hints so that c stays in
@@ -994,6 +1027,127 @@ __global__ void __launch_bounds__(256) k_sigma(const int64_t* __restrict__ rowpt
         double a = lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3];
         const int64_t o = (int64_t)(v0 + lane) * nV + i;
         sigma[o] = fma(diag[i], c[o], a);
+      }
+    }
+  }
+}
+
+// The stored half of row i: its entries' columns and values.
+__device__ __forceinline__ void row_entries(const SegTab& T, int64_t rs, const int32_t*& col, const double*& val) {
+  const int sg = (int)(rs >> GRAPH_SEG_SHIFT);
+  const int64_t o = rs & GRAPH_SEG_MASK;
+  col = T.col[sg] + o;
+  val = T.val[sg] + o;
+}
+
+// One-orientation form: sigma = diag .* c + H_off c.  Each stored entry (i, j, v), j < i, adds
+// v c_j to sigma_i (the row sum) and v c_i to sigma_j (an FP64 atomic add
+// into sigma, which stays in L2); sigma is zeroed before the launch and each
+// row's sum is added atomically too, since other rows scatter into it at the
+// same time.  One warp per contiguous range of rows holding an equal share
+// of the entries, four (col, val, c[col]) loads per lane in flight, the entry
+// stream read with evict-first hints so that c and sigma stay in L2.  A
+// stored row holds ~10^3 entries on the full-size spaces, so its cross-lane
+// reduction (5 FP64 additions) is a small share of the 2 FP64 operations per
+// entry that bound the kernel (2 DFMA per clock per SM).
+// blocks of k_sigma1_half per SM: all resident (64 registers, no spills), so
+// the equal shares of the entries run in one wave
+constexpr int SIGMA_HALF_BLOCKS_PER_SM = 4;
+
+__global__ void __launch_bounds__(256, SIGMA_HALF_BLOCKS_PER_SM) k_sigma1_half(const int64_t* __restrict__ rowptr,
+                                                  const int64_t* __restrict__ rowstart, const __grid_constant__ SegTab T,
+                                                  const double* __restrict__ diag, int64_t nV,
+                                                  const double* __restrict__ c, double* sigma) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // contiguous row ranges holding an equal share of the entries
+  const int64_t tot = rowptr[nV];
+  const int64_t chunk = (tot + nwarps - 1) / nwarps;
+  int64_t r0, r1;
+  {
+    int64_t lo = 0, hi = nV, x = warp * chunk;
+    while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (rowptr[mid] < x) lo = mid + 1; else hi = mid; }
+    r0 = lo;
+    lo = r0; hi = nV; x = (warp + 1) * chunk;
+    while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (rowptr[mid] < x) lo = mid + 1; else hi = mid; }
+    r1 = warp == nwarps - 1 ? nV : lo;
+  }
+  for (int64_t i = r0; i < r1; ++i) {
+    const int64_t len = rowptr[i + 1] - rowptr[i];
+    const int32_t* col;
+    const double* val;
+    row_entries(T, rowstart[i], col, val);
+    const double ci = c[i];
+    double a = 0.0;
+    int64_t k = lane;
+    for (; k + 96 < len; k += 128) {
+      const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
+                    j3 = __ldcs(col + k + 96);
+      const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
+                   v3 = __ldcs(val + k + 96);
+      const double c0 = c[j0], c1 = c[j1], c2 = c[j2], c3 = c[j3];
+      atomicAdd(sigma + j0, v0 * ci);
+      atomicAdd(sigma + j1, v1 * ci);
+      atomicAdd(sigma + j2, v2 * ci);
+      atomicAdd(sigma + j3, v3 * ci);
+      a = fma(v0, c0, a);
+      a = fma(v1, c1, a);
+      a = fma(v2, c2, a);
+      a = fma(v3, c3, a);
+    }
+    for (; k < len; k += 32) {
+      const int32_t j = __ldcs(col + k);
+      const double v = __ldcs(val + k);
+      atomicAdd(sigma + j, v * ci);
+      a = fma(v, c[j], a);
+    }
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) atomicAdd(sigma + i, fma(diag[i], ci, a));
+  }
+}
+
+// several vectors at once (one pass over the entries per 4 vectors); sigma
+// zeroed before the launch, as for k_sigma1
+__global__ void __launch_bounds__(256) k_sigma_half(const int64_t* __restrict__ rowptr,
+                                               const int64_t* __restrict__ rowstart, const __grid_constant__ SegTab T,
+                                               const double* __restrict__ diag, int64_t nV,
+                                               const double* __restrict__ c, double* sigma, int nvec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < nV; i += nwarps) {
+    const int64_t len = rowptr[i + 1] - rowptr[i];
+    const int32_t* col;
+    const double* val;
+    row_entries(T, rowstart[i], col, val);
+    for (int v0 = 0; v0 < nvec; v0 += 4) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      double cin[4] = {0.0, 0.0, 0.0, 0.0};
+      const int nv = nvec - v0 < 4 ? nvec - v0 : 4;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nv) cin[t] = c[(int64_t)(v0 + t) * nV + i];
+      for (int64_t k = lane; k < len; k += 32) {
+        const int64_t j = col[k];
+        const double hv = val[k];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nv) {
+            acc[t] = fma(hv, c[(int64_t)(v0 + t) * nV + j], acc[t]);
+            atomicAdd(sigma + (int64_t)(v0 + t) * nV + j, hv * cin[t]);
+          }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        double a = acc[t];
+        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        acc[t] = a;
+      }
+      if (lane < nv) {
+        double a = lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3];
+        const int64_t o = (int64_t)(v0 + lane) * nV + i;
+        atomicAdd(sigma + o, fma(diag[i], c[o], a));
       }
     }
   }
@@ -1127,6 +1281,7 @@ static void space_args(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr; A.rowcnt = nullptr;
   A.scr = nullptr; A.scr_cap = 0; A.stage = nullptr; A.stage_cap = 0; A.rowoff = nullptr; A.stage_ctl = nullptr;
   A.s2i = bp<int32_t>(ctx->graph.s2i);
+  A.lower = 0;
   A.dc = nullptr; A.dsig = nullptr; A.ddiag = nullptr; A.dnnz = nullptr;
 }
 
@@ -1136,7 +1291,7 @@ static hci_status rows_count(hci_ctx* ctx, GraphArgs& A, DevBuf& cnt) {
   A.rowcnt = bp<int64_t>(cnt);
   A.rowptr = nullptr; A.col = nullptr; A.val = nullptr;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<ROWS_COUNT>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_LAUNCH(k_rows<ROWS_COUNT>, rows_grid(ctx), G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   A.rowcnt = nullptr;
   return HCI_OK;
@@ -1146,7 +1301,7 @@ static hci_status rows_count(hci_ctx* ctx, GraphArgs& A, DevBuf& cnt) {
 static hci_status rows_fill(hci_ctx* ctx, GraphArgs& A, const int64_t* offs, int32_t* col, double* val) {
   A.rowptr = offs; A.col = col; A.val = val;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<ROWS_FILL>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_LAUNCH(k_rows<ROWS_FILL>, rows_grid(ctx), G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
 }
@@ -1160,19 +1315,19 @@ static int64_t read_i64(hci_ctx* ctx, const int64_t* d, hci_status* st) {
   return v;
 }
 
-// The rows listed in A (rowlist, nrows; a list is required) searched once:
-// counts into inc.cnt, the CSR offsets into inc.rpN and the columns into
-// inc.colN (inc.valN sized to match).  Rows longer than ROW_SCR, or beyond
-// the staging space (sized from est entries), are filled by a second search
-// at their offsets.  *nnz = entries of the listed rows.
-static hci_status rows_staged(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* nnz) {
+// The rows listed in A (rowlist, nrows; a list is required) searched once
+// into per-warp scratch and a staging buffer (sized from est entries):
+// counts into inc.cnt, their prefix sums into inc.rpN (inc.rpN[nrows] =
+// *total), rows that outgrew the scratch or the staging space marked for a
+// second search (*left of them).
+static hci_status stage_search(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* total, int64_t* left) {
   IncScratch& S = ctx->inc;
   cudaStream_t st = ctx->st;
   const int64_t nrows = A.nrows;
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
   HCI_TRY(ensure_buf(ctx, S.cnt, (size_t)(nrows + 1) * 8));
   HCI_TRY(ensure_buf(ctx, S.roff, (size_t)(nrows + 1) * 8));
-  HCI_TRY(ensure_buf(ctx, S.scr, (size_t)ROWS_GRID * G_WARPS * ROW_SCR * 4));
+  HCI_TRY(ensure_buf(ctx, S.scr, (size_t)rows_grid(ctx) * G_WARPS * ROW_SCR * 4));
   if (S.stage.bytes < (size_t)est * 4) HCI_TRY(ensure_buf(ctx, S.stage, (size_t)est * 4));
   HCI_TRY(ensure_buf(ctx, S.ctl, 32));
   HCI_CUDA(ctx, cudaMemsetAsync(S.ctl.p, 0, 32, st));
@@ -1185,7 +1340,7 @@ static hci_status rows_staged(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* 
   A.rowoff = bp<int64_t>(S.roff);
   A.stage_ctl = ctl;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, st));
-  HCI_LAUNCH(k_rows<ROWS_STAGED>, ROWS_GRID, G_WARPS * 32, 0, st)(A);
+  HCI_LAUNCH(k_rows<ROWS_STAGED>, rows_grid(ctx), G_WARPS * 32, 0, st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   A.rowcnt = nullptr; A.scr = nullptr; A.scr_cap = 0; A.stage = nullptr; A.stage_cap = 0; A.rowoff = nullptr;
   A.stage_ctl = nullptr;
@@ -1193,17 +1348,25 @@ static hci_status rows_staged(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* 
   HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.rpN), nrows, dtot));
   HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(S.rpN), nrows, dtot);
   hci_status hs = HCI_OK;
-  const int64_t total = read_i64(ctx, dtot, &hs);
+  *total = read_i64(ctx, dtot, &hs);
   HCI_TRY(hs);
-  const int64_t left = read_i64(ctx, reinterpret_cast<const int64_t*>(ctl + 1), &hs);
+  *left = read_i64(ctx, reinterpret_cast<const int64_t*>(ctl + 1), &hs);
   HCI_TRY(hs);
-  HCI_TRY(ensure_buf(ctx, S.colN, (size_t)(total + 1) * 4));
-  HCI_TRY(ensure_buf(ctx, S.valN, (size_t)(total + 1) * 8));
+  return HCI_OK;
+}
+
+// Columns of the rows of stage_search written to col (row q at inc.rpN[q]):
+// staged rows copied, the rows left searched again at their offsets.
+static hci_status stage_place(hci_ctx* ctx, GraphArgs& A, int64_t left, int32_t* col) {
+  IncScratch& S = ctx->inc;
+  cudaStream_t st = ctx->st;
+  const int64_t nrows = A.nrows;
   HCI_LAUNCH(k_copy_staged, grid_for(nrows * 32, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN), nrows,
-                                                                    bp<int32_t>(S.stage), bp<int32_t>(S.colN));
+                                                                    bp<int32_t>(S.stage), col);
   HCI_CUDA(ctx, cudaGetLastError());
   ctx->st_counts[HCI_ST_ROWS_REFILLED] += left;
   if (left > 0) {
+    unsigned long long* ctl = bp<unsigned long long>(S.ctl);
     HCI_TRY(ensure_buf(ctx, S.left, (size_t)left * 12 + 16));
     int64_t* left_off = bp<int64_t>(S.left);
     int32_t* left_rows = reinterpret_cast<int32_t*>(left_off + left);
@@ -1212,12 +1375,11 @@ static hci_status rows_staged(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t* 
     const int32_t* rl = A.rowlist;
     A.rowlist = left_rows;
     A.nrows = left;
-    hci_status fs = rows_fill(ctx, A, left_off, bp<int32_t>(S.colN), bp<double>(S.valN));
+    hci_status fs = rows_fill(ctx, A, left_off, col, nullptr);
     A.rowlist = rl;
     A.nrows = nrows;
     HCI_TRY(fs);
   }
-  *nnz = total;
   return HCI_OK;
 }
 
@@ -1233,10 +1395,229 @@ static hci_status compute_diag(hci_ctx* ctx, int64_t nrows, const ulonglong2* ke
   return HCI_OK;
 }
 
-hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
+// b grown to at least `bytes` (a quarter more, for later growth), its first
+// `keep` bytes preserved
+static hci_status grow_keep(hci_ctx* ctx, DevBuf& b, size_t bytes, size_t keep) {
+  if (b.p && b.bytes >= bytes) return HCI_OK;
+  DevBuf& t = ctx->inc.grow;
+  HCI_TRY(ensure_buf(ctx, t, bytes + bytes / 4));
+  if (keep > 0 && b.p) HCI_CUDA(ctx, cudaMemcpyAsync(t.p, b.p, keep, cudaMemcpyDeviceToDevice, ctx->st));
+  std::swap(b, t);
+  free_buf(ctx->st, t);
+  return HCI_OK;
+}
+
+static void free_segments(hci_ctx* ctx) {
+  Graph& G = ctx->graph;
+  for (int k = 0; k < GRAPH_MAXSEG; ++k) {
+    free_buf(ctx->st, G.seg_col[k]);
+    free_buf(ctx->st, G.seg_val[k]);
+  }
+  G.nseg = 0;
+  G.nstored = 0;
+  G.nnz = 0;
+  G.pool_used = G.pool_cap = 0;
+}
+
+// A new segment of `entries` stored connections; HCI_ERR_NOMEM when the
+// stored connections would exceed the context's budget.
+static hci_status seg_alloc(hci_ctx* ctx, int64_t entries, int* seg) {
+  Graph& G = ctx->graph;
+  if (G.nseg >= GRAPH_MAXSEG) return hci_fail(ctx, HCI_ERR_INVALID, "graph: segment table full");
+  const int64_t bytes = (G.nstored + entries) * 12;
+  if (ctx->graph_budget > 0 && bytes > ctx->graph_budget)
+    return hci_fail(ctx, HCI_ERR_NOMEM, "graph: %lld bytes of stored connections exceed the budget of %lld",
+                    (long long)bytes, (long long)ctx->graph_budget);
+  HCI_TRY(ensure_buf(ctx, G.seg_col[G.nseg], (size_t)(entries + 1) * 4));
+  HCI_TRY(ensure_buf(ctx, G.seg_val[G.nseg], (size_t)(entries + 1) * 8));
+  *seg = G.nseg++;
+  return HCI_OK;
+}
+
+// The new rows listed in A searched once (stage_search), the staging space
+// sized from the mean length of a strided sample of them (the old rows'
+// lengths say little when the space grows many-fold).
+static hci_status stage_new_rows(hci_ctx* ctx, GraphArgs& A, int64_t nnew, int64_t nV, int64_t* total, int64_t* left) {
+  IncScratch& S = ctx->inc;
+  cudaStream_t st = ctx->st;
+  const int64_t ns = std::min<int64_t>(nnew, ROW_SAMPLE);
+  HCI_TRY(ensure_buf(ctx, S.samp, (size_t)ns * 12 + 16));
+  int64_t* samp_cnt = bp<int64_t>(S.samp);
+  int32_t* samp_rows = reinterpret_cast<int32_t*>(samp_cnt + ns);
+  HCI_LAUNCH(k_stride_sample, grid_for(ns, 256), 256, 0, st)(A.rowlist, nnew, ns, samp_rows);
+  GraphArgs B = A;
+  B.rowlist = samp_rows;
+  B.nrows = ns;
+  B.rowcnt = samp_cnt;
+  HCI_CUDA(ctx, cudaMemsetAsync(B.queue, 0, 8, st));
+  HCI_LAUNCH(k_rows<ROWS_COUNT>, rows_grid(ctx), G_WARPS * 32, 0, st)(B);
+  HCI_CUDA(ctx, cudaGetLastError());
+  std::vector<int64_t> cnt((size_t)ns);
+  HCI_CUDA(ctx, cudaMemcpyAsync(cnt.data(), samp_cnt, (size_t)ns * 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  double sum = 0.0;
+  for (int64_t v : cnt) sum += (double)v;
+  const double mean = ns > 0 ? sum / (double)ns : 0.0;
+  const double want = 1.5 * (double)nnew * mean;
+  const int64_t est = (int64_t)std::min((double)nnew * (double)nV, want) + ((int64_t)1 << 22);
+  return stage_search(ctx, A, est, total, left);
+}
+
+static hci_status graph_build_half(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   Graph& G = ctx->graph;
   G.valid = false;
   if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 columns");
+  free_segments(ctx);
+  G.half = true;
+  prof_tic(ctx, HCI_PH_GRAPH);
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+  HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  // a fresh space: internal ids = sorted positions
+  HCI_TRY(ensure_buf(ctx, G.keys_int, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys_int.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, ctx->st));
+  HCI_TRY(ensure_buf(ctx, G.s2i, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, G.i2s, (size_t)nV * 4));
+  HCI_LAUNCH(k_iota, grid_for(nV, 256), 256, 0, ctx->st)(bp<int32_t>(G.s2i), bp<int32_t>(G.i2s), nV);
+  GraphArgs A;
+  HCI_TRY(build_space(ctx, nV, A));
+  A.s2i = bp<int32_t>(G.s2i);
+  A.lower = 1;
+  prof_tic(ctx, HCI_PH_GRAPH_ROWS);
+  // stored halves of the rows: count, offsets, one segment, fill, elements
+  HCI_TRY(rows_count(ctx, A, ctx->inc.cnt));
+  HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
+  HCI_TRY(ensure_buf(ctx, G.rowstart, (size_t)(nV + 1) * 8));
+  HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->inc.cnt), bp<int64_t>(G.rowptr), nV, dtot));
+  HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(G.rowptr), nV, dtot);
+  hci_status st = HCI_OK;
+  const int64_t nst = read_i64(ctx, dtot, &st);
+  HCI_TRY(st);
+  int seg = 0;
+  HCI_TRY(seg_alloc(ctx, nst, &seg));
+  int32_t* col = bp<int32_t>(G.seg_col[seg]);
+  double* val = bp<double>(G.seg_val[seg]);
+  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowptr), col, val));
+  HCI_LAUNCH(k_row_values<true>, grid_for(nV * 32, 256), 256, 0, ctx->st)(
+      nullptr, nV, bp<int64_t>(G.rowptr), nullptr, col, val, bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);
+  HCI_LAUNCH(k_append_rows, grid_for(nV + 1, 256), 256, 0, ctx->st)(0, nV, bp<int64_t>(G.rowptr), 0, seg,
+                                                                     bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart));
+  HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_GRAPH_ROWS);
+  HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
+  HCI_TRY(compute_diag(ctx, nV, bp<ulonglong2>(G.keys_int), bp<double>(G.diag)));
+  prof_toc(ctx, HCI_PH_GRAPH);
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  G.nV = nV;
+  G.nstored = nst;
+  G.nnz = 2 * nst;
+  ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
+  G.valid = true;
+  return HCI_OK;
+}
+
+// V' contains every determinant of the cached space.  Rows and columns of the
+// graph are internal ids (insertion order): old determinants keep theirs and
+// the new ones are numbered after them, so a connection between an old and a
+// new determinant belongs to the new row, and the stored rows never change.
+// Only the new rows are searched (once, staged), into one new segment.
+static hci_status graph_extend_half(hci_ctx* ctx, const uint64_t* keys, int64_t nV, bool* done) {
+  Graph& G = ctx->graph;
+  IncScratch& S = ctx->inc;
+  *done = false;
+  const int64_t nold = G.nV;
+  if (nV <= nold || nV >= ((int64_t)1 << 31) - 1 || G.nseg >= GRAPH_MAXSEG) return HCI_OK;
+  cudaStream_t st = ctx->st;
+  unsigned long long* missing = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 24);
+  int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+  const ulonglong2* Vn = reinterpret_cast<const ulonglong2*>(keys);
+  HCI_TRY(ensure_buf(ctx, S.pos_old, (size_t)nold * 8));
+  HCI_TRY(ensure_buf(ctx, S.mark, (size_t)nV * 8));
+  HCI_CUDA(ctx, cudaMemsetAsync(S.mark.p, 0, (size_t)nV * 8, st));
+  HCI_CUDA(ctx, cudaMemsetAsync(missing, 0, 8, st));
+  HCI_LAUNCH(k_find_old, grid_for(nold, 256), 256, 0, st)(bp<ulonglong2>(G.keys), nold, Vn, nV,
+                                                          bp<int64_t>(S.pos_old), bp<int64_t>(S.mark), missing);
+  unsigned long long miss = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&miss, missing, 8, cudaMemcpyDeviceToHost, st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  if (miss) return HCI_OK;        // not an extension: full rebuild
+  prof_tic(ctx, HCI_PH_GRAPH);
+  hci_status hs = HCI_OK;
+  const int64_t nnew = nV - nold;
+  // keys and map of the old space move to the scratch side
+  std::swap(G.keys, S.keys_old);
+  std::swap(G.s2i, S.s2i_old);
+  HCI_TRY(ensure_buf(ctx, G.keys, (size_t)nV * 16));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.keys.p, keys, (size_t)nV * 16, cudaMemcpyDeviceToDevice, st));
+  // new determinants in sorted order, their internal ids nold + q
+  HCI_TRY(ensure_buf(ctx, S.flag, (size_t)(2 * nV + 1) * 8));
+  int64_t* nflag = bp<int64_t>(S.flag);
+  int64_t* npos = nflag + nV;
+  HCI_LAUNCH(k_not, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.mark), nV, nflag);
+  HCI_TRY(scan_i64(ctx, nflag, npos, nV, dtot));
+  HCI_TRY(ensure_buf(ctx, S.newrows, (size_t)nnew * 4));
+  HCI_LAUNCH(k_compact_idx, grid_for(nV, 256), 256, 0, st)(nflag, npos, nV, bp<int32_t>(S.newrows));
+  // maps and internal-order keys of V' (old ids and keys unchanged)
+  HCI_TRY(ensure_buf(ctx, G.s2i, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, G.i2s, (size_t)nV * 4));
+  HCI_TRY(grow_keep(ctx, G.keys_int, (size_t)nV * 16, (size_t)nold * 16));
+  HCI_LAUNCH(k_build_perm, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<int32_t>(S.s2i_old), nold,
+                                                          bp<int32_t>(S.newrows), nnew, Vn, bp<int32_t>(G.s2i),
+                                                          bp<int32_t>(G.i2s), bp<ulonglong2>(G.keys_int));
+  GraphArgs A;
+  HCI_TRY(build_space(ctx, nV, A));
+  A.s2i = bp<int32_t>(G.s2i);
+  A.lower = 1;
+  A.rowlist = bp<int32_t>(S.newrows);
+  A.nrows = nnew;
+  prof_tic(ctx, HCI_PH_GRAPH_ROWS);
+  int64_t total = 0, left = 0;
+  HCI_TRY(stage_new_rows(ctx, A, nnew, nV, &total, &left));
+  int seg = 0;
+  HCI_TRY(seg_alloc(ctx, total, &seg));
+  int32_t* col = bp<int32_t>(G.seg_col[seg]);
+  double* val = bp<double>(G.seg_val[seg]);
+  HCI_TRY(stage_place(ctx, A, left, col));
+  HCI_LAUNCH(k_row_values<true>, grid_for(nnew * 32, 256), 256, 0, st)(
+      bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), nullptr, col, val, bp<ulonglong2>(G.keys),
+      bp<ulonglong2>(G.keys_int), A.H);
+  HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_GRAPH_ROWS);
+  // row table: the new rows after the old ones
+  prof_tic(ctx, HCI_PH_GRAPH_MERGE);
+  HCI_TRY(grow_keep(ctx, G.rowptr, (size_t)(nV + 1) * 8, (size_t)(nold + 1) * 8));
+  HCI_TRY(grow_keep(ctx, G.rowstart, (size_t)(nV + 1) * 8, (size_t)nold * 8));
+  HCI_LAUNCH(k_append_rows, grid_for(nnew + 1, 256), 256, 0, st)(nold, nnew, bp<int64_t>(S.rpN), G.nstored, seg,
+                                                                  bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart));
+  HCI_CUDA(ctx, cudaGetLastError());
+  prof_toc(ctx, HCI_PH_GRAPH_MERGE);
+  // diagonal: old entries stay, the new ids are computed
+  HCI_TRY(grow_keep(ctx, G.diag, (size_t)nV * 8, (size_t)nold * 8));
+  HCI_TRY(compute_diag(ctx, nnew, bp<ulonglong2>(G.keys_int) + nold, bp<double>(G.diag) + nold));
+  prof_toc(ctx, HCI_PH_GRAPH);
+  HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  (void)hs;
+  G.nV = nV;
+  G.nstored += total;
+  G.nnz = 2 * G.nstored;
+  ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
+  *done = true;
+  return HCI_OK;
+}
+
+// entries the both-orientation pool (segment 0) holds
+static int64_t pool_entries(const Graph& G) {
+  const int64_t a = (int64_t)(G.seg_col[0].bytes / 4), b = (int64_t)(G.seg_val[0].bytes / 8);
+  return a < b ? a : b;
+}
+
+static hci_status graph_build_full(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
+  Graph& G = ctx->graph;
+  G.valid = false;
+  if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 columns");
+  free_segments(ctx);
+  G.half = false;
   prof_tic(ctx, HCI_PH_GRAPH);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
@@ -1271,12 +1652,13 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   if (ctx->graph_budget > 0 && cap * 12 > ctx->graph_budget)
     return hci_fail(ctx, HCI_ERR_NOMEM, "graph: a pool of %lld bytes exceeds the budget of %lld", (long long)(cap * 12),
                     (long long)ctx->graph_budget);
-  HCI_TRY(ensure_buf(ctx, G.col, (size_t)cap * 4));
-  HCI_TRY(ensure_buf(ctx, G.val, (size_t)cap * 8));
-  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val)));
+  HCI_TRY(ensure_buf(ctx, G.seg_col[0], (size_t)cap * 4));
+  HCI_TRY(ensure_buf(ctx, G.seg_val[0], (size_t)cap * 8));
+  G.nseg = 1;
+  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.seg_col[0]), bp<double>(G.seg_val[0])));
   HCI_LAUNCH(k_row_values<false>, grid_for(nV * 32, 256), 256, 0, ctx->st)(
-      nullptr, nV, bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen), bp<int32_t>(G.col), bp<double>(G.val),
-      bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);
+      nullptr, nV, bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen), bp<int32_t>(G.seg_col[0]),
+      bp<double>(G.seg_val[0]), bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_GRAPH_ROWS);
   HCI_TRY(ensure_buf(ctx, G.diag, (size_t)nV * 8));
@@ -1285,9 +1667,9 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
   G.nV = nV;
   G.nnz = nnz;
+  G.nstored = nnz;
   G.pool_used = used;
-  G.pool_cap = (int64_t)(G.col.bytes / 4) < (int64_t)(G.val.bytes / 8) ? (int64_t)(G.col.bytes / 4)
-                                                                        : (int64_t)(G.val.bytes / 8);
+  G.pool_cap = pool_entries(G);
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   G.valid = true;
   return HCI_OK;
@@ -1298,12 +1680,12 @@ hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
 // the new ones are numbered after them, so only the new rows are searched,
 // their transposes are appended to the old rows (in place where the row's
 // slack allows), and no stored column changes.
-static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, bool* done) {
+static hci_status graph_extend_full(hci_ctx* ctx, const uint64_t* keys, int64_t nV, bool* done) {
   Graph& G = ctx->graph;
   IncScratch& S = ctx->inc;
   *done = false;
   const int64_t nold = G.nV;
-  if (nV <= nold || nV >= ((int64_t)1 << 31) - 1) return HCI_OK;
+  if (nV <= nold || nV >= ((int64_t)1 << 31) - 1 || G.nseg != 1) return HCI_OK;
   cudaStream_t st = ctx->st;
   unsigned long long* missing = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 24);
   int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
@@ -1340,11 +1722,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   // maps and internal-order keys of V' (old ids and keys unchanged)
   HCI_TRY(ensure_buf(ctx, G.s2i, (size_t)nV * 4));
   HCI_TRY(ensure_buf(ctx, G.i2s, (size_t)nV * 4));
-  if (G.keys_int.bytes < (size_t)nV * 16) {
-    HCI_TRY(ensure_buf(ctx, S.keys_int_old, (size_t)nV * 16 + (size_t)nV * 4));
-    HCI_CUDA(ctx, cudaMemcpyAsync(S.keys_int_old.p, G.keys_int.p, (size_t)nold * 16, cudaMemcpyDeviceToDevice, st));
-    std::swap(G.keys_int, S.keys_int_old);
-  }
+  HCI_TRY(grow_keep(ctx, G.keys_int, (size_t)nV * 16, (size_t)nold * 16));
   HCI_LAUNCH(k_build_perm, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(S.pos_old), bp<int32_t>(S.s2i_old), nold,
                                                           bp<int32_t>(S.newrows), nnew, Vn, bp<int32_t>(G.s2i),
                                                           bp<int32_t>(G.i2s), bp<ulonglong2>(G.keys_int));
@@ -1358,27 +1736,11 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   // (the old rows' lengths say little when the space grows many-fold)
   int64_t nnzN = 0;
   {
-    const int64_t ns = std::min<int64_t>(nnew, ROW_SAMPLE);
-    HCI_TRY(ensure_buf(ctx, S.samp, (size_t)ns * 12 + 16));
-    int64_t* samp_cnt = bp<int64_t>(S.samp);
-    int32_t* samp_rows = reinterpret_cast<int32_t*>(samp_cnt + ns);
-    HCI_LAUNCH(k_stride_sample, grid_for(ns, 256), 256, 0, st)(bp<int32_t>(S.newrows), nnew, ns, samp_rows);
-    GraphArgs B = A;
-    B.rowlist = samp_rows;
-    B.nrows = ns;
-    B.rowcnt = samp_cnt;
-    HCI_CUDA(ctx, cudaMemsetAsync(B.queue, 0, 8, st));
-    HCI_LAUNCH(k_rows<ROWS_COUNT>, ROWS_GRID, G_WARPS * 32, 0, st)(B);
-    HCI_CUDA(ctx, cudaGetLastError());
-    std::vector<int64_t> cnt((size_t)ns);
-    HCI_CUDA(ctx, cudaMemcpyAsync(cnt.data(), samp_cnt, (size_t)ns * 8, cudaMemcpyDeviceToHost, st));
-    HCI_CUDA(ctx, cudaStreamSynchronize(st));
-    double sum = 0.0;
-    for (int64_t v : cnt) sum += (double)v;
-    const double mean = ns > 0 ? sum / (double)ns : 0.0;
-    const double want = 1.5 * (double)nnew * mean;
-    const int64_t est = (int64_t)std::min((double)nnew * (double)nV, want) + ((int64_t)1 << 22);
-    HCI_TRY(rows_staged(ctx, A, est, &nnzN));
+    int64_t left = 0;
+    HCI_TRY(stage_new_rows(ctx, A, nnew, nV, &nnzN, &left));
+    HCI_TRY(ensure_buf(ctx, S.colN, (size_t)(nnzN + 1) * 4));
+    HCI_TRY(ensure_buf(ctx, S.valN, (size_t)(nnzN + 1) * 8));
+    HCI_TRY(stage_place(ctx, A, left, bp<int32_t>(S.colN)));
   }
   HCI_LAUNCH(k_row_values<true>, grid_for(nnew * 32, 256), 256, 0, st)(
       bp<int32_t>(S.newrows), nnew, bp<int64_t>(S.rpN), nullptr, bp<int32_t>(S.colN), bp<double>(S.valN),
@@ -1424,8 +1786,8 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
     if (repack || G.pool_used + total <= G.pool_cap) break;
     repack = 1;
   }
-  int32_t* col_dst = bp<int32_t>(G.col);
-  double* val_dst = bp<double>(G.val);
+  int32_t* col_dst = bp<int32_t>(G.seg_col[0]);
+  double* val_dst = bp<double>(G.seg_val[0]);
   int64_t base = G.pool_used;
   if (repack) {
     const int64_t cap = total + total / 4 + 1024;
@@ -1441,17 +1803,18 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
   }
   HCI_LAUNCH(k_assign_starts, grid_for(nV, 256), 256, 0, st)(bp<int64_t>(G.rowstart), rel, nV, base);
   HCI_LAUNCH(k_move_old_rows, grid_for(nold * 32, 256), 256, 0, st)(
-      bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), nold, bp<int32_t>(G.col), bp<double>(G.val),
+      bp<int64_t>(S.rp_old), bp<int64_t>(S.len_old), nold, bp<int32_t>(G.seg_col[0]), bp<double>(G.seg_val[0]),
       bp<int64_t>(G.rowstart), col_dst, val_dst, bp<ulonglong2>(S.T), bp<int64_t>(S.tstart), bp<int64_t>(S.hist),
       bp<double>(S.valN));
   HCI_LAUNCH(k_place_new_rows, gw, 256, 0, st)(nold, nnew, bp<int64_t>(S.rpN), bp<int32_t>(S.colN),
                                                 bp<double>(S.valN), bp<int64_t>(G.rowstart), col_dst, val_dst);
   HCI_CUDA(ctx, cudaGetLastError());
   if (repack) {
-    std::swap(G.col, S.col_old);
-    std::swap(G.val, S.val_old);
-    G.pool_cap = (int64_t)(G.col.bytes / 4) < (int64_t)(G.val.bytes / 8) ? (int64_t)(G.col.bytes / 4)
-                                                                          : (int64_t)(G.val.bytes / 8);
+    std::swap(G.seg_col[0], S.col_old);
+    std::swap(G.seg_val[0], S.val_old);
+    free_buf(st, S.col_old);
+    free_buf(st, S.val_old);
+    G.pool_cap = pool_entries(G);
     G.pool_used = total;
   } else {
     G.pool_used += total;
@@ -1467,16 +1830,13 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
     return hci_fail(ctx, HCI_ERR_CUDA, "graph_extend: inconsistent sizes %lld != %lld + %lld + %lld", (long long)nnz,
                     (long long)G.nnz, (long long)nnzN, (long long)nT);
   // diagonal: old entries stay, the new ids are computed
-  if (G.diag.bytes < (size_t)nV * 8) {
-    HCI_TRY(ensure_buf(ctx, S.diag_old, (size_t)nV * 8 + (size_t)nV * 4));
-    HCI_CUDA(ctx, cudaMemcpyAsync(S.diag_old.p, G.diag.p, (size_t)nold * 8, cudaMemcpyDeviceToDevice, st));
-    std::swap(G.diag, S.diag_old);
-  }
+  HCI_TRY(grow_keep(ctx, G.diag, (size_t)nV * 8, (size_t)nold * 8));
   HCI_TRY(compute_diag(ctx, nnew, bp<ulonglong2>(G.keys_int) + nold, bp<double>(G.diag) + nold));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   G.nV = nV;
   G.nnz = nnz;
+  G.nstored = nnz;
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   *done = true;
   return HCI_OK;
@@ -1487,6 +1847,7 @@ static hci_status graph_extend(hci_ctx* ctx, const uint64_t* keys, int64_t nV, b
 static hci_status graph_build_direct(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   Graph& G = ctx->graph;
   G.valid = false;
+  free_segments(ctx);
   if (nV >= ((int64_t)1 << 31) - 1) return hci_fail(ctx, HCI_ERR_INVALID, "graph: nV exceeds int32 indices");
   prof_tic(ctx, HCI_PH_GRAPH);
   HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
@@ -1515,14 +1876,38 @@ static hci_status graph_build_direct(hci_ctx* ctx, const uint64_t* keys, int64_t
 static void release_stored(hci_ctx* ctx) {
   Graph& G = ctx->graph;
   IncScratch& S = ctx->inc;
-  DevBuf* bufs[] = {&G.rowptr, &G.rowstart, &G.rowlen, &G.rowcap, &G.col, &G.val, &S.col_old, &S.val_old,
-                    &S.colN, &S.valN, &S.T, &S.T2, &S.scr, &S.stage};
+  free_segments(ctx);
+  DevBuf* bufs[] = {&G.rowptr, &G.rowstart, &G.rowlen, &G.rowcap, &S.scr, &S.stage, &S.grow, &S.col_old,
+                    &S.val_old, &S.colN, &S.valN, &S.T, &S.T2};
   for (DevBuf* b : bufs) free_buf(ctx->st, *b);
-  G.pool_used = G.pool_cap = 0;
-  G.nnz = 0;
   cudaStreamSynchronize(ctx->st);
 }
 
+// Stored form of the next build: both orientations unless the context was
+// set to one orientation or fell back to it.
+static bool want_half(const hci_ctx* ctx) {
+  return ctx->sigma_mode == HCI_SIGMA_HALF || (ctx->sigma_mode == HCI_SIGMA_AUTO && ctx->half_fallback);
+}
+
+static hci_status graph_stored(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
+  Graph& G = ctx->graph;
+  const bool half = want_half(ctx);
+  hci_status s = HCI_OK;
+  bool done = false;
+  if (G.valid && !G.direct && G.half == half && ctx->incremental) {
+    G.valid = false;
+    s = half ? graph_extend_half(ctx, keys, nV, &done) : graph_extend_full(ctx, keys, nV, &done);
+  }
+  if (s == HCI_OK && !done) {
+    G.direct = false;
+    s = half ? graph_build_half(ctx, keys, nV) : graph_build_full(ctx, keys, nV);
+  }
+  return s;
+}
+
+// HCI_SIGMA_AUTO: both orientations while they fit the budget (or device
+// memory), then one orientation, then the direct form, each step for the
+// rest of the context's life.
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   uint64_t hsh = 0;
   HCI_TRY(hash_keys(ctx, keys, nV, &hsh));
@@ -1532,15 +1917,13 @@ hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV) {
   if (!ok) return hci_fail(ctx, HCI_ERR_INVALID, "keys are not strictly ascending");
   const bool direct = ctx->sigma_mode == HCI_SIGMA_DIRECT || (ctx->sigma_mode == HCI_SIGMA_AUTO && ctx->direct_fallback);
   if (!direct) {
-    hci_status s = HCI_OK;
-    bool done = false;
-    if (ctx->graph.valid && !ctx->graph.direct && ctx->incremental) {
+    hci_status s = graph_stored(ctx, keys, nV);
+    if (s == HCI_ERR_NOMEM && ctx->sigma_mode == HCI_SIGMA_AUTO && !ctx->half_fallback) {
+      // both orientations do not fit: store one orientation of each pair
       ctx->graph.valid = false;
-      s = graph_extend(ctx, keys, nV, &done);
-    }
-    if (s == HCI_OK && !done) {
-      ctx->graph.direct = false;
-      s = graph_build(ctx, keys, nV);
+      ctx->half_fallback = true;
+      release_stored(ctx);
+      s = graph_stored(ctx, keys, nV);
     }
     if (s == HCI_OK) {
       ctx->graph.hash = hsh;
@@ -1572,7 +1955,7 @@ static hci_status sigma_direct(hci_ctx* ctx, const double* c, double* sigma, int
     A.dnnz = G.nnz < 0 ? cnt : nullptr;
     if (A.dnnz) HCI_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8, ctx->st));
     HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-    HCI_LAUNCH(k_rows<ROWS_SIGMA>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
+    HCI_LAUNCH(k_rows<ROWS_SIGMA>, rows_grid(ctx), G_WARPS * 32, 0, ctx->st)(A);
     HCI_CUDA(ctx, cudaGetLastError());
     if (A.dnnz) {
       unsigned long long h = 0;
@@ -1591,7 +1974,7 @@ hci_status direct_rdm(hci_ctx* ctx, const double* c, const RdmAcc& R) {
   A.dc = c;
   A.R = R;
   HCI_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 8, ctx->st));
-  HCI_LAUNCH(k_rows<ROWS_RDM>, ROWS_GRID, G_WARPS * 32, 0, ctx->st)(A);
+  HCI_LAUNCH(k_rows<ROWS_RDM>, rows_grid(ctx), G_WARPS * 32, 0, ctx->st)(A);
   HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
 }
@@ -1607,18 +1990,28 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
     prof_toc(ctx, HCI_PH_SIGMA);
     return HCI_OK;
   }
+  if (G.half) HCI_CUDA(ctx, cudaMemsetAsync(sigma, 0, (size_t)G.nV * nvec * 8, ctx->st));
   prof_tic(ctx, HCI_PH_SIGMA);
   ctx->st_counts[HCI_ST_SIGMA_CALLS] += nvec;
   ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;
   ctx->st_counts[HCI_ST_SIGMA_NNZ] += G.nnz * nvec;
-  if (nvec == 1)
-    HCI_LAUNCH(k_sigma1, 152 * 6, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart),
-                                                   bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag), G.nV,
-                                                   c, sigma, 1);
-  else
-    HCI_LAUNCH(k_sigma, grid_for(G.nV * 32, 256, 152 * 16), 256, 0, ctx->st)(
-        bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), bp<int32_t>(G.col), bp<double>(G.val), bp<double>(G.diag),
-        G.nV, c, sigma, nvec);
+  if (G.half) {
+    const SegTab T = G.tab();
+    if (nvec == 1)
+      HCI_LAUNCH(k_sigma1_half, ctx->nsm * SIGMA_HALF_BLOCKS_PER_SM, 256, 0, ctx->st)(
+          bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), T, bp<double>(G.diag), G.nV, c, sigma);
+    else
+      HCI_LAUNCH(k_sigma_half, grid_for(G.nV * 32, 256, ctx->nsm * 16), 256, 0, ctx->st)(
+          bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), T, bp<double>(G.diag), G.nV, c, sigma, nvec);
+  } else if (nvec == 1) {
+    HCI_LAUNCH(k_sigma1, ctx->nsm * 6, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart),
+                                                        bp<int32_t>(G.seg_col[0]), bp<double>(G.seg_val[0]),
+                                                        bp<double>(G.diag), G.nV, c, sigma, 1);
+  } else {
+    HCI_LAUNCH(k_sigma, grid_for(G.nV * 32, 256, ctx->nsm * 16), 256, 0, ctx->st)(
+        bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), bp<int32_t>(G.seg_col[0]), bp<double>(G.seg_val[0]),
+        bp<double>(G.diag), G.nV, c, sigma, nvec);
+  }
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_SIGMA);
   return HCI_OK;

@@ -22,27 +22,55 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Stored connections are kept in segments (one per build or extension of
+// the space); a row's first entry is addressed as segment << GRAPH_SEG_SHIFT
+// | offset within the segment, and the segment table is handed to kernels by
+// value.
+constexpr int GRAPH_MAXSEG = 32;
+constexpr int GRAPH_SEG_SHIFT = 40;
+constexpr int64_t GRAPH_SEG_MASK = ((int64_t)1 << GRAPH_SEG_SHIFT) - 1;
+struct SegTab {
+  const int32_t* col[GRAPH_MAXSEG];
+  const double* val[GRAPH_MAXSEG];
+};
+
 // Connection graph of one determinant space (Sec. IV: the Hamiltonian on V
 // is evaluated from every single and double excitation linking two
-// determinants of V; the same connections feed the RDMs).
+// determinants of V; the same connections feed the RDMs).  Rows and columns
+// are internal ids (insertion order).  Both orientations: each row holds all
+// of its connections in a pool with per-row slack (segment 0).  One
+// orientation: each connected pair is stored once, in the row of the
+// determinant with the larger id, one segment per build or extension (a
+// grown space only adds rows); H c adds every stored entry to both rows.
 struct Graph {
   bool valid = false;
   int64_t nV = 0;
   uint64_t hash = 0;
-  int64_t nnz = 0;           // off-diagonal entries (both orientations stored)
+  int64_t nnz = 0;           // off-diagonal connections, both orientations counted (2 x stored)
+  int64_t nstored = 0;       // stored entries, one per connected pair
   int64_t nua = 0, nub = 0;  // distinct alpha / beta strings of the space
-  DevBuf rowptr;             // int64 [nV+1] prefix sums of the row lengths (logical CSR)
-  DevBuf rowstart;           // int64 [nV] first pool slot of each row
-  DevBuf rowlen;             // int64 [nV] live entries of each row
-  DevBuf rowcap;             // int64 [nV] slots owned by each row (>= rowlen)
-  DevBuf col;                // int32 pool of columns
-  DevBuf val;                // double pool of values
-  int64_t pool_used = 0, pool_cap = 0;
+  bool half = false;         // one orientation per pair (else both, in a row pool with slack)
+  DevBuf rowptr;             // int64 [nV+1] prefix sums of the stored row lengths (internal order)
+  DevBuf rowstart;           // int64 [nV] first entry of each row: segment << GRAPH_SEG_SHIFT | offset
+  DevBuf rowlen;             // both orientations: int64 [nV] live entries of each row
+  DevBuf rowcap;             // both orientations: int64 [nV] slots owned by each row (>= rowlen)
+  int64_t pool_used = 0, pool_cap = 0;   // both orientations: slots of the row pool (segment 0)
+  DevBuf seg_col[GRAPH_MAXSEG];   // int32 columns (internal ids; one orientation: all below the row's id)
+  DevBuf seg_val[GRAPH_MAXSEG];   // double <D_i|H|D_j>
+  int nseg = 0;
   DevBuf diag;               // double [nV]
   DevBuf keys;               // copy of the space's keys [nV][2], sorted
   DevBuf keys_int;           // the same keys by internal id (insertion order)
   DevBuf s2i, i2s;           // int32 maps sorted position <-> internal id
   bool direct = false;       // no stored rows: every traversal searches and evaluates the connections again
+  SegTab tab() const {
+    SegTab t{};
+    for (int k = 0; k < nseg; ++k) {
+      t.col[k] = reinterpret_cast<const int32_t*>(seg_col[k].p);
+      t.val[k] = reinterpret_cast<const double*>(seg_val[k].p);
+    }
+    return t;
+  }
 };
 
 struct Lists {
@@ -60,8 +88,8 @@ struct Lists {
 
 // Scratch of the incremental graph update (V' = V + new determinants).
 struct IncScratch {
-  DevBuf pos_old, mark, flag, newrows, rpN, colN, valN, cnt, hist, tbase, T, T2, tstart, len;
-  DevBuf keys_old, rp_old, col_old, val_old, len_old, cap_old, diag_old, s2i_old, keys_int_old;
+  DevBuf pos_old, mark, flag, newrows, rpN, cnt, keys_old, s2i_old, grow;
+  DevBuf colN, valN, hist, tbase, T, T2, tstart, len, rp_old, col_old, val_old, len_old, cap_old;  // both orientations
   DevBuf scr, stage, roff, ctl, left, samp;   // staged row search
 };
 
@@ -94,6 +122,7 @@ struct hci_ctx {
   int sigma_mode = HCI_SIGMA_AUTO;
   int64_t graph_budget = 0;  // bytes the stored connection pool may take (0: device memory)
   bool direct_fallback = false;
+  bool half_fallback = false;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
   int nsm = 0;               // streaming multiprocessors of the context's device (grid sizes)
   int64_t fail_alloc_after = -1;  // HCI_FAIL_ALLOC_AFTER: allocations left before one is refused (-1: off)
@@ -175,7 +204,6 @@ hci_status hash_keys(hci_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t* ha
 hci_status check_sorted(hci_ctx* ctx, const uint64_t* keys, int64_t n, int* ok_host);
 
 // graph.cu
-hci_status graph_build(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 // sigma on vectors in internal order (rows/columns of the cached graph)
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec);

@@ -13,8 +13,8 @@
 //   double a->c, b->d (holes a<b, particles c<d in one spin, or a->c alpha
 //   and b->d beta): rdm2[c,a,d,b] += w; rdm2[d,b,c,a] += w;
 //     same spin only: rdm2[c,b,d,a] -= w; rdm2[d,a,c,b] -= w
-// The graph stores both orientations (i,j) and (j,i) of a pair; one is
-// accumulated and the other added as its transpose.  The diagonal part is
+// One orientation of each connected pair is accumulated (the graph stores
+// one, or both) and the other added as its transpose.  The diagonal part is
 // reduced through the weighted
 // occupation correlation M[sp][tq] = sum_i c_i^2 n_sp(i) n_tq(i), folded over
 // the alpha and beta string groups of the graph.
@@ -26,11 +26,14 @@ namespace {
 constexpr int R_WARPS = 8;
 
 
+// One warp per row from a queue.  One-orientation graphs: every stored entry
+// is one orientation of a connected pair; both-orientation graphs: the
+// entries with j > i are.
 __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulonglong2* __restrict__ V, int64_t nV,
                                                               const double* __restrict__ c,
                                                               const int64_t* __restrict__ rowptr,
                                                               const int64_t* __restrict__ rowstart,
-                                                              const int32_t* __restrict__ col, RdmAcc R,
+                                                              const __grid_constant__ SegTab T, int both, RdmAcc R,
                                                               unsigned long long* __restrict__ queue) {
   const int lane = threadIdx.x & 31;
   while (true) {
@@ -39,11 +42,13 @@ __global__ void __launch_bounds__(R_WARPS * 32) k_rdm_offdiag(int n, const ulong
     const int64_t i = (int64_t)__shfl_sync(0xffffffffu, qi, 0);
     if (i >= nV) break;
     const double ci = c[i];
+    if (ci == 0.0) continue;
     const ulonglong2 ki = V[i];
-    const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
-    for (int64_t k = b + lane; k < e; k += 32) {
+    const int64_t rs = rowstart[i], len = rowptr[i + 1] - rowptr[i];
+    const int32_t* col = T.col[rs >> GRAPH_SEG_SHIFT] + (rs & GRAPH_SEG_MASK);
+    for (int64_t k = lane; k < len; k += 32) {
       const int64_t j = col[k];
-      if (j <= i) continue;
+      if (both && j <= i) continue;
       const double cc = ci * c[j];
       if (cc == 0.0) continue;
       rdm_accumulate(R, n, ki, V[j], cc);
@@ -432,9 +437,9 @@ extern "C" hci_status hci_rdm12(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
     HCI_TRY(direct_rdm(ctx, ci, R));   // connections searched again, one orientation each
   else
     HCI_LAUNCH(k_rdm_offdiag, ctx->nsm * 8, R_WARPS * 32, 0, st)(n, bp<ulonglong2>(ctx->graph.keys_int), nV, ci,
-                                                           bp<int64_t>(ctx->graph.rowptr),
-                                                           bp<int64_t>(ctx->graph.rowstart),
-                                                           bp<int32_t>(ctx->graph.col), R, queue);
+                                                                 bp<int64_t>(ctx->graph.rowptr),
+                                                                 bp<int64_t>(ctx->graph.rowstart), ctx->graph.tab(),
+                                                                 ctx->graph.half ? 0 : 1, R, queue);
   HCI_LAUNCH(k_rdm_finish, grid_for((int64_t)n4, 256, ctx->nsm * 8), 256, 0, st)(n, R, rdm1, rdm2, 1);
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_RDM);

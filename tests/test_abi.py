@@ -70,8 +70,8 @@ def test_binding_constants_match_header():
     assert ev["HCI_ST_COUNT"] == len(_abi.STATS)
     for i, name in enumerate(_abi.STATS):
         assert ev["HCI_ST_" + name.upper()] == i, name
-    assert (ev["HCI_SIGMA_AUTO"], ev["HCI_SIGMA_STORED"], ev["HCI_SIGMA_DIRECT"]) == \
-        (_abi.SIGMA_AUTO, _abi.SIGMA_STORED, _abi.SIGMA_DIRECT)
+    assert (ev["HCI_SIGMA_AUTO"], ev["HCI_SIGMA_STORED"], ev["HCI_SIGMA_DIRECT"], ev["HCI_SIGMA_HALF"]) == \
+        (_abi.SIGMA_AUTO, _abi.SIGMA_STORED, _abi.SIGMA_DIRECT, _abi.SIGMA_HALF)
     assert ev["HCI_PH_COUNT"] == len(_abi.PHASES)
     for i, name in enumerate(_abi.PHASES):
         assert ev["HCI_PH_" + name.upper()] == i, name

@@ -329,8 +329,9 @@ def test_incremental_graph_row_beyond_scratch(pkg):
     """A new row longer than the row search's per-warp scratch (32768
     entries): the aufbau determinant of 26 orbitals with 13 + 13 electrons
     joins a space of all its single and double excitations (41067 of them)
-    in an incremental update; its row is filled by the second search.  That
-    row of H c and sampled others equal the oracle's."""
+    in an incremental update; its stored row (the connections to every
+    earlier determinant) is filled by the second search.  That row of H c
+    and sampled others equal the oracle's."""
     norb, ne = 26, 13
     inst = hi.random_tiny(norb, ne, ne, 31)
     a0 = b0 = (1 << ne) - 1
@@ -344,7 +345,7 @@ def test_incremental_graph_row_beyond_scratch(pkg):
     exc = np.array(sorted(exc), dtype=np.uint64)
     full = np.array(sorted([tuple(r) for r in exc.tolist()] + [(a0, b0)]), dtype=np.uint64)
     rng = np.random.default_rng(5)
-    first = exc[np.sort(rng.choice(len(exc), len(exc) // 2, replace=False))]
+    first = exc
     c = hi.random_vector(len(full), seed=6)
     i0 = int(np.nonzero((full[:, 0] == a0) & (full[:, 1] == b0))[0][0])
     rows = np.unique(np.concatenate([[i0], rng.choice(len(full), 64, replace=False)]))
