@@ -11,6 +11,7 @@
 namespace {
 
 constexpr int MAXSUB = 24;          // subspace size before restart (<= 32)
+constexpr int DAV_KEEP = 4;         // Ritz vectors kept for the next, grown space
 constexpr int LDG = 32;             // leading dimension of the subspace matrix
 constexpr int DBLOCK = 256;
 
@@ -19,6 +20,7 @@ struct DavDev {
   double Qp[LDG * LDG];   // eigenvectors of the previous subspace matrix (kq x kq)
   double y[LDG];
   double dots[LDG];
+  double ev[LDG];         // eigenvalues of the subspace matrix (columns of Qp)
   double theta;
   double nrm2;
   double ols[4];          // |r|^2, x . M^-1 r, x . M^-1 x (Olsen correction)
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(JW * 32) k_jacobi(DavDev* d, int k) {
   if (w == 0 && l < LDG) d->y[l] = (l < k) ? Q[l][mi] : 0.0;
   if (l < k)
     for (int j = w; j < k; j += JW) d->Qp[l * LDG + j] = Q[l][j];
+  if (w == 0 && l < k) d->ev[l] = A[l][l];
   if (threadIdx.x == 0) d->kq = k;
 }
 
@@ -260,6 +263,52 @@ __global__ void __launch_bounds__(DBLOCK) k_ritz(const double* __restrict__ V, c
     double s = 0.0;
     for (int w = 0; w < DBLOCK / 32; ++w) s += red[threadIdx.x][w];
     partial[(int64_t)blockIdx.x * LDG + threadIdx.x] = s;
+  }
+}
+
+// The kk <= DAV_KEEP lowest Ritz vectors of the current subspace (ascending Ritz value)
+// and their H products: Qo[t] = sum_j Qp[j][o_t] V[j], Wo[t] likewise from W.
+__global__ void __launch_bounds__(DBLOCK) k_keep(const double* __restrict__ V, const double* __restrict__ W,
+                                                 int64_t ld, int k, const DavDev* __restrict__ d, int kk, int64_t n,
+                                                 double* __restrict__ Qo, double* __restrict__ Wo) {
+  __shared__ double ys[DAV_KEEP][LDG];
+  __shared__ int order[DAV_KEEP];
+  if (threadIdx.x == 0) {
+    bool used[LDG];
+    for (int j = 0; j < k; ++j) used[j] = false;
+    for (int t = 0; t < kk; ++t) {
+      int b = -1;
+      for (int j = 0; j < k; ++j)
+        if (!used[j] && (b < 0 || d->ev[j] < d->ev[b])) b = j;
+      used[b] = true;
+      order[t] = b;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * k; e += blockDim.x) {
+    const int t = e / k, j = e % k;
+    ys[t][j] = d->Qp[j * LDG + order[t]];
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double qv[DAV_KEEP], wv[DAV_KEEP];
+#pragma unroll
+    for (int t = 0; t < DAV_KEEP; ++t) { qv[t] = 0.0; wv[t] = 0.0; }
+    for (int j = 0; j < k; ++j) {
+      const double vj = V[(int64_t)j * ld + i], wj = W[(int64_t)j * ld + i];
+#pragma unroll
+      for (int t = 0; t < DAV_KEEP; ++t)
+        if (t < kk) {
+          qv[t] = fma(ys[t][j], vj, qv[t]);
+          wv[t] = fma(ys[t][j], wj, wv[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DAV_KEEP; ++t)
+      if (t < kk) {
+        Qo[(int64_t)t * ld + i] = qv[t];
+        Wo[(int64_t)t * ld + i] = wv[t];
+      }
   }
 }
 
@@ -428,18 +477,61 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   const double* diag = bp<double>(ctx->graph.diag);
   cudaStream_t st = ctx->st;
   HCI_CUDA(ctx, cudaMemsetAsync(D.d, 0, sizeof(DavDev), st));
-  // start vector, in the graph's internal order
-  HCI_TRY(to_internal(ctx, c_inout, D.V, 1));
-  HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
+  // A single-root run on the space the last one converged on, or on a space
+  // grown from it, starts from that run's lowest Ritz vectors (zero on the
+  // new determinants) with their H products: the old rows of those are
+  // unchanged and the new rows cost one pass over the new rows' entries per
+  // vector, so the warm start is taken when that is at most one product.
+  const Graph& G = ctx->graph;
+  DavKeep& K = ctx->dkeep;
+  const bool same = K.valid && K.epoch == G.epoch && K.nV == nV;
+  const bool grown = K.valid && !G.direct && G.parent == K.epoch && G.nold == K.nV &&
+                     (double)G.tail_entries * K.k <= (double)(G.nstored > 0 ? G.nstored : 1);
+  int kwarm = (m == 0 && (same || grown)) ? K.k : 0;
+  if (kwarm > 0) {
+    for (int j = 0; j < kwarm; ++j) {
+      double* vj = D.V + (int64_t)j * D.ld;
+      double* wj = D.W + (int64_t)j * D.ld;
+      HCI_CUDA(ctx, cudaMemcpyAsync(vj, bp<double>(K.Q) + (int64_t)j * K.ld, (size_t)K.nV * 8,
+                                    cudaMemcpyDeviceToDevice, st));
+      HCI_CUDA(ctx, cudaMemcpyAsync(wj, bp<double>(K.W) + (int64_t)j * K.ld, (size_t)K.nV * 8,
+                                    cudaMemcpyDeviceToDevice, st));
+      if (nV > K.nV) {
+        HCI_CUDA(ctx, cudaMemsetAsync(vj + K.nV, 0, (size_t)(nV - K.nV) * 8, st));
+        HCI_TRY(sigma_tail(ctx, K.nV, vj, wj));
+      }
+    }
+    for (int j = 0; j < kwarm; ++j) {
+      HCI_TRY(D.dots(D.V, j + 1, D.W + (int64_t)j * D.ld, D.d->dots));
+      HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, j);
+    }
+  }
+  // start vector, in the graph's internal order (after the kept vectors)
+  double* V0 = D.V + (int64_t)kwarm * D.ld;
+  HCI_TRY(to_internal(ctx, c_inout, V0, 1));
+  HCI_TRY(D.dots(V0, 1, V0, &D.d->nrm2));
   double nrm2 = 0.0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) {
-    HCI_CUDA(ctx, cudaMemsetAsync(D.V, 0, (size_t)nV * 8, st));
-    HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(D.V, diag, nV);
-    if (m > 0) HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(D.V, nV, 1e-2 / std::sqrt((double)nV));
+    HCI_CUDA(ctx, cudaMemsetAsync(V0, 0, (size_t)nV * 8, st));
+    HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(V0, diag, nV);
+    if (m > 0) HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(V0, nV, 1e-2 / std::sqrt((double)nV));
   } else {
-    HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.V, nV, 1.0 / std::sqrt(nrm2));
+    HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(V0, nV, 1.0 / std::sqrt(nrm2));
+  }
+  bool add_start = true;
+  if (kwarm > 0) {
+    // the start vector joins the kept ones only with what they do not span
+    for (int pass = 0; pass < 2; ++pass) {
+      HCI_TRY(D.dots(D.V, kwarm, V0, D.d->dots));
+      HCI_LAUNCH(k_orth, D.nblk, DBLOCK, 0, st)(D.V, D.ld, kwarm, D.d, V0, nV);
+    }
+    HCI_TRY(D.dots(V0, 1, V0, &D.d->nrm2));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    add_start = nrm2 > 1e-16;
+    if (add_start) HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(V0, nV, 1.0 / std::sqrt(nrm2));
   }
   if (m > 0) {
     // start orthogonal to the locked vectors (else the unit vector at the
@@ -460,10 +552,13 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
     }
     HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.V, nV, 1.0 / std::sqrt(nrm2));
   }
-  HCI_TRY(D.sigma(0));
-  HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots));
-  HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, 0);
-  int k = 1;
+  int k = kwarm;
+  if (add_start) {
+    HCI_TRY(D.sigma(k));
+    HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots));
+    HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, k);
+    ++k;
+  }
   bool converged = false;
   double theta = 0.0, rn = 0.0;
   int it = 0;
@@ -520,6 +615,19 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
     ++k;
   }
   if (iters) *iters = it + (converged ? 1 : 0);
+  // the lowest Ritz vectors for a later run on this space or a grown one
+  K.valid = false;
+  if (m == 0 && converged) {
+    const int kk = k < DAV_KEEP ? k : DAV_KEEP;
+    if (ensure_buf(ctx, K.Q, (size_t)D.ld * kk * 8) == HCI_OK && ensure_buf(ctx, K.W, (size_t)D.ld * kk * 8) == HCI_OK) {
+      HCI_LAUNCH(k_keep, D.nblk, DBLOCK, 0, st)(D.V, D.W, D.ld, k, D.d, kk, nV, bp<double>(K.Q), bp<double>(K.W));
+      K.valid = true;
+      K.epoch = G.epoch;
+      K.nV = nV;
+      K.ld = D.ld;
+      K.k = kk;
+    }
+  }
   // final vector: normalise, back to the caller's order, fix the phase
   // there (largest |c|, first sorted position on ties)
   HCI_TRY(D.dots(D.x, 1, D.x, &D.d->nrm2));

@@ -1107,6 +1107,29 @@ __global__ void __launch_bounds__(256, SIGMA_HALF_BLOCKS_PER_SM) k_sigma1_half(c
   }
 }
 
+// Rows r0 .. nV-1 of H c for a vector that vanishes on them (the rows a
+// space gained in its last extension): out[i] = sum of the row's stored
+// entries times c (both forms store every connection of such a row to an
+// earlier determinant in the row itself); one warp per row.
+__global__ void __launch_bounds__(256) k_sigma_tail(const int64_t* __restrict__ rowptr,
+                                                    const int64_t* __restrict__ rowstart,
+                                                    const __grid_constant__ SegTab T, int64_t r0, int64_t nV,
+                                                    const double* __restrict__ c, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = r0 + warp; i < nV; i += nwarps) {
+    const int64_t len = rowptr[i + 1] - rowptr[i];
+    const int32_t* col;
+    const double* val;
+    row_entries(T, rowstart[i], col, val);
+    double a = 0.0;
+    for (int64_t k = lane; k < len; k += 32) a = fma(__ldcs(val + k), c[__ldcs(col + k)], a);
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[i] = a;
+  }
+}
+
 // several vectors at once (one pass over the entries per 4 vectors); sigma
 // zeroed before the launch, as for k_sigma1
 __global__ void __launch_bounds__(256) k_sigma_half(const int64_t* __restrict__ rowptr,
@@ -1512,6 +1535,8 @@ static hci_status graph_build_half(hci_ctx* ctx, const uint64_t* keys, int64_t n
   G.nV = nV;
   G.nstored = nst;
   G.nnz = 2 * nst;
+  G.epoch += 1;
+  G.parent = -1;
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   G.valid = true;
   return HCI_OK;
@@ -1598,6 +1623,10 @@ static hci_status graph_extend_half(hci_ctx* ctx, const uint64_t* keys, int64_t 
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
   (void)hs;
+  G.parent = G.epoch;
+  G.epoch += 1;
+  G.nold = nold;
+  G.tail_entries = total;
   G.nV = nV;
   G.nstored += total;
   G.nnz = 2 * G.nstored;
@@ -1668,6 +1697,8 @@ static hci_status graph_build_full(hci_ctx* ctx, const uint64_t* keys, int64_t n
   G.nV = nV;
   G.nnz = nnz;
   G.nstored = nnz;
+  G.epoch += 1;
+  G.parent = -1;
   G.pool_used = used;
   G.pool_cap = pool_entries(G);
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
@@ -1834,6 +1865,10 @@ static hci_status graph_extend_full(hci_ctx* ctx, const uint64_t* keys, int64_t 
   HCI_TRY(compute_diag(ctx, nnew, bp<ulonglong2>(G.keys_int) + nold, bp<double>(G.diag) + nold));
   prof_toc(ctx, HCI_PH_GRAPH);
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  G.parent = G.epoch;
+  G.epoch += 1;
+  G.tail_entries = nnzN;
+  G.nold = nold;
   G.nV = nV;
   G.nnz = nnz;
   G.nstored = nnz;
@@ -1867,6 +1902,8 @@ static hci_status graph_build_direct(hci_ctx* ctx, const uint64_t* keys, int64_t
   G.nV = nV;
   G.nnz = -1;   // counted by the first direct sigma
   G.direct = true;
+  G.epoch += 1;
+  G.parent = -1;
   ctx->st_counts[HCI_ST_GRAPH_BUILDS] += 1;
   G.valid = true;
   return HCI_OK;
@@ -2014,6 +2051,15 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
   }
   HCI_CUDA(ctx, cudaGetLastError());
   prof_toc(ctx, HCI_PH_SIGMA);
+  return HCI_OK;
+}
+
+hci_status sigma_tail(hci_ctx* ctx, int64_t r0, const double* c, double* out) {
+  Graph& G = ctx->graph;
+  if (G.direct || r0 >= G.nV) return HCI_OK;
+  HCI_LAUNCH(k_sigma_tail, grid_for((G.nV - r0) * 32, 256), 256, 0, ctx->st)(
+      bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), G.tab(), r0, G.nV, c, out);
+  HCI_CUDA(ctx, cudaGetLastError());
   return HCI_OK;
 }
 

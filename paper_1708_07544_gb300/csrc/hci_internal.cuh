@@ -63,6 +63,10 @@ struct Graph {
   DevBuf keys_int;           // the same keys by internal id (insertion order)
   DevBuf s2i, i2s;           // int32 maps sorted position <-> internal id
   bool direct = false;       // no stored rows: every traversal searches and evaluates the connections again
+  int64_t epoch = 0;         // increases with every build or extension
+  int64_t parent = -1;       // extension: the epoch it grew from (else -1)
+  int64_t nold = 0;          // extension: rows of the space it grew from (ids below nold)
+  int64_t tail_entries = 0;  // extension: stored entries in rows nold .. nV-1
   SegTab tab() const {
     SegTab t{};
     for (int k = 0; k < nseg; ++k) {
@@ -103,6 +107,16 @@ struct Prof {
   int64_t count[HCI_PH_COUNT] = {};
 };
 
+// Lowest Ritz vectors (and their H products) of the last single-root
+// Davidson, in the internal order of the graph epoch they belong to; a
+// Davidson on a space grown from that one starts from them.
+struct DavKeep {
+  bool valid = false;
+  int64_t epoch = -1, nV = 0, ld = 0;
+  int k = 0;
+  DevBuf Q, W;
+};
+
 struct hci_ctx {
   int n = 0, na = 0, nb = 0;
   double ecore = 0;
@@ -124,6 +138,7 @@ struct hci_ctx {
   bool direct_fallback = false;
   bool half_fallback = false;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
+  DavKeep dkeep;
   int nsm = 0;               // streaming multiprocessors of the context's device (grid sizes)
   int64_t fail_alloc_after = -1;  // HCI_FAIL_ALLOC_AFTER: allocations left before one is refused (-1: off)
   int64_t last_candidates = 0;
@@ -207,6 +222,9 @@ hci_status check_sorted(hci_ctx* ctx, const uint64_t* keys, int64_t n, int* ok_h
 hci_status graph_ensure(hci_ctx* ctx, const uint64_t* keys, int64_t nV);
 // sigma on vectors in internal order (rows/columns of the cached graph)
 hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec);
+// out[i] = sum_j H_ij c_j for the rows i in [r0, nV) of the cached stored
+// graph, off-diagonal entries only, for a c that vanishes on those rows
+hci_status sigma_tail(hci_ctx* ctx, int64_t r0, const double* c, double* out);
 struct RdmAcc;
 // off-diagonal RDM contributions of a direct graph (one orientation per pair)
 hci_status direct_rdm(hci_ctx* ctx, const double* c, const RdmAcc& R);
