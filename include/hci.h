@@ -116,7 +116,12 @@ hci_status hci_sigma(hci_ctx* ctx, const uint64_t* keys, int64_t nV, const doubl
  * the lowest diagonal element), the normalised eigenvector on exit, with
  * its largest-magnitude component (lowest index on ties) positive.
  * energy: host out (includes e_core).  Converged when ||H c - E c||_2 <= tol.
- * iters: host out (may be NULL).  Synchronises. */
+ * iters: host out (may be NULL).  Synchronises.
+ * The context keeps the four lowest Ritz vectors of a converged run (and
+ * their H products); a later run with a non-zero start vector, on the same
+ * space or on one grown from it by determinants appended since (the space
+ * of the next selection step), starts from them together with the start
+ * vector.  A zero start vector starts cold, from the unit vector alone. */
 hci_status hci_davidson(hci_ctx* ctx, const uint64_t* keys, int64_t nV, double* c_inout,
                         double* energy, double tol, int maxit, int* iters);
 

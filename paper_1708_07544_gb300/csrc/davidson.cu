@@ -484,10 +484,17 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   // vector, so the warm start is taken when that is at most one product.
   const Graph& G = ctx->graph;
   DavKeep& K = ctx->dkeep;
+  // A zero start vector asks for a cold start: the kept vectors are not used.
+  double c0n2 = 0.0;
+  {
+    HCI_TRY(D.dots(c_inout, 1, c_inout, &D.d->nrm2));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&c0n2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  }
   const bool same = K.valid && K.epoch == G.epoch && K.nV == nV;
   const bool grown = K.valid && !G.direct && G.parent == K.epoch && G.nold == K.nV &&
                      (double)G.tail_entries * K.k <= (double)(G.nstored > 0 ? G.nstored : 1);
-  int kwarm = (m == 0 && (same || grown)) ? K.k : 0;
+  int kwarm = (m == 0 && c0n2 > 0.0 && (same || grown)) ? K.k : 0;
   if (kwarm > 0) {
     for (int j = 0; j < kwarm; ++j) {
       double* vj = D.V + (int64_t)j * D.ld;

@@ -106,20 +106,28 @@ class HCIEnergy(torch.autograd.Function):
     """E(h, eri, kappa) = variational HCI energy of the rotated integrals.
 
     forward: U = exp(kappa), h' = U^T h U, eri' = U^4 eri, variational HCI
-    on (h', eri') -> E; the selected space V is saved.
-    backward: c is recomputed by Davidson on the saved V (not stored), the
-    RDMs give dE/dh' = rdm1 and dE/deri' = rdm2/2 (dE/dc = 0 at the
-    variational minimum), and the rotation's adjoint returns dE/dh, dE/deri
-    and dE/dkappa for every entry of the full kappa matrix.
+    on (h', eri') -> E; the selected space V and the solver context (its
+    integrals and connection graph, not the CI vector) are kept for the
+    backward.
+    backward: c is recomputed by a cold-started Davidson on the saved V
+    (the CI vector is not stored), the RDMs give dE/dh' = rdm1 and
+    dE/deri' = rdm2/2 (dE/dc = 0 at the variational minimum), and the
+    rotation's adjoint returns dE/dh, dE/deri and dE/dkappa for every entry
+    of the full kappa matrix.
     """
 
     @staticmethod
     def forward(ctx, h, eri, kappa, nalpha, nbeta, e_core, eps1, max_iter=30, dav_tol=1e-10):
         n = h.shape[0]
         _, h2, e2 = _abi.hci_rotate(kappa, h, eri)
-        with HCISolver(n, nalpha, nbeta, h2, e2, e_core) as s:
+        s = HCISolver(n, nalpha, nbeta, h2, e2, e_core)
+        try:
             out = s.solve(eps1, max_iter, dav_tol)
+        except Exception:
+            s.close()
+            raise
         ctx.save_for_backward(h, eri, kappa, out["keys"])
+        ctx.solver = s
         ctx.cfg = (n, nalpha, nbeta, e_core, dav_tol)
         ctx.nV = out["keys"].shape[0]
         return torch.tensor(out["E"], dtype=torch.float64, device=h.device)
@@ -128,10 +136,17 @@ class HCIEnergy(torch.autograd.Function):
     def backward(ctx, gE):
         h, eri, kappa, keys = ctx.saved_tensors
         n, na, nb, e_core, tol = ctx.cfg
-        _, h2, e2 = _abi.hci_rotate(kappa, h, eri)
-        with HCISolver(n, na, nb, h2, e2, e_core) as s:
-            _, c, _ = s.davidson(keys, None, tol)
+        s = ctx.solver
+        ctx.solver = None
+        if s is None:
+            # a second backward through the same graph: a fresh context
+            _, h2, e2 = _abi.hci_rotate(kappa, h, eri)
+            s = HCISolver(n, na, nb, h2, e2, e_core)
+        try:
+            _, c, _ = s.davidson(keys, None, tol)          # zero start: cold, c recomputed
             r1, r2 = s.rdm12(keys, c)
+        finally:
+            s.close()
         dh, de, dk = _abi.hci_rotate_backward(kappa, h, eri, r1, r2)
         g = gE.to(torch.float64)
         return g * dh, g * de, g * dk, None, None, None, None, None, None

@@ -273,6 +273,32 @@ def test_autograd_gradient_vs_oracle_and_fd(pkg):
         assert abs(fd - an) < 1e-7, (p, q, fd, an)
 
 
+def test_autograd_backward_twice_and_warm_start(pkg):
+    """The backward reuses the forward's context (graph kept, CI vector
+    recomputed by a cold Davidson); a second backward through a retained
+    graph gives the same gradient from a fresh context.  A Davidson on the
+    converged space with the converged start vector finishes at once (its
+    kept Ritz vectors span the answer), and from a zero start it starts
+    cold and reaches the same energy."""
+    inst = hi.df_instance(8, 32, seed=11, name="df8")
+    kap = hi.random_kappa(8, seed=12, sigma=0.05)
+    h = torch.tensor(inst.h).cuda()
+    eri = torch.tensor(inst.eri).cuda()
+    k = torch.tensor(kap).cuda().requires_grad_(True)
+    E = pkg.HCIEnergy.apply(h, eri, k, inst.nalpha, inst.nbeta, 0.0, 1e-3)
+    (g1,) = torch.autograd.grad(E, k, retain_graph=True)
+    (g2,) = torch.autograd.grad(E, k)
+    assert torch.max(torch.abs(g1 - g2)).item() < 1e-10
+    _, h2, e2 = pkg.hci_rotate(k.detach(), h, eri)
+    with pkg.HCISolver(8, inst.nalpha, inst.nbeta, h2, e2, 0.0) as s:
+        out = s.solve(1e-3, dav_tol=1e-10)
+        e_warm, c_warm, it_warm = s.davidson(out["keys"], out["c"], tol=1e-10)
+        e_cold, c_cold, it_cold = s.davidson(out["keys"], None, tol=1e-10)
+    assert it_warm == 1 and it_cold > 3
+    assert abs(e_warm - out["E"]) < 1e-12 and abs(e_cold - out["E"]) < 1e-9
+    assert torch.max(torch.abs(c_cold - out["c"])).item() < 1e-7
+
+
 def test_capacity_error_reports_required_size(pkg):
     inst = hi.ppp_polyene(8)
     k0 = oracle.aufbau(4, 4)
