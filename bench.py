@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--pt2-reps", type=int, default=2)
     ap.add_argument("--direct-reps", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1, help="also time the 64-instance batched solve")
+    ap.add_argument("--large", type=int, default=1,
+                    help="also time one solve + RDMs of the ~1e7-determinant (44e,44o) space")
     return ap.parse_args()
 
 
@@ -436,6 +438,49 @@ def gpu_arm(args):
                  "tuning_s": {str(k): round(v, 4) for k, v in tuned.items()},
                  "includes": "solve + 1/2-RDM per instance"}
 
+    # the ~1e7-determinant (44e,44o) space (Fe(P)-sized, Sec. V.C): one
+    # solve + RDMs through the same public API, the graph form chosen by
+    # HCI_SIGMA_AUTO (both orientations, one orientation, or direct, as
+    # device memory allows)
+    large = {}
+    if args.large:
+        linst = hi.df_44o_large()
+        lh = torch.tensor(linst.h, device=dev)
+        leri = torch.tensor(linst.eri, device=dev)
+        _, lh2, le2 = _abi.hci_rotate(k_d, lh, leri)
+        sl = pkg.HCISolver(n, linst.nalpha, linst.nbeta, lh2, le2, linst.e_core)
+        try:
+            sl.profile(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lk, lc, lE, lit = _abi.hci_solve(sl.ctx, eps1, 30, DAV_TOL, DAV_MAXIT, 1 << 25, device=dev)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            sl.rdm12(lk, lc)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            ltm = sl.timers()
+            lst = sl.stats()
+            lsig = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                a0 = time.perf_counter()
+                sl.sigma(lk, lc)
+                torch.cuda.synchronize()
+                lsig.append(time.perf_counter() - a0)
+            lnV = int(lk.shape[0])
+            form = "direct" if lst["sigma_direct"] else ("one orientation" if lst["graph_half"] else "both orientations")
+            lnnz = lst["graph_nnz"]
+            large = {"workload": f"synthetic DF (44e,44o) at {hi.DF44_LARGE_SCALE_FACTOR} of the survey's scale, eps1=1e-4",
+                     "nV": lnV, "E": lE, "selections": lit, "solve_s": round(t1 - t0, 3), "rdm_s": round(t2 - t1, 3),
+                     "graph_form": form, "graph_nnz": lnnz, "sigma_calls": lst["sigma_calls"],
+                     "sigma_ms": round(1e3 * min(lsig), 2),
+                     "hc_connections_per_s": (lnnz + lnV) / min(lsig),
+                     "stored_bytes": 6 * lnnz if lst["graph_half"] else None,
+                     "phases_ms": {k: round(v[0], 1) for k, v in ltm.items() if v[1]}}
+        finally:
+            sl.close()
+
     out = None
     if rank == 0:
         value = aggregate_seconds(ms_step, world)
@@ -472,6 +517,7 @@ def gpu_arm(args):
             "pt2": pt2,
             "sigma_direct": direct,
             "batch": batch,
+            "large": large,
             "e2e": {"value": round(aggregate_seconds(e2e_step, world), 6), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

@@ -254,6 +254,8 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
     } else {
       ctx->nsm = hci_nsm();
     }
+    size_t fr = 0, tot = 0;
+    ctx->mem_total = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? tot : ((size_t)64 << 30);
     cudaGetLastError();
   }
   ctx->n = norb;

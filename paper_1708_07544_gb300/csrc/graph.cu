@@ -1379,11 +1379,13 @@ static hci_status stage_search(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t*
 }
 
 // Columns of the rows of stage_search written to col (row q at inc.rpN[q]):
-// staged rows copied, the rows left searched again at their offsets.
+// staged rows copied, the rows left searched again at their offsets (left <
+// 0: no row was staged, all are searched again).
 static hci_status stage_place(hci_ctx* ctx, GraphArgs& A, int64_t left, int32_t* col) {
   IncScratch& S = ctx->inc;
   cudaStream_t st = ctx->st;
   const int64_t nrows = A.nrows;
+  if (left < 0) return rows_fill(ctx, A, bp<int64_t>(S.rpN), col, nullptr);   // counted, not staged
   HCI_LAUNCH(k_copy_staged, grid_for(nrows * 32, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN), nrows,
                                                                     bp<int32_t>(S.stage), col);
   HCI_CUDA(ctx, cudaGetLastError());
@@ -1459,7 +1461,9 @@ static hci_status seg_alloc(hci_ctx* ctx, int64_t entries, int* seg) {
 
 // The new rows listed in A searched once (stage_search), the staging space
 // sized from the mean length of a strided sample of them (the old rows'
-// lengths say little when the space grows many-fold).
+// lengths say little when the space grows many-fold).  When that space would
+// exceed an eighth of device memory the rows are only counted here (*left =
+// -1) and stage_place searches them a second time, straight into place.
 static hci_status stage_new_rows(hci_ctx* ctx, GraphArgs& A, int64_t nnew, int64_t nV, int64_t* total, int64_t* left) {
   IncScratch& S = ctx->inc;
   cudaStream_t st = ctx->st;
@@ -1483,6 +1487,30 @@ static hci_status stage_new_rows(hci_ctx* ctx, GraphArgs& A, int64_t nnew, int64
   const double mean = ns > 0 ? sum / (double)ns : 0.0;
   const double want = 1.5 * (double)nnew * mean;
   const int64_t est = (int64_t)std::min((double)nnew * (double)nV, want) + ((int64_t)1 << 22);
+  {
+    // a graph that cannot fit device memory is refused before the search:
+    // both orientations add the new rows, their transposes and slack to the
+    // pool, one orientation adds the new rows
+    const Graph& G = ctx->graph;
+    const double rows = (double)nnew * mean;
+    const double need = G.half ? (double)G.nstored + rows : (double)G.pool_used + 2.5 * rows;
+    if (need * 12.0 > 0.9 * (double)ctx->mem_total)
+      return hci_fail(ctx, HCI_ERR_NOMEM, "graph: about %.3g bytes of stored connections would exceed device memory",
+                      need * 12.0);
+  }
+  if ((double)est * 4.0 > (double)ctx->mem_total / 8.0) {
+    // a staging buffer this large would crowd out the stored rows: count
+    // the rows first and let stage_place search them again into place
+    int64_t* dtot = reinterpret_cast<int64_t*>(bp<char>(ctx->s_counter) + 40);
+    HCI_TRY(rows_count(ctx, A, S.cnt));
+    HCI_TRY(ensure_buf(ctx, S.rpN, (size_t)(nnew + 1) * 8));
+    HCI_TRY(scan_i64(ctx, bp<int64_t>(S.cnt), bp<int64_t>(S.rpN), nnew, dtot));
+    HCI_LAUNCH(k_store_at, 1, 1, 0, st)(bp<int64_t>(S.rpN), nnew, dtot);
+    hci_status hs = HCI_OK;
+    *total = read_i64(ctx, dtot, &hs);
+    *left = -1;
+    return hs;
+  }
   return stage_search(ctx, A, est, total, left);
 }
 

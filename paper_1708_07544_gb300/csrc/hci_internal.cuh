@@ -140,6 +140,7 @@ struct hci_ctx {
   DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
   DavKeep dkeep;
   int nsm = 0;               // streaming multiprocessors of the context's device (grid sizes)
+  size_t mem_total = 0;      // device memory of the context's device (bytes)
   int64_t fail_alloc_after = -1;  // HCI_FAIL_ALLOC_AFTER: allocations left before one is refused (-1: off)
   int64_t last_candidates = 0;
   int64_t st_counts[HCI_ST_COUNT] = {};
