@@ -31,6 +31,14 @@ What each function follows:
                      exact expectation over every draw sequence), the draws
                      made by ``philox4x64`` (pinned against numpy's Philox)
                      and an exact integer inverse CDF (``sample_draws``).
+* ``hci_parity`` -- the variational stage restricted to states of one spin
+                     parity in the S_z = 0 sector (the singlet / triplet
+                     states of Sec. VI told apart by the spin-flip symmetry
+                     of the spin-free Hamiltonian): the space is closed under
+                     exchanging the alpha and beta strings, and the state is
+                     the lowest eigenvector of H in the subspace c(beta,
+                     alpha) = p c(alpha, beta) (``parity_ground_state``,
+                     pinned against Jordan-Wigner spectra sorted by S).
 * ``rotate`` / ``gradient`` -- vHCISCF gradient Eq. (vdedk2): the
                      derivative of the rotated integrals contracted with
                      the RDMs, chained through U = exp(kappa) (Sec. III.B).
@@ -470,6 +478,100 @@ def hci(inst, eps1, max_iter=30, verbose=False):
         keys, c = merge(keys, c, new)
         e, c = ground_state(P, keys, v0=c)
     return {"keys": keys, "c": c, "E": e, "history": history}
+
+
+# ----------------------------------------------------------------------------
+# spin parity in the S_z = 0 sector (spin-flip symmetry)
+# ----------------------------------------------------------------------------
+# The spin flip F exchanges a+_{p alpha} and a+_{p beta}.  With m = n_alpha =
+# n_beta, F |alpha, beta> = (-1)^(m m) |beta, alpha> = (-1)^m |beta, alpha>
+# (the m beta creators move past the m alpha ones), F commutes with the
+# spin-free H, and an eigenstate of total spin S has F = (-1)^(m + S).  So
+# the states of spin parity p = (-1)^S are the vectors with
+# c(beta, alpha) = p c(alpha, beta): even S (singlets, quintets) p = +1, odd S
+# (triplets) p = -1; a determinant with alpha = beta belongs to p = +1 only.
+
+def flip_keys(keys):
+    """(alpha, beta) -> (beta, alpha) for every determinant."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    return np.ascontiguousarray(keys[:, ::-1])
+
+
+def close_under_flip(keys):
+    """The sorted union of a key set and its spin-flipped partners."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    allk = np.unique(np.concatenate([keys, flip_keys(keys)]), axis=0)
+    return allk[np.lexsort((allk[:, 1], allk[:, 0]))]
+
+
+def parity_basis(keys, parity):
+    """Orthonormal basis (sparse nV x nb) of {c : c(b, a) = parity c(a, b)}
+    on a flip-closed V: (e_D + parity e_Dbar) / sqrt(2) per pair D != Dbar,
+    e_D for alpha = beta when parity = +1."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    index = {(int(a), int(b)): i for i, (a, b) in enumerate(keys.tolist())}
+    rows, cols, vals = [], [], []
+    nb = 0
+    for i, (a, b) in enumerate(keys.tolist()):
+        j = index.get((int(b), int(a)))
+        if j is None:
+            raise ValueError("space not closed under the spin flip")
+        if j == i:
+            if parity > 0:
+                rows.append(i); cols.append(nb); vals.append(1.0)
+                nb += 1
+        elif i < j:
+            r = 1.0 / np.sqrt(2.0)
+            rows += [i, j]; cols += [nb, nb]; vals += [r, parity * r]
+            nb += 1
+    return sp.csr_matrix((vals, (rows, cols)), shape=(len(keys), nb))
+
+
+def parity_ground_state(inst, keys, parity):
+    """Lowest eigenpair of H on a flip-closed V restricted to spin parity
+    `parity` (Eq. variational in that symmetry sector); c in the determinant
+    basis with the phase of fix_phase."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    B = parity_basis(keys, parity)
+    if B.shape[1] == 0:
+        raise ValueError("no state of this spin parity in V")
+    H = hamiltonian(inst, keys)
+    Hs = (B.T @ H @ B).tocsr()
+    if Hs.shape[0] <= 2500:
+        w, v = np.linalg.eigh(Hs.toarray())
+        e, y = float(w[0]), v[:, 0]
+    else:
+        w, v = spla.eigsh(Hs, k=1, which="SA", tol=0, ncv=min(Hs.shape[0], 40))
+        e, y = float(w[0]), v[:, 0]
+    c = B @ y
+    return e, fix_phase(c / np.linalg.norm(c))
+
+
+def hci_parity(inst, eps1, parity, max_iter=30):
+    """Variational HCI for the lowest state of spin parity `parity` in the
+    S_z = 0 sector (Sec. II.A with the sector of Sec. VI's singlet and
+    triplet states).  Reading: V^0 = {aufbau}, c^0 = [1] (the first
+    selection is made from the aufbau determinant whatever its parity);
+    each selection C^mu(eps1) of Eq. (criteria) is completed by the spin-flip
+    partners of its determinants, V^{mu+1} = V^mu + C^mu + F C^mu, and the
+    state on V^{mu+1} is the lowest eigenvector of spin parity `parity`;
+    stop when C^mu is empty."""
+    P = Problem.of(inst)
+    if P.nalpha != P.nbeta:
+        raise ValueError("spin parity needs n_alpha = n_beta")
+    keys = aufbau(P.nalpha, P.nbeta)
+    c = np.array([1.0])
+    e = None
+    for mu in range(max_iter):
+        new, _, _ = select(P, keys, c, eps1)
+        if len(new) == 0:
+            break
+        new = close_under_flip(new)
+        keys, _ = merge(keys, np.zeros(len(keys)), new)
+        e, c = parity_ground_state(P, keys, parity)
+    if e is None:
+        e, c = parity_ground_state(P, keys, parity)
+    return {"keys": keys, "c": c, "E": e}
 
 
 # ----------------------------------------------------------------------------
