@@ -174,6 +174,24 @@ hci_status hci_pt2(hci_ctx* ctx, double eps2, const uint64_t* keys, const double
 enum { HCI_SIGMA_AUTO = 0, HCI_SIGMA_STORED = 1, HCI_SIGMA_DIRECT = 2, HCI_SIGMA_HALF = 3 };
 hci_status hci_set_sigma_mode(hci_ctx* ctx, int mode, int64_t graph_budget);
 
+/* Spin parity of the states sought in the S_z = 0 sector (n_alpha =
+ * n_beta): the paper compares singlet and triplet states (Sec. VI), which
+ * in that sector differ by their symmetry under the spin flip F (alpha and
+ * beta strings exchanged; F |a, b> = (-1)^n_alpha |b, a>, and a state of
+ * total spin S has F = (-1)^(n_alpha + S)).  parity = +1: even S
+ * (singlets, quintets), -1: odd S (triplets), 0: no restriction (default).
+ * With a parity set, hci_select adds the flip partner of every selected
+ * determinant (so the space stays closed under F), and hci_davidson,
+ * hci_davidson_roots, hci_solve and hci_solve_roots return states with
+ * c(b, a) = parity c(a, b) (vectors projected on that sector; a zero start
+ * vector starts from the lowest diagonal determinant plus a small fixed
+ * hash, projected).  The first selection of hci_solve is made from the
+ * aufbau determinant with c = [1] whatever its parity.  Davidson needs a
+ * space closed under F (HCI_ERR_INVALID otherwise, or when it holds no
+ * state of the parity).  HCI_ERR_INVALID for parity outside {-1, 0, 1} or
+ * n_alpha != n_beta. */
+hci_status hci_set_spin_parity(hci_ctx* ctx, int parity);
+
 /* Semistochastic second-order correction (Sec. II.B, Eq. semistoc):
  *   E2(eps2) ~ E2^D(eps2_det) + mean_s [E2^S_s(eps2) - E2^S_s(eps2_det)],
  * E2^D the deterministic hci_pt2 value, and both stochastic terms of a

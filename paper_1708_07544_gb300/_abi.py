@@ -30,7 +30,7 @@ EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hc
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
            "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12", "hci_davidson_roots",
-           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode", "hci_spin_square", "hci_solve_from"]
+           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode", "hci_spin_square", "hci_solve_from", "hci_set_spin_parity"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -74,6 +74,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_rdm12.argtypes = [V, V, I64, V, V, V]
     L.hci_pt2.argtypes = [V, D, V, V, I64, D, I64, P(D), P(I64), V, V, V, V, V]
     L.hci_set_sigma_mode.argtypes = [V, I, I64]
+    L.hci_set_spin_parity.argtypes = [V, I]
     L.hci_spin_square.argtypes = [V, V, P(D)]
     L.hci_pt2_stochastic.argtypes = [V, V, V, I64, D, D, D, I64, I, ctypes.c_uint64, I64, V, V, V]
     L.hci_zvector.argtypes = [V, V, I64, V, D, V, V, D, I, P(I)]
@@ -215,6 +216,10 @@ def hci_pt2(ctx, keys, c, eps2, e0, max_pairs=0, norb=None, grad=False):
     if grad:
         out = out + (g,)
     return out
+
+
+def hci_set_spin_parity(ctx, parity):
+    _check(load().hci_set_spin_parity(ctx, int(parity)), ctx)
 
 
 def hci_spin_square(ctx, rdm2):

@@ -321,7 +321,7 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->inc.roff, &ctx->inc.ctl, &ctx->inc.left, &ctx->inc.samp,
                     &ctx->p2_vals, &ctx->p2_vals2, &ctx->p2_ref,
                     &ctx->p2_src, &ctx->p2_src2, &ctx->p2_d, &ctx->p2_dd,
-                    &ctx->d_zv, &ctx->d_rel, &ctx->d_lock, &ctx->ss_w, &ctx->ss_draw,
+                    &ctx->d_zv, &ctx->d_rel, &ctx->d_lock, &ctx->d_partner, &ctx->dkeep.Q, &ctx->dkeep.W, &ctx->ss_w, &ctx->ss_draw,
                     &ctx->ss_draw2, &ctx->ss_run, &ctx->ss_src};
   for (int k = 0; k < GRAPH_MAXSEG; ++k) {
     free_buf(st, ctx->graph.seg_col[k]);

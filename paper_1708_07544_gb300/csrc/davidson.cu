@@ -312,6 +312,49 @@ __global__ void __launch_bounds__(DBLOCK) k_keep(const double* __restrict__ V, c
   }
 }
 
+// Spin-flip partners (S_z = 0 sector): partner[i] = internal id of the
+// determinant with the alpha and beta strings of internal id i exchanged;
+// *missing counts determinants whose partner is not in the space.
+__global__ void k_flip_partner(const ulonglong2* __restrict__ keys_int, const ulonglong2* __restrict__ sorted,
+                               const int32_t* __restrict__ s2i, int64_t n, int32_t* __restrict__ partner,
+                               unsigned long long* __restrict__ missing) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 k = keys_int[i];
+    const ulonglong2 f = make_ulonglong2(k.y, k.x);
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      const ulonglong2 m = sorted[mid];
+      if (m.x < f.x || (m.x == f.x && m.y < f.y)) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < n && sorted[lo].x == f.x && sorted[lo].y == f.y) {
+      partner[i] = s2i[lo];
+    } else {
+      partner[i] = -1;
+      atomicAdd(missing, 1ull);
+    }
+  }
+}
+
+// Projection on spin parity p: v_i <- (v_i + p v_partner(i)) / 2, each pair
+// once (from its lower id, both entries written); alpha = beta determinants
+// keep v_i for p = +1 and vanish for p = -1.  The two entries of a pair end
+// up with exactly equal magnitudes.
+__global__ void k_parity_project(double* __restrict__ v, const int32_t* __restrict__ partner, int64_t n, double p) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = partner[i];
+    if (j == i) {
+      if (p < 0.0) v[i] = 0.0;
+    } else if (j > i) {
+      const double a = v[i], b = v[j];
+      const double s = 0.5 * (a + p * b);
+      v[i] = s;
+      v[j] = p * s;
+    }
+  }
+}
+
 // Olsen correction: t = M^-1 (r - eps x) with eps = (x M^-1 r) / (x M^-1 x),
 // which makes the correction orthogonal to x to first order.
 __global__ void __launch_bounds__(DBLOCK) k_olsen(const DavDev* __restrict__ d, const double* __restrict__ diag,
@@ -446,6 +489,33 @@ struct Dav {
 
 }  // namespace
 
+// Spin-flip partners of the cached space (built once per graph epoch);
+// HCI_ERR_INVALID when the space is not closed under the flip.
+static hci_status parity_prepare(hci_ctx* ctx, int64_t nV) {
+  const Graph& G = ctx->graph;
+  if (ctx->partner_epoch == G.epoch && ctx->d_partner.bytes >= (size_t)nV * 4) return HCI_OK;
+  HCI_TRY(ensure_buf(ctx, ctx->d_partner, (size_t)nV * 4));
+  HCI_TRY(ensure_buf(ctx, ctx->s_counter, 64));
+  unsigned long long* miss = reinterpret_cast<unsigned long long*>(bp<char>(ctx->s_counter) + 8);
+  HCI_CUDA(ctx, cudaMemsetAsync(miss, 0, 8, ctx->st));
+  HCI_LAUNCH(k_flip_partner, grid_for(nV, 256), 256, 0, ctx->st)(
+      reinterpret_cast<const ulonglong2*>(G.keys_int.p), reinterpret_cast<const ulonglong2*>(G.keys.p),
+      reinterpret_cast<const int32_t*>(G.s2i.p), nV, bp<int32_t>(ctx->d_partner), miss);
+  HCI_CUDA(ctx, cudaGetLastError());
+  unsigned long long h = 0;
+  HCI_CUDA(ctx, cudaMemcpyAsync(&h, miss, 8, cudaMemcpyDeviceToHost, ctx->st));
+  HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
+  if (h) return hci_fail(ctx, HCI_ERR_INVALID, "spin parity: %llu determinants of V lack their spin-flip partner", h);
+  ctx->partner_epoch = G.epoch;
+  return HCI_OK;
+}
+
+static void parity_project(hci_ctx* ctx, double* v, int64_t nV, int nblk) {
+  if (ctx->spin_parity == 0) return;
+  HCI_LAUNCH(k_parity_project, nblk, DBLOCK, 0, ctx->st)(v, bp<int32_t>(ctx->d_partner), nV,
+                                                        (double)ctx->spin_parity);
+}
+
 // The Davidson loop; with m > 0 locked vectors L (orthonormal, internal
 // order, leading dimension (nV + 31) & ~31) the start vector and every
 // correction are kept orthogonal to them, so the iteration converges to the
@@ -455,6 +525,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
                                 double tol, int maxit, int* iters, const double* L, int m) {
   if (iters) *iters = 0;
   HCI_TRY(graph_ensure(ctx, keys, nV));
+  if (ctx->spin_parity != 0) HCI_TRY(parity_prepare(ctx, nV));
   prof_tic(ctx, HCI_PH_DAVIDSON);
   Dav D;
   D.ctx = ctx;
@@ -520,10 +591,28 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   double nrm2 = 0.0;
   HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
   HCI_CUDA(ctx, cudaStreamSynchronize(st));
+  if (ctx->spin_parity != 0 && nrm2 > 0.0 && std::isfinite(nrm2)) {
+    // the start vector's part of the requested spin parity
+    parity_project(ctx, V0, nV, D.nblk);
+    HCI_TRY(D.dots(V0, 1, V0, &D.d->nrm2));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaStreamSynchronize(st));
+    if (!(nrm2 > 1e-20)) nrm2 = 0.0;
+  }
   if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) {
     HCI_CUDA(ctx, cudaMemsetAsync(V0, 0, (size_t)nV * 8, st));
     HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(V0, diag, nV);
-    if (m > 0) HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(V0, nV, 1e-2 / std::sqrt((double)nV));
+    if (m > 0 || ctx->spin_parity != 0)
+      HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(V0, nV, 1e-2 / std::sqrt((double)nV));
+    if (ctx->spin_parity != 0) {
+      parity_project(ctx, V0, nV, D.nblk);
+      HCI_TRY(D.dots(V0, 1, V0, &D.d->nrm2));
+      HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
+      HCI_CUDA(ctx, cudaStreamSynchronize(st));
+      if (!(nrm2 > 1e-20)) return hci_fail(ctx, HCI_ERR_INVALID, "hci_davidson: no state of spin parity %+d in V",
+                                           ctx->spin_parity);
+      HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(V0, nV, 1.0 / std::sqrt(nrm2));
+    }
   } else {
     HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(V0, nV, 1.0 / std::sqrt(nrm2));
   }
@@ -556,6 +645,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
       HCI_CUDA(ctx, cudaMemsetAsync(D.V, 0, (size_t)nV * 8, st));
       HCI_LAUNCH(k_unit_min_diag, 1, 1024, 0, st)(D.V, diag, nV);
       HCI_LAUNCH(k_add_hash, D.nblk, DBLOCK, 0, st)(D.V, nV, 1e-2 / std::sqrt((double)nV));
+      parity_project(ctx, D.V, nV, D.nblk);
     }
     HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.V, nV, 1.0 / std::sqrt(nrm2));
   }
@@ -597,6 +687,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
       k = 1;
     }
     HCI_LAUNCH(k_olsen, D.nblk, DBLOCK, 0, st)(D.d, diag, nV, D.x, D.t);
+    parity_project(ctx, D.t, nV, D.nblk);
     // orthogonalise the correction twice, normalise
     for (int pass = 0; pass < 2; ++pass) {
       HCI_TRY(D.dots(D.V, k, D.t, D.d->dots));
@@ -636,7 +727,10 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
     }
   }
   // final vector: normalise, back to the caller's order, fix the phase
-  // there (largest |c|, first sorted position on ties)
+  // there (largest |c|, first sorted position on ties); with a spin parity
+  // projected once more, so that the entries of a flip pair have equal
+  // magnitudes exactly
+  parity_project(ctx, D.x, nV, D.nblk);
   HCI_TRY(D.dots(D.x, 1, D.x, &D.d->nrm2));
   HCI_LAUNCH(k_scale_by, D.nblk, DBLOCK, 0, st)(D.x, nullptr, nV, &D.d->nrm2);
   HCI_TRY(to_sorted(ctx, D.x, c_inout, 1));
@@ -650,6 +744,17 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   if (!converged && rn > tol)
     return hci_fail(ctx, HCI_ERR_NOT_CONVERGED, "hci_davidson: residual %.3e > tol %.3e after %d iterations", rn, tol,
                     it);
+  return HCI_OK;
+}
+
+extern "C" hci_status hci_set_spin_parity(hci_ctx* ctx, int parity) {
+  if (!ctx) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_set_spin_parity: null context");
+  if (parity < -1 || parity > 1) return hci_fail(ctx, HCI_ERR_INVALID, "hci_set_spin_parity: parity %d not in {-1, 0, 1}", parity);
+  if (parity != 0 && ctx->na != ctx->nb)
+    return hci_fail(ctx, HCI_ERR_INVALID, "hci_set_spin_parity: needs n_alpha = n_beta (S_z = 0), got %d and %d", ctx->na,
+                    ctx->nb);
+  if (parity != ctx->spin_parity) ctx->dkeep.valid = false;
+  ctx->spin_parity = parity;
   return HCI_OK;
 }
 

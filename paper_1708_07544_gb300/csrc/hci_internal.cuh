@@ -139,6 +139,9 @@ struct hci_ctx {
   bool half_fallback = false;
   DevBuf d_vb, d_wb, d_diag, d_small, d_part, d_perm, d_zv, d_rel, d_lock;
   DavKeep dkeep;
+  int spin_parity = 0;             // 0, or +1 / -1: states with c(beta,alpha) = p c(alpha,beta) (S_z = 0)
+  DevBuf d_partner;                // int32 spin-flip partner of each internal id
+  int64_t partner_epoch = -1;      // graph epoch d_partner belongs to
   int nsm = 0;               // streaming multiprocessors of the context's device (grid sizes)
   size_t mem_total = 0;      // device memory of the context's device (bytes)
   int64_t fail_alloc_after = -1;  // HCI_FAIL_ALLOC_AFTER: allocations left before one is refused (-1: off)

@@ -406,6 +406,14 @@ __device__ __forceinline__ int64_t lower_bound(const ulonglong2* __restrict__ ar
 }
 
 // flag = first of its run in the sorted candidates and not already in V
+// c[m + t] = c[t] with the alpha and beta strings exchanged
+__global__ void k_flip_append(ulonglong2* __restrict__ c, int64_t m) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const ulonglong2 k = c[t];
+    c[m + t] = make_ulonglong2(k.y, k.x);
+  }
+}
+
 __global__ void k_flag_new(const ulonglong2* __restrict__ cand, int64_t m, const ulonglong2* __restrict__ V,
                            int64_t nV, int64_t* __restrict__ flag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -539,6 +547,15 @@ extern "C" hci_status hci_select(hci_ctx* ctx, double eps1, const uint64_t* keys
     int64_t m2 = 0;
     HCI_TRY(run_walk(ctx, A, &m2));
     if (m2 != m) return hci_fail(ctx, HCI_ERR_CUDA, "hci_select: candidate count changed between runs");
+  }
+  if (ctx->spin_parity != 0 && m > 0) {
+    // spin parity: every selected determinant brings its spin-flip partner
+    HCI_TRY(ensure_buf(ctx, ctx->s_cand2, (size_t)2 * m * 16));
+    HCI_CUDA(ctx, cudaMemcpyAsync(ctx->s_cand2.p, ctx->s_cand.p, (size_t)m * 16, cudaMemcpyDeviceToDevice, ctx->st));
+    HCI_LAUNCH(k_flip_append, grid_for(m, 256), 256, 0, ctx->st)(bp<ulonglong2>(ctx->s_cand2), m);
+    HCI_CUDA(ctx, cudaGetLastError());
+    std::swap(ctx->s_cand, ctx->s_cand2);
+    m *= 2;
   }
   ctx->last_candidates = m;
   ctx->st_counts[HCI_ST_SELECT_CALLS] += 1;

@@ -65,9 +65,13 @@ static hci_status solve_core(hci_ctx* ctx, double eps1, int max_iter, double dav
     }
   } else {
     HCI_LAUNCH(k_aufbau, 1, 1, 0, st)(ctx->na, ctx->nb, bp<ulonglong2>(kb[0]), bp<double>(cb[0]));
-    s = hci_davidson(ctx, bp<uint64_t>(kb[0]), 1, bp<double>(cb[0]), &e, dav_tol, dav_maxit, &dav_it);
-    if (s != HCI_OK) { cleanup(); return s; }
-    have_e = true;
+    // the first selection starts from c = [1] on the aufbau determinant; with
+    // a spin parity that excludes it (odd, alpha = beta) V^0 holds no state
+    if (ctx->spin_parity == 0) {
+      s = hci_davidson(ctx, bp<uint64_t>(kb[0]), 1, bp<double>(cb[0]), &e, dav_tol, dav_maxit, &dav_it);
+      if (s != HCI_OK) { cleanup(); return s; }
+      have_e = true;
+    }
   }
   int mu = 0;
   for (; mu < max_iter; ++mu) {

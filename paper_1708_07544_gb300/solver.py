@@ -60,6 +60,10 @@ class HCISolver:
         """<S^2> of the state whose spin-summed 2-RDM is rdm2 (hci_rdm12)."""
         return _abi.hci_spin_square(self.ctx, rdm2)
 
+    def set_spin_parity(self, parity):
+        """+1: even total spin, -1: odd, 0: any (S_z = 0 only; hci_set_spin_parity)."""
+        _abi.hci_set_spin_parity(self.ctx, parity)
+
     def set_sigma_mode(self, mode, graph_budget=0):
         """_abi.SIGMA_AUTO / SIGMA_STORED / SIGMA_DIRECT (see hci_set_sigma_mode)."""
         _abi.hci_set_sigma_mode(self.ctx, mode, graph_budget)
