@@ -44,11 +44,12 @@ WORKLOADS = {
 
 # Work structure of one solve of each workload (selection source passes,
 # sigma row passes, sigma connection passes), as counted by the library's
-# own counters on GB300; the CPU reference scales its sampled per-row and
-# per-source costs by these to a whole solve.
+# own counters (hci_stats) in a bench run on GB300 at DAV_TOL; the reference
+# arm, which runs no GPU code, scales its sampled per-row and per-source
+# oracle costs by these.  The GPU arm's cpu_baseline uses the counters of its
+# own run instead, and each JSON line records the counts it used.
 WORK_PROFILE = {
-    "df44": {"select_sources": 18311266, "sigma_rows": 268173014, "sigma_nnz": 510006710052},
-    "pentacene22": {"select_sources": 3176006, "sigma_rows": 64715281, "sigma_nnz": 44604948696},
+    "df44": {"select_sources": 18311266, "sigma_rows": 256134997, "sigma_nnz": 488299005664},
 }
 
 DAV_TOL = 1e-10     # Davidson residual ||Hc - Ec||_2 at every selection (the parity tests' value)
@@ -611,7 +612,8 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "impl": "reference",
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl['desc']}"},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc,
+                             "work_counts": prof},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -630,7 +632,9 @@ def main():
         c_np = last["c"].cpu().numpy()
         est, threads, desc = oracle_sample(inst, WORKLOADS[args.workload]["eps1"], keys_np, c_np,
                                            args.cpu_seconds, out["work"])
-        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
+        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc,
+                               "work_counts": {k: out["work"][k] for k in ("select_sources", "sigma_rows",
+                                                                           "sigma_nnz")}}
     print(json.dumps(out))
 
 
