@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--pt2-reps", type=int, default=2)
     ap.add_argument("--direct-reps", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1, help="also time the 64-instance batched solve")
+    ap.add_argument("--sigma-mode", default="auto", choices=["auto", "stored", "half", "direct"],
+                    help="connection-graph form of the timed step and the sigma section (hci_set_sigma_mode)")
     ap.add_argument("--large", type=int, default=1,
                     help="also time one solve + RDMs of the ~1e7-determinant (44e,44o) space")
     return ap.parse_args()
@@ -212,11 +214,14 @@ def gpu_arm(args):
     eri_d = torch.tensor(inst.eri, device=dev)
     k_d = torch.tensor(kap, device=dev)
     cap = 1 << 22
+    sigma_mode = {"auto": _abi.SIGMA_AUTO, "stored": _abi.SIGMA_STORED, "half": _abi.SIGMA_HALF,
+                  "direct": _abi.SIGMA_DIRECT}[args.sigma_mode]
 
     def step(h_in, eri_in, k_in, record=None):
         U, h2, e2 = _abi.hci_rotate(k_in, h_in, eri_in)
         s = pkg.HCISolver(n, inst.nalpha, inst.nbeta, h2, e2, inst.e_core)
         try:
+            s.set_sigma_mode(sigma_mode)
             s.profile(True)
             keys, c, E, it = _abi.hci_solve(s.ctx, eps1, 30, DAV_TOL, DAV_MAXIT, cap, device=dev)
             r1, r2 = s.rdm12(keys, c)
@@ -296,6 +301,7 @@ def gpu_arm(args):
     last = rec
     U, h2, e2 = _abi.hci_rotate(k_d, h_d, eri_d)
     s = pkg.HCISolver(n, inst.nalpha, inst.nbeta, h2, e2, inst.e_core)
+    s.set_sigma_mode(sigma_mode)
     keys, c = last["keys"], last["c"]
     s.sigma(keys, c)                 # builds the graph
     s.timers()
@@ -374,7 +380,12 @@ def gpu_arm(args):
     sig_ms = tm["sigma"][0] / max(tm["sigma"][1], 1)
     nnz = st["graph_nnz"]
     nV = int(keys.shape[0])
-    sig_bytes = 12 * nnz + 40 * nV + 8
+    half = bool(st["graph_half"])
+    # algorithmic bytes of one product: 12 per stored entry (both
+    # orientations: one per connection; one orientation: one per pair) and
+    # 40 per row (row pointer, row start, diagonal, c_i, sigma_i)
+    sig_bytes = 12 * (nnz // 2 if half else nnz) + 40 * nV + 8
+    sig_kernel = "k_sigma1_half (one orientation, FP64 atomic scatter)" if half else "k_sigma1 (pooled-CSR FP64 H c)"
     sig_flops = 2 * (nnz + nV)
     peak, peak_kind = measured_peaks()
     fp64_tf, fp64_kind = fp64_peak_tflops(dev)
@@ -507,11 +518,11 @@ def gpu_arm(args):
             "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
             "phase_counts": {k: v[1] for k, v in phases.items()},
             "work": work,
-            "roofline": {"kernel": "k_sigma1 (pooled-CSR FP64 H c)", "bound": "alu", "achieved": round(achieved_tf, 4),
+            "roofline": {"kernel": sig_kernel, "bound": "alu", "achieved": round(achieved_tf, 4),
                          "peak": round(fp64_tf, 4), "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_tf, 4),
-                         "traffic": traffic_per_launch(nnz, nV), "peak_kind": fp64_kind,
+                         "traffic": None if half else traffic_per_launch(nnz, nV), "peak_kind": fp64_kind,
                          "flops_per_launch": sig_flops, "launch_ms": round(sig_ms, 4)},
-            "roofline_hbm": {"kernel": "k_sigma1", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "roofline_hbm": {"kernel": sig_kernel.split()[0], "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                              "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                              "bytes_per_launch": sig_bytes},
             "fwd_bwd": fb,

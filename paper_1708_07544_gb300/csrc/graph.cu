@@ -1046,10 +1046,10 @@ __device__ __forceinline__ void row_entries(const SegTab& T, int64_t rs, const i
 // row's sum is added atomically too, since other rows scatter into it at the
 // same time.  One warp per contiguous range of rows holding an equal share
 // of the entries, four (col, val, c[col]) loads per lane in flight, the entry
-// stream read with evict-first hints so that c and sigma stay in L2.  A
-// stored row holds ~10^3 entries on the full-size spaces, so its cross-lane
-// reduction (5 FP64 additions) is a small share of the 2 FP64 operations per
-// entry that bound the kernel (2 DFMA per clock per SM).
+// stream read with evict-first hints so that c and sigma stay in L2.  Rows
+// are summed four at a time, as in k_sigma1: the FP64 pipe (2 operations per
+// entry, 2 DFMA per clock per SM) bounds this kernel (80% busy on the
+// pentacene space), and stored rows are half as long as full ones.
 // blocks of k_sigma1_half per SM: all resident (64 registers, no spills), so
 // the equal shares of the entries run in one wave
 constexpr int SIGMA_HALF_BLOCKS_PER_SM = 4;
@@ -1073,37 +1073,56 @@ __global__ void __launch_bounds__(256, SIGMA_HALF_BLOCKS_PER_SM) k_sigma1_half(c
     while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (rowptr[mid] < x) lo = mid + 1; else hi = mid; }
     r1 = warp == nwarps - 1 ? nV : lo;
   }
-  for (int64_t i = r0; i < r1; ++i) {
-    const int64_t len = rowptr[i + 1] - rowptr[i];
-    const int32_t* col;
-    const double* val;
-    row_entries(T, rowstart[i], col, val);
-    const double ci = c[i];
-    double a = 0.0;
-    int64_t k = lane;
-    for (; k + 96 < len; k += 128) {
-      const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
-                    j3 = __ldcs(col + k + 96);
-      const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
-                   v3 = __ldcs(val + k + 96);
-      const double c0 = c[j0], c1 = c[j1], c2 = c[j2], c3 = c[j3];
-      atomicAdd(sigma + j0, v0 * ci);
-      atomicAdd(sigma + j1, v1 * ci);
-      atomicAdd(sigma + j2, v2 * ci);
-      atomicAdd(sigma + j3, v3 * ci);
-      a = fma(v0, c0, a);
-      a = fma(v1, c1, a);
-      a = fma(v2, c2, a);
-      a = fma(v3, c3, a);
+  for (int64_t g = r0; g < r1; g += 4) {
+    double acc[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      double a = 0.0;
+      const int64_t i = g + r;
+      if (i < r1) {
+        const int64_t len = rowptr[i + 1] - rowptr[i];
+        const int32_t* col;
+        const double* val;
+        row_entries(T, rowstart[i], col, val);
+        const double ci = c[i];
+        int64_t k = lane;
+        for (; k + 96 < len; k += 128) {
+          const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
+                        j3 = __ldcs(col + k + 96);
+          const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
+                       v3 = __ldcs(val + k + 96);
+          a = fma(v0, c[j0], a);
+          a = fma(v1, c[j1], a);
+          a = fma(v2, c[j2], a);
+          a = fma(v3, c[j3], a);
+          atomicAdd(sigma + j0, v0 * ci);
+          atomicAdd(sigma + j1, v1 * ci);
+          atomicAdd(sigma + j2, v2 * ci);
+          atomicAdd(sigma + j3, v3 * ci);
+        }
+        for (; k < len; k += 32) {
+          const int32_t j = __ldcs(col + k);
+          const double v = __ldcs(val + k);
+          a = fma(v, c[j], a);
+          atomicAdd(sigma + j, v * ci);
+        }
+      }
+      acc[r] = a;
     }
-    for (; k < len; k += 32) {
-      const int32_t j = __ldcs(col + k);
-      const double v = __ldcs(val + k);
-      atomicAdd(sigma + j, v * ci);
-      a = fma(v, c[j], a);
+    // four row sums at once (1.5 FP64 additions per row for the cross-lane
+    // reduction instead of 5): halve the values held per lane across lanes
+    // 16 apart, then 8 apart, then a plain tree over the last 8 lanes
+    const bool h16 = lane & 16, h8 = lane & 8;
+    const double w0 = (h16 ? acc[2] : acc[0]) + __shfl_xor_sync(0xffffffffu, h16 ? acc[0] : acc[2], 16);
+    const double w1 = (h16 ? acc[3] : acc[1]) + __shfl_xor_sync(0xffffffffu, h16 ? acc[1] : acc[3], 16);
+    double u = (h8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, h8 ? w0 : w1, 8);
+    u += __shfl_xor_sync(0xffffffffu, u, 4);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    if ((lane & 7) == 0) {
+      const int64_t i = g + (h16 ? 2 : 0) + (h8 ? 1 : 0);
+      if (i < r1) atomicAdd(sigma + i, fma(diag[i], c[i], u));
     }
-    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) atomicAdd(sigma + i, fma(diag[i], ci, a));
   }
 }
 
