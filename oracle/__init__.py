@@ -504,27 +504,36 @@ def close_under_flip(keys):
     return allk[np.lexsort((allk[:, 1], allk[:, 0]))]
 
 
+def flip_partner(keys):
+    """index of the spin-flipped partner of every determinant of a
+    flip-closed V (ValueError when one is missing)."""
+    keys = np.asarray(keys, np.uint64).reshape(-1, 2)
+    n = len(keys)
+    allk = np.concatenate([keys, flip_keys(keys)])
+    uniq, inv = np.unique(allk, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    if len(uniq) != n:
+        raise ValueError("space not closed under the spin flip")
+    pos = np.empty(n, np.int64)
+    pos[inv[:n]] = np.arange(n)
+    return pos[inv[n:]]
+
+
 def parity_basis(keys, parity):
     """Orthonormal basis (sparse nV x nb) of {c : c(b, a) = parity c(a, b)}
     on a flip-closed V: (e_D + parity e_Dbar) / sqrt(2) per pair D != Dbar,
     e_D for alpha = beta when parity = +1."""
     keys = np.asarray(keys, np.uint64).reshape(-1, 2)
-    index = {(int(a), int(b)): i for i, (a, b) in enumerate(keys.tolist())}
-    rows, cols, vals = [], [], []
-    nb = 0
-    for i, (a, b) in enumerate(keys.tolist()):
-        j = index.get((int(b), int(a)))
-        if j is None:
-            raise ValueError("space not closed under the spin flip")
-        if j == i:
-            if parity > 0:
-                rows.append(i); cols.append(nb); vals.append(1.0)
-                nb += 1
-        elif i < j:
-            r = 1.0 / np.sqrt(2.0)
-            rows += [i, j]; cols += [nb, nb]; vals += [r, parity * r]
-            nb += 1
-    return sp.csr_matrix((vals, (rows, cols)), shape=(len(keys), nb))
+    part = flip_partner(keys)
+    idx = np.arange(len(keys))
+    selfp = idx[part == idx] if parity > 0 else idx[:0]
+    lo = idx[part > idx]
+    nb_self, nb_pair = len(selfp), len(lo)
+    r = 1.0 / np.sqrt(2.0)
+    rows = np.concatenate([selfp, lo, part[lo]])
+    cols = np.concatenate([np.arange(nb_self), nb_self + np.arange(nb_pair), nb_self + np.arange(nb_pair)])
+    vals = np.concatenate([np.ones(nb_self), np.full(nb_pair, r), np.full(nb_pair, parity * r)])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(len(keys), nb_self + nb_pair))
 
 
 def parity_ground_state(inst, keys, parity):

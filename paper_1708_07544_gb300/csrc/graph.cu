@@ -536,17 +536,19 @@ __global__ void k_stride_sample(const int32_t* __restrict__ list, int64_t n, int
   if (t < ns) rows[t] = list[t * n / ns];
 }
 
-// CSR of the staged rows: row q (rowoff[q] >= 0) copied from the staging
-// buffer to [rp[q], rp[q+1]) of col, one warp per row.
-__global__ void k_copy_staged(const int64_t* __restrict__ rowoff, const int64_t* __restrict__ rp, int64_t nrows,
-                              const int32_t* __restrict__ stage, int32_t* __restrict__ col) {
+// Staged rows placed: row q (rowoff[q] >= 0) copied from the staging buffer
+// to [rp[q], rp[q] + len) of col, len = lens[q] (or rp[q+1] - rp[q] when
+// lens is NULL, a dense CSR), one warp per row.
+__global__ void k_copy_staged(const int64_t* __restrict__ rowoff, const int64_t* __restrict__ rp,
+                              const int64_t* __restrict__ lens, int64_t nrows, const int32_t* __restrict__ stage,
+                              int32_t* __restrict__ col) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = warp; q < nrows; q += nwarps) {
     const int64_t off = rowoff[q];
     if (off < 0) continue;
-    const int64_t b = rp[q], len = rp[q + 1] - b;
+    const int64_t b = rp[q], len = lens ? lens[q] : rp[q + 1] - b;
     for (int64_t t = lane; t < len; t += 32) col[b + t] = stage[off + t];
   }
 }
@@ -1397,15 +1399,18 @@ static hci_status stage_search(hci_ctx* ctx, GraphArgs& A, int64_t est, int64_t*
   return HCI_OK;
 }
 
-// Columns of the rows of stage_search written to col (row q at inc.rpN[q]):
+// Columns of the rows of stage_search written to col, row q at off[q]
+// (default inc.rpN[q]; lens[q] entries, default the dense rpN differences):
 // staged rows copied, the rows left searched again at their offsets (left <
 // 0: no row was staged, all are searched again).
-static hci_status stage_place(hci_ctx* ctx, GraphArgs& A, int64_t left, int32_t* col) {
+static hci_status stage_place(hci_ctx* ctx, GraphArgs& A, int64_t left, int32_t* col, const int64_t* off = nullptr,
+                              const int64_t* lens = nullptr) {
   IncScratch& S = ctx->inc;
   cudaStream_t st = ctx->st;
   const int64_t nrows = A.nrows;
-  if (left < 0) return rows_fill(ctx, A, bp<int64_t>(S.rpN), col, nullptr);   // counted, not staged
-  HCI_LAUNCH(k_copy_staged, grid_for(nrows * 32, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN), nrows,
+  if (!off) off = bp<int64_t>(S.rpN);
+  if (left < 0) return rows_fill(ctx, A, off, col, nullptr);   // counted, not staged
+  HCI_LAUNCH(k_copy_staged, grid_for(nrows * 32, 256), 256, 0, st)(bp<int64_t>(S.roff), off, lens, nrows,
                                                                     bp<int32_t>(S.stage), col);
   HCI_CUDA(ctx, cudaGetLastError());
   ctx->st_counts[HCI_ST_ROWS_REFILLED] += left;
@@ -1414,8 +1419,8 @@ static hci_status stage_place(hci_ctx* ctx, GraphArgs& A, int64_t left, int32_t*
     HCI_TRY(ensure_buf(ctx, S.left, (size_t)left * 12 + 16));
     int64_t* left_off = bp<int64_t>(S.left);
     int32_t* left_rows = reinterpret_cast<int32_t*>(left_off + left);
-    HCI_LAUNCH(k_collect_left, grid_for(nrows, 256), 256, 0, st)(bp<int64_t>(S.roff), bp<int64_t>(S.rpN),
-                                                                  A.rowlist, nrows, ctl + 2, left_rows, left_off);
+    HCI_LAUNCH(k_collect_left, grid_for(nrows, 256), 256, 0, st)(bp<int64_t>(S.roff), off, A.rowlist, nrows, ctl + 2,
+                                                                  left_rows, left_off);
     const int32_t* rl = A.rowlist;
     A.rowlist = left_rows;
     A.nrows = left;
@@ -1555,20 +1560,21 @@ static hci_status graph_build_half(hci_ctx* ctx, const uint64_t* keys, int64_t n
   A.s2i = bp<int32_t>(G.s2i);
   A.lower = 1;
   prof_tic(ctx, HCI_PH_GRAPH_ROWS);
-  // stored halves of the rows: count, offsets, one segment, fill, elements
-  HCI_TRY(rows_count(ctx, A, ctx->inc.cnt));
+  // stored halves of the rows, each searched once (staged; the row list is
+  // the identity map), into one segment, then their elements
+  A.rowlist = bp<int32_t>(G.s2i);
+  A.nrows = nV;
+  int64_t nst = 0, left = 0;
+  HCI_TRY(stage_new_rows(ctx, A, nV, nV, &nst, &left));
   HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
   HCI_TRY(ensure_buf(ctx, G.rowstart, (size_t)(nV + 1) * 8));
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->inc.cnt), bp<int64_t>(G.rowptr), nV, dtot));
-  HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(G.rowptr), nV, dtot);
-  hci_status st = HCI_OK;
-  const int64_t nst = read_i64(ctx, dtot, &st);
-  HCI_TRY(st);
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.rowptr.p, ctx->inc.rpN.p, (size_t)(nV + 1) * 8, cudaMemcpyDeviceToDevice, ctx->st));
   int seg = 0;
   HCI_TRY(seg_alloc(ctx, nst, &seg));
   int32_t* col = bp<int32_t>(G.seg_col[seg]);
   double* val = bp<double>(G.seg_val[seg]);
-  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowptr), col, val));
+  HCI_TRY(stage_place(ctx, A, left, col));
+  A.rowlist = nullptr;
   HCI_LAUNCH(k_row_values<true>, grid_for(nV * 32, 256), 256, 0, ctx->st)(
       nullptr, nV, bp<int64_t>(G.rowptr), nullptr, col, val, bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);
   HCI_LAUNCH(k_append_rows, grid_for(nV + 1, 256), 256, 0, ctx->st)(0, nV, bp<int64_t>(G.rowptr), 0, seg,
@@ -1709,20 +1715,23 @@ static hci_status graph_build_full(hci_ctx* ctx, const uint64_t* keys, int64_t n
   HCI_TRY(build_space(ctx, nV, A));
   A.s2i = bp<int32_t>(G.s2i);
   prof_tic(ctx, HCI_PH_GRAPH_ROWS);
+  // every row searched once (staged, as for the new rows of an extension;
+  // the row list is the identity map), lengths and logical offsets from it
+  A.rowlist = bp<int32_t>(G.s2i);
+  A.nrows = nV;
+  int64_t nnz = 0, left = 0;
+  HCI_TRY(stage_new_rows(ctx, A, nV, nV, &nnz, &left));
   HCI_TRY(ensure_buf(ctx, G.rowlen, (size_t)(nV + 1) * 8));
-  HCI_TRY(rows_count(ctx, A, G.rowlen));
+  HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.rowlen.p, ctx->inc.cnt.p, (size_t)nV * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  HCI_CUDA(ctx, cudaMemcpyAsync(G.rowptr.p, ctx->inc.rpN.p, (size_t)(nV + 1) * 8, cudaMemcpyDeviceToDevice, ctx->st));
   // capacities with slack, starts = their prefix sums, pool with headroom
   HCI_TRY(ensure_buf(ctx, G.rowcap, (size_t)(nV + 1) * 8));
   HCI_TRY(ensure_buf(ctx, G.rowstart, (size_t)(nV + 1) * 8));
-  HCI_TRY(ensure_buf(ctx, G.rowptr, (size_t)(nV + 1) * 8));
   HCI_LAUNCH(k_caps, grid_for(nV, 256), 256, 0, ctx->st)(bp<int64_t>(G.rowlen), nV, bp<int64_t>(G.rowcap));
   HCI_TRY(scan_i64(ctx, bp<int64_t>(G.rowcap), bp<int64_t>(G.rowstart), nV, dtot));
   hci_status st = HCI_OK;
   const int64_t used = read_i64(ctx, dtot, &st);
-  HCI_TRY(st);
-  HCI_TRY(scan_i64(ctx, bp<int64_t>(G.rowlen), bp<int64_t>(G.rowptr), nV, dtot));
-  HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(G.rowptr), nV, dtot);
-  const int64_t nnz = read_i64(ctx, dtot, &st);
   HCI_TRY(st);
   const int64_t cap = used + used / 4 + 1024;
   if (ctx->graph_budget > 0 && cap * 12 > ctx->graph_budget)
@@ -1731,7 +1740,8 @@ static hci_status graph_build_full(hci_ctx* ctx, const uint64_t* keys, int64_t n
   HCI_TRY(ensure_buf(ctx, G.seg_col[0], (size_t)cap * 4));
   HCI_TRY(ensure_buf(ctx, G.seg_val[0], (size_t)cap * 8));
   G.nseg = 1;
-  HCI_TRY(rows_fill(ctx, A, bp<int64_t>(G.rowstart), bp<int32_t>(G.seg_col[0]), bp<double>(G.seg_val[0])));
+  HCI_TRY(stage_place(ctx, A, left, bp<int32_t>(G.seg_col[0]), bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen)));
+  A.rowlist = nullptr;
   HCI_LAUNCH(k_row_values<false>, grid_for(nV * 32, 256), 256, 0, ctx->st)(
       nullptr, nV, bp<int64_t>(G.rowstart), bp<int64_t>(G.rowlen), bp<int32_t>(G.seg_col[0]),
       bp<double>(G.seg_val[0]), bp<ulonglong2>(G.keys), bp<ulonglong2>(G.keys_int), A.H);

@@ -381,6 +381,12 @@ def test_incremental_graph_row_beyond_scratch(pkg):
         assert s.stats()["rows_refilled"] >= 1
     want = oracle.sigma_rows(inst, full, c, rows)
     assert np.abs(got[rows] - want).max() < 1e-11 * max(1.0, np.abs(want).max())
+    # the same space built at once: the aufbau row of the fresh graph takes
+    # the second search too
+    with solver(pkg, inst) as s:
+        got2 = s.sigma(dev_keys(full), torch.tensor(c).cuda()).cpu().numpy()
+        assert s.stats()["rows_refilled"] >= 1
+    assert np.abs(got2[rows] - want).max() < 1e-11 * max(1.0, np.abs(want).max())
 
 
 def test_incremental_solve_matches_fresh_contexts(pkg, poly8_ref):

@@ -104,7 +104,8 @@ def test_davidson_in_the_sector_matches_oracle(pkg, name, make, parity):
 
 
 @pytest.mark.parametrize("name,make,eps1", [("polyene8", lambda: hi.ppp_polyene(8), 1e-4),
-                                            ("df12", hi.df_12o, 1e-3)])
+                                            ("df12", hi.df_12o, 5e-3),
+                                            ("df12_batch", lambda: hi.df_batch(64)[2], 1e-4)])
 @pytest.mark.parametrize("parity", [1, -1])
 def test_solve_in_the_sector_matches_oracle(pkg, name, make, eps1, parity):
     inst = make()
