@@ -937,7 +937,10 @@ __global__ void k_diag(int n, const double* __restrict__ h, const double* __rest
 // L2.  Rows are summed four at a time, so that the cross-lane reduction
 // costs 1.5 FP64 additions per row instead of 8 (the FP64 pipe, 2 DFMA per
 // clock per SM, bounds this kernel).
-__global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ rowptr,
+// blocks of k_sigma1 per SM, all resident (the grid is this many per SM)
+constexpr int SIGMA_BLOCKS_PER_SM = 5;
+
+__global__ void __launch_bounds__(256, SIGMA_BLOCKS_PER_SM) k_sigma1(const int64_t* __restrict__ rowptr,
                                                   const int64_t* __restrict__ rowstart, const int32_t* __restrict__ col,
                                                const double* __restrict__ val, const double* __restrict__ diag,
                                                int64_t nV, const double* __restrict__ c, double* __restrict__ sigma,
@@ -962,7 +965,7 @@ __global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ r
       double acc[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        double a = 0.0;
+        double a = 0.0, a2 = 0.0;   // two chains, so consecutive FMAs do not wait on each other
         const int64_t i = g + r;
         if (i < r1) {
           const int64_t b = rowstart[i], e = b + (rowptr[i + 1] - rowptr[i]);
@@ -973,13 +976,13 @@ __global__ void __launch_bounds__(256, 6) k_sigma1(const int64_t* __restrict__ r
             const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
                          v3 = __ldcs(val + k + 96);
             a = fma(v0, c[j0], a);
-            a = fma(v1, c[j1], a);
+            a2 = fma(v1, c[j1], a2);
             a = fma(v2, c[j2], a);
-            a = fma(v3, c[j3], a);
+            a2 = fma(v3, c[j3], a2);
           }
           for (; k < e; k += 32) a = fma(__ldcs(val + k), c[__ldcs(col + k)], a);
         }
-        acc[r] = a;
+        acc[r] = a + a2;
       }
       // four row sums at once: halve the values held per lane across lanes
       // 16 apart, then 8 apart, then a plain tree over the last 8 lanes
@@ -2098,7 +2101,7 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
       HCI_LAUNCH(k_sigma_half, grid_for(G.nV * 32, 256, ctx->nsm * 16), 256, 0, ctx->st)(
           bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), T, bp<double>(G.diag), G.nV, c, sigma, nvec);
   } else if (nvec == 1) {
-    HCI_LAUNCH(k_sigma1, ctx->nsm * 6, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart),
+    HCI_LAUNCH(k_sigma1, ctx->nsm * SIGMA_BLOCKS_PER_SM, 256, 0, ctx->st)(bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart),
                                                         bp<int32_t>(G.seg_col[0]), bp<double>(G.seg_val[0]),
                                                         bp<double>(G.diag), G.nV, c, sigma, 1);
   } else {
