@@ -246,6 +246,10 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
   }
   ctx->fail_alloc_after = hci_fail_alloc_env();
   {
+    const char* v = getenv("HCI_SIGMA_HALF_PASSES");
+    ctx->half_passes = (v && (v[0] == '1' || v[0] == '2') && v[1] == 0) ? v[0] - '0' : 0;
+  }
+  {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0) {
@@ -256,6 +260,9 @@ extern "C" hci_status hci_create(hci_ctx** out, int norb, int nalpha, int nbeta,
     }
     size_t fr = 0, tot = 0;
     ctx->mem_total = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? tot : ((size_t)64 << 30);
+    int l2 = 0;
+    ctx->l2_bytes = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess && l2 > 0
+                        ? (size_t)l2 : ((size_t)126 << 20);
     cudaGetLastError();
   }
   ctx->n = norb;

@@ -1059,6 +1059,11 @@ __device__ __forceinline__ void row_entries(const SegTab& T, int64_t rs, const i
 // the equal shares of the entries run in one wave
 constexpr int SIGMA_HALF_BLOCKS_PER_SM = 4;
 
+// PASS 0: both contributions of every entry (sigma zeroed first).  When c
+// and sigma do not fit L2 together, two passes keep one random-access
+// vector in L2 each: PASS 1 writes sigma_i = H_ii c_i + the row sum (plain
+// stores, no atomics, no zeroing), PASS 2 then adds the scatters.
+template <int PASS>
 __global__ void __launch_bounds__(256, SIGMA_HALF_BLOCKS_PER_SM) k_sigma1_half(const int64_t* __restrict__ rowptr,
                                                   const int64_t* __restrict__ rowstart, const __grid_constant__ SegTab T,
                                                   const double* __restrict__ diag, int64_t nV,
@@ -1091,25 +1096,31 @@ __global__ void __launch_bounds__(256, SIGMA_HALF_BLOCKS_PER_SM) k_sigma1_half(c
         row_entries(T, rowstart[i], col, val);
         const double ci = c[i];
         int64_t k = lane;
-        for (; k + 96 < len; k += 128) {
-          const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
-                        j3 = __ldcs(col + k + 96);
-          const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
-                       v3 = __ldcs(val + k + 96);
-          a = fma(v0, c[j0], a);
-          a = fma(v1, c[j1], a);
-          a = fma(v2, c[j2], a);
-          a = fma(v3, c[j3], a);
-          atomicAdd(sigma + j0, v0 * ci);
-          atomicAdd(sigma + j1, v1 * ci);
-          atomicAdd(sigma + j2, v2 * ci);
-          atomicAdd(sigma + j3, v3 * ci);
-        }
-        for (; k < len; k += 32) {
-          const int32_t j = __ldcs(col + k);
-          const double v = __ldcs(val + k);
-          a = fma(v, c[j], a);
-          atomicAdd(sigma + j, v * ci);
+        if (PASS != 2 || ci != 0.0) {
+          for (; k + 96 < len; k += 128) {
+            const int32_t j0 = __ldcs(col + k), j1 = __ldcs(col + k + 32), j2 = __ldcs(col + k + 64),
+                          j3 = __ldcs(col + k + 96);
+            const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
+                         v3 = __ldcs(val + k + 96);
+            if (PASS != 2) {
+              a = fma(v0, c[j0], a);
+              a = fma(v1, c[j1], a);
+              a = fma(v2, c[j2], a);
+              a = fma(v3, c[j3], a);
+            }
+            if (PASS != 1) {
+              atomicAdd(sigma + j0, v0 * ci);
+              atomicAdd(sigma + j1, v1 * ci);
+              atomicAdd(sigma + j2, v2 * ci);
+              atomicAdd(sigma + j3, v3 * ci);
+            }
+          }
+          for (; k < len; k += 32) {
+            const int32_t j = __ldcs(col + k);
+            const double v = __ldcs(val + k);
+            if (PASS != 2) a = fma(v, c[j], a);
+            if (PASS != 1) atomicAdd(sigma + j, v * ci);
+          }
         }
       }
       acc[r] = a;
@@ -1124,9 +1135,12 @@ __global__ void __launch_bounds__(256, SIGMA_HALF_BLOCKS_PER_SM) k_sigma1_half(c
     u += __shfl_xor_sync(0xffffffffu, u, 4);
     u += __shfl_xor_sync(0xffffffffu, u, 2);
     u += __shfl_xor_sync(0xffffffffu, u, 1);
-    if ((lane & 7) == 0) {
+    if (PASS != 2 && (lane & 7) == 0) {
       const int64_t i = g + (h16 ? 2 : 0) + (h8 ? 1 : 0);
-      if (i < r1) atomicAdd(sigma + i, fma(diag[i], c[i], u));
+      if (i < r1) {
+        if (PASS == 0) atomicAdd(sigma + i, fma(diag[i], c[i], u));
+        else sigma[i] = fma(diag[i], c[i], u);
+      }
     }
   }
 }
@@ -2087,15 +2101,24 @@ hci_status sigma_apply(hci_ctx* ctx, const double* c, double* sigma, int nvec) {
     prof_toc(ctx, HCI_PH_SIGMA);
     return HCI_OK;
   }
-  if (G.half) HCI_CUDA(ctx, cudaMemsetAsync(sigma, 0, (size_t)G.nV * nvec * 8, ctx->st));
+  // one orientation: two passes when c and sigma together exceed half of L2
+  // (HCI_SIGMA_HALF_PASSES set at context creation overrides the choice)
+  const bool two_pass = G.half && nvec == 1 &&
+                        (ctx->half_passes ? ctx->half_passes == 2 : (double)G.nV * 16.0 > 0.5 * (double)ctx->l2_bytes);
+  if (G.half && !two_pass) HCI_CUDA(ctx, cudaMemsetAsync(sigma, 0, (size_t)G.nV * nvec * 8, ctx->st));
   prof_tic(ctx, HCI_PH_SIGMA);
   ctx->st_counts[HCI_ST_SIGMA_CALLS] += nvec;
   ctx->st_counts[HCI_ST_SIGMA_ROWS] += G.nV * nvec;
   ctx->st_counts[HCI_ST_SIGMA_NNZ] += G.nnz * nvec;
   if (G.half) {
     const SegTab T = G.tab();
-    if (nvec == 1)
-      HCI_LAUNCH(k_sigma1_half, ctx->nsm * SIGMA_HALF_BLOCKS_PER_SM, 256, 0, ctx->st)(
+    if (nvec == 1 && two_pass) {
+      HCI_LAUNCH(k_sigma1_half<1>, ctx->nsm * SIGMA_HALF_BLOCKS_PER_SM, 256, 0, ctx->st)(
+          bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), T, bp<double>(G.diag), G.nV, c, sigma);
+      HCI_LAUNCH(k_sigma1_half<2>, ctx->nsm * SIGMA_HALF_BLOCKS_PER_SM, 256, 0, ctx->st)(
+          bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), T, bp<double>(G.diag), G.nV, c, sigma);
+    } else if (nvec == 1)
+      HCI_LAUNCH(k_sigma1_half<0>, ctx->nsm * SIGMA_HALF_BLOCKS_PER_SM, 256, 0, ctx->st)(
           bp<int64_t>(G.rowptr), bp<int64_t>(G.rowstart), T, bp<double>(G.diag), G.nV, c, sigma);
     else
       HCI_LAUNCH(k_sigma_half, grid_for(G.nV * 32, 256, ctx->nsm * 16), 256, 0, ctx->st)(

@@ -144,6 +144,8 @@ struct hci_ctx {
   int64_t partner_epoch = -1;      // graph epoch d_partner belongs to
   int nsm = 0;               // streaming multiprocessors of the context's device (grid sizes)
   size_t mem_total = 0;      // device memory of the context's device (bytes)
+  size_t l2_bytes = 0;       // L2 cache of the context's device (bytes)
+  int half_passes = 0;       // HCI_SIGMA_HALF_PASSES: 1 or 2 forces the one-orientation product's passes (0: by size)
   int64_t fail_alloc_after = -1;  // HCI_FAIL_ALLOC_AFTER: allocations left before one is refused (-1: off)
   int64_t last_candidates = 0;
   int64_t st_counts[HCI_ST_COUNT] = {};

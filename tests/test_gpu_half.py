@@ -5,7 +5,8 @@ adds the entry to both rows (the second through an FP64 atomic add), so
 the graph takes half the memory of the both-orientation form.
 
 * sigma equals the oracle's H c and the both-orientation form's (rounding
-  order), with the same connection count;
+  order), with the same connection count, in one pass and as a row-sum
+  pass plus a scatter pass (the form for vectors beyond L2);
 * Davidson energies and the RDMs (one orientation accumulated, the other as
   its transpose) equal the oracle's;
 * a space grown in steps (rows appended, stored rows untouched), including a
@@ -61,8 +62,18 @@ CASES = [
 ]
 
 
+@pytest.fixture(params=["by_size", "two_passes"])
+def passes(request, monkeypatch):
+    """The product in one pass (c and sigma fit L2 at these sizes) and, with
+    HCI_SIGMA_HALF_PASSES=2, as a row-sum pass plus a scatter pass (the form
+    taken when c and sigma exceed half of L2)."""
+    if request.param == "two_passes":
+        monkeypatch.setenv("HCI_SIGMA_HALF_PASSES", "2")
+    return request.param
+
+
 @pytest.mark.parametrize("name,make,nv", CASES)
-def test_half_sigma_davidson_rdm_match_oracle(pkg, name, make, nv):
+def test_half_sigma_davidson_rdm_match_oracle(pkg, name, make, nv, passes):
     from paper_1708_07544_gb300 import _abi
 
     inst = make()
@@ -94,7 +105,7 @@ def test_half_sigma_davidson_rdm_match_oracle(pkg, name, make, nv):
     assert np.abs(r2.cpu().numpy() - w2).max() < 1e-8
 
 
-def test_half_grown_space_matches_oracle(pkg):
+def test_half_grown_space_matches_oracle(pkg, passes):
     from paper_1708_07544_gb300 import _abi
 
     inst = hi.df_12o()
