@@ -136,7 +136,7 @@ class Clocks:
 # capture of k_sigma1 on the pentacene (22e,22o) space (profiles/);
 # traffic grows in proportion to the connections, so it is scaled to the
 # launch.  None while the kernel differs from the captured one.
-SIGMA_TRAFFIC_PER_CONN = 12.38
+SIGMA_TRAFFIC_PER_CONN = 12.40
 
 
 def traffic_per_launch(nnz, nV):
