@@ -198,6 +198,14 @@ inline int hci_nsm() { return g_hci_nsm > 0 ? g_hci_nsm : 152; }
 // one is refused as if the device were out of memory), or -1 when unset.
 int64_t hci_fail_alloc_env();
 
+// Quarter transform of the integral rotation, out[J][p] = sum_a in[a][J]
+// M[a][p] for J < n^3 (qtrans_tc.cu): exact digit products on the bf16
+// tensor cores, rounded once to FP64.  qtrans_tc_check() reports (and
+// clears) a launch on stream st that gave up waiting for its products (it
+// reads a device flag on st and synchronises st).
+hci_status qtrans_tc(cudaStream_t st, int n, const double* in, const double* M, double* out);
+hci_status qtrans_tc_check(cudaStream_t st);
+
 inline int grid_for(int64_t work, int block, int max_blocks = -1) {
   if (max_blocks < 0) max_blocks = hci_nsm() * 16;
   int64_t g = (work + block - 1) / block;

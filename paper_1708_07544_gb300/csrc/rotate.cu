@@ -12,8 +12,9 @@
 //           8-fold symmetric integrals contribute equally);
 //           dE/dkappa = L_exp(kappa^T, dE/dU), the Frechet derivative of
 //           exp at kappa^T, read off exp([[k^T, G], [0, k^T]]).
-// FP64 on CUDA cores: double-precision tensor throughput on this part is no
-// higher than the FP64 pipe, and the contraction is a small share of a solve.
+// The quarter transforms (the n^5 part) run on the bf16 tensor cores as
+// exact digit products rounded once to FP64 (qtrans_tc.cu); the n x n
+// matrix work stays on the FP64 pipe.
 #include <cuda.h>
 
 #include <algorithm>
@@ -100,32 +101,6 @@ __global__ void k_upper_right(int n, const double* __restrict__ B, double* __res
 __global__ void k_eye(int n, double* __restrict__ I) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n * n) I[t] = (t / n == t % n) ? 1.0 : 0.0;
-}
-
-// out[J*n + p] = sum_a in[a*N3 + J] * M[a*n + p], J < N3 = n^3
-constexpr int QT_J = 32;
-__global__ void __launch_bounds__(256) k_qtrans(int n, const double* __restrict__ in, const double* __restrict__ M,
-                                                double* __restrict__ out) {
-  extern __shared__ double sm[];
-  double* Ms = sm;               // n*n
-  double* tile = sm + n * n;     // n * QT_J
-  const int64_t N3 = (int64_t)n * n * n;
-  const int64_t J0 = (int64_t)blockIdx.x * QT_J;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ms[t] = M[t];
-  for (int t = threadIdx.x; t < n * QT_J; t += blockDim.x) {
-    int a = t / QT_J, jj = t % QT_J;
-    int64_t J = J0 + jj;
-    tile[a * QT_J + jj] = J < N3 ? in[(int64_t)a * N3 + J] : 0.0;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < QT_J * n; t += blockDim.x) {
-    int jj = t / n, p = t % n;
-    int64_t J = J0 + jj;
-    if (J >= N3) continue;
-    double acc = 0.0;
-    for (int a = 0; a < n; ++a) acc = fma(tile[a * QT_J + jj], Ms[a * n + p], acc);
-    out[J * n + p] = acc;
-  }
 }
 
 // The solver reads different permutations of one integral (heat-bath lists,
@@ -238,11 +213,21 @@ hci_status expm_dev(cudaStream_t st, int m, const double* A, double* E, double* 
   return cudaGetLastError() == cudaSuccess ? HCI_OK : HCI_ERR_CUDA;
 }
 
-void qtrans(cudaStream_t st, int n, const double* in, const double* M, double* out) {
-  const int64_t N3 = (int64_t)n * n * n;
-  size_t smem = (size_t)(n * n + n * QT_J) * 8;
-  HCI_LAUNCH(k_qtrans, blocks(N3, QT_J), 256, smem, st)(n, in, M, out);
-}
+// out[J*n + p] = sum_a in[a*N3 + J] * M[a*n + p], J < N3 = n^3
+#define QTRANS(who, in, M, out)                                                              \
+  do {                                                                                       \
+    if (qtrans_tc(st, n, in, M, out) != HCI_OK)                                              \
+      return hci_fail(nullptr, HCI_ERR_CUDA, who ": quarter transform launch failed: %s",     \
+                      cudaGetErrorString(cudaGetLastError()));                               \
+  } while (0)
+
+// after the final synchronisation: the quarter transforms completed
+#define QTRANS_CHECK(who)                                                                        \
+  do {                                                                                           \
+    if (qtrans_tc_check(st) != HCI_OK)                                                             \
+      return hci_fail(nullptr, HCI_ERR_CUDA, who ": a quarter transform gave up waiting for its " \
+                      "tensor-core products");                                                   \
+  } while (0)
 
 // exact permutational symmetry of the rotated integrals (see k_sym8)
 void symmetrize(cudaStream_t st, int n, double* h, double* eri) {
@@ -266,20 +251,20 @@ extern "C" hci_status hci_rotate(int norb, const double* kappa, const double* h,
   if (!w1 || !w2 || !w3 || !ds || !t4)
     return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate: allocation failed%s",
                     S.left == 0 ? " (injected by HCI_FAIL_ALLOC_AFTER)" : "");
-  cudaFuncSetAttribute(k_qtrans, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 * 64 + 64 * QT_J) * 8);
   hci_status s = expm_dev(st, n, kappa, U, w1, w2, w3, ds);
   if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate: matrix exponential failed");
   mm(st, n, h, 0, U, 0, w1, 1.0, 0.0);          // h U
   mm(st, n, U, 1, w1, 0, h_out, 1.0, 0.0);      // U^T h U
-  qtrans(st, n, eri, U, t4);
-  qtrans(st, n, t4, U, eri_out);
-  qtrans(st, n, eri_out, U, t4);
-  qtrans(st, n, t4, U, eri_out);
+  QTRANS("hci_rotate", eri, U, t4);
+  QTRANS("hci_rotate", t4, U, eri_out);
+  QTRANS("hci_rotate", eri_out, U, t4);
+  QTRANS("hci_rotate", t4, U, eri_out);
   symmetrize(st, n, h_out, eri_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate: %s", cudaGetErrorString(e));
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate: %s", cudaGetErrorString(e));
+  QTRANS_CHECK("hci_rotate");
   return HCI_OK;
 }
 
@@ -302,7 +287,6 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
   if (!U || !Ut || !I || !w1 || !gU || !b1 || !b2 || !b3 || !b4 || !b5 || !ds || !D || !t4)
     return hci_fail(nullptr, HCI_ERR_NOMEM, "hci_rotate_backward: allocation failed%s",
                     S.left == 0 ? " (injected by HCI_FAIL_ALLOC_AFTER)" : "");
-  cudaFuncSetAttribute(k_qtrans, cudaFuncAttributeMaxDynamicSharedMemorySize, (64 * 64 + 64 * QT_J) * 8);
   cudaFuncSetAttribute(k_gemm_nt_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * NT_CH * 8);
   hci_status s = expm_dev(st, n, kappa, U, w1, b1, b2, ds);
   if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_backward: matrix exponential failed");
@@ -315,10 +299,10 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
   }
   HCI_LAUNCH(k_scale_copy, blocks((int64_t)n4), 256, 0, st)((int64_t)n4, rdm2, 0.5, D);
   if (deri) {
-    qtrans(st, n, D, Ut, t4);
-    qtrans(st, n, t4, Ut, deri);
-    qtrans(st, n, deri, Ut, t4);
-    qtrans(st, n, t4, Ut, deri);
+    QTRANS("hci_rotate_backward", D, Ut, t4);
+    QTRANS("hci_rotate_backward", t4, Ut, deri);
+    QTRANS("hci_rotate_backward", deri, Ut, t4);
+    QTRANS("hci_rotate_backward", t4, Ut, deri);
   }
   if (dkappa) {
     // h-part: h U g1^T + h^T U g1
@@ -328,10 +312,10 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
     mm(st, n, w1, 0, rdm1, 0, gU, 1.0, 1.0);
     // T[y][b][c][d] = sum_qrs U_bq U_cr U_ds D[y][q][r][s]
     double* T = t4;
-    qtrans(st, n, D, I, T);          // (q r s y)
-    qtrans(st, n, T, Ut, D);         // (r s y b)
-    qtrans(st, n, D, Ut, T);         // (s y b c)
-    qtrans(st, n, T, Ut, D);         // (y b c d)
+    QTRANS("hci_rotate_backward", D, I, T);          // (q r s y)
+    QTRANS("hci_rotate_backward", T, Ut, D);         // (r s y b)
+    QTRANS("hci_rotate_backward", D, Ut, T);         // (s y b c)
+    QTRANS("hci_rotate_backward", T, Ut, D);         // (y b c d)
     const int64_t K = (int64_t)n * n * n;
     const int nparts = (int)((K + NT_CH - 1) / NT_CH);
     double* part = S.get((size_t)nparts * n2);
@@ -350,6 +334,7 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_backward: %s", cudaGetErrorString(e));
+  QTRANS_CHECK("hci_rotate_backward");
   return HCI_OK;
 }
 
@@ -468,14 +453,15 @@ extern "C" hci_status hci_rotate_noalloc(int norb, const double* kappa, const do
   if (s != HCI_OK) return hci_fail(nullptr, s, "hci_rotate_noalloc: matrix exponential failed");
   mm(st, n, h, 0, U, 0, w1, 1.0, 0.0);          // h U
   mm(st, n, U, 1, w1, 0, h_out, 1.0, 0.0);      // U^T h U
-  qtrans(st, n, eri, U, t4);
-  qtrans(st, n, t4, U, eri_out);
-  qtrans(st, n, eri_out, U, t4);
-  qtrans(st, n, t4, U, eri_out);
+  QTRANS("hci_rotate_noalloc", eri, U, t4);
+  QTRANS("hci_rotate_noalloc", t4, U, eri_out);
+  QTRANS("hci_rotate_noalloc", eri_out, U, t4);
+  QTRANS("hci_rotate_noalloc", t4, U, eri_out);
   symmetrize(st, n, h_out, eri_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: %s", cudaGetErrorString(e));
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hci_fail(nullptr, HCI_ERR_CUDA, "hci_rotate_noalloc: %s", cudaGetErrorString(e));
+  QTRANS_CHECK("hci_rotate_noalloc");
   return HCI_OK;
 }
