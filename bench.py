@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -70,6 +71,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of one CPU sample")
     ap.add_argument("--sigma-reps", type=int, default=20)
+    ap.add_argument("--rotation-reps", type=int, default=20, help="launches of the quarter transform timed alone")
     ap.add_argument("--fwd-bwd-reps", type=int, default=5)
     ap.add_argument("--pt2-reps", type=int, default=2)
     ap.add_argument("--direct-reps", type=int, default=2)
@@ -493,6 +495,14 @@ def gpu_arm(args):
         finally:
             sl.close()
 
+    # the rotation's quarter transform alone (Sec. III.A), on the tensor
+    # cores: per-launch time over buffers rotated through more than L2, the
+    # FP64-equivalent rate 2 n^5 / t, the bf16 tensor work of the digit
+    # products against the measured bf16 peak, and its HBM bytes
+    rotation = {}
+    if args.rotation_reps > 0:
+        rotation = rotation_section(args, n, h_d, eri_d, k_d, dev)
+
     out = None
     if rank == 0:
         value = aggregate_seconds(ms_step, world)
@@ -530,6 +540,7 @@ def gpu_arm(args):
             "sigma_direct": direct,
             "batch": batch,
             "large": large,
+            "rotation": rotation,
             "e2e": {"value": round(aggregate_seconds(e2e_step, world), 6), "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
@@ -538,6 +549,76 @@ def gpu_arm(args):
     if world > 1:
         dist.barrier()
     return out, last, inst
+
+
+def qtrans_mma_flops(n):
+    """bf16 tensor work of one quarter transform as the kernel issues it:
+    per tile of 128 rows, every pair (s, t) of the seven digits of each
+    operand with s + t <= 9 (34 pairs), one M=128 x N=np x K=np product each
+    (np = n rounded up to 16)."""
+    npad = -(-n // 16) * 16
+    pairs = sum(min(L - 1, 7) - max(1, L - 7) + 1 for L in range(2, 10))
+    tiles = -(-n ** 3 // 128)
+    return tiles * pairs * 2 * 128 * npad * npad
+
+
+def rotation_section(args, n, h_d, eri_d, k_d, dev):
+    import torch
+
+    from paper_1708_07544_gb300 import _abi
+
+    U, _, _ = _abi.hci_rotate(k_d, h_d, eri_d)
+    n4 = n ** 4
+    # enough distinct input/output pairs that each launch misses L2
+    nbuf = max(2, int(math.ceil(3 * 129e6 / (16 * n4))) + 1)
+    ins = [eri_d.clone() for _ in range(nbuf)]
+    outs = [torch.empty_like(eri_d) for _ in range(nbuf)]
+    st = torch.cuda.current_stream()
+    for i in range(3):
+        _abi.hci_qtrans(ins[i % nbuf], U, outs[i % nbuf], check=False, stream=st)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("qtrans_reps")
+    e0.record(st)
+    for i in range(args.rotation_reps):
+        _abi.hci_qtrans(ins[i % nbuf], U, outs[i % nbuf], check=False, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    _abi.hci_qtrans(ins[0], U, outs[0], check=True, stream=st)
+    t = e0.elapsed_time(e1) / args.rotation_reps * 1e-3
+    # whole rotation and its backward (host clock around the synchronising calls)
+    r1 = torch.eye(n, dtype=torch.float64, device=dev)
+    r2 = torch.zeros((n,) * 4, dtype=torch.float64, device=dev)
+    tr, tb = [], []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        _abi.hci_rotate(k_d, h_d, eri_d)
+        b = time.perf_counter()
+        _abi.hci_rotate_backward(k_d, h_d, eri_d, r1, r2, want_dh=False, want_deri=False)
+        tr.append(b - a)
+        tb.append(time.perf_counter() - b)
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    pk = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            pk = json.load(fh)
+    bf16 = float(pk.get("bf16_tflops", 1900.0))
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    mma = qtrans_mma_flops(n)
+    byt = 2 * n4 * 8
+    del ins, outs
+    return {"kernel": "k_qtrans_tc (digit products on tcgen05 bf16, FP32 in tensor memory, rounded to FP64)",
+            "norb": n, "launch_ms": round(t * 1e3, 4), "reps": args.rotation_reps, "buffers": nbuf,
+            "fp64_equiv_tflops": round(2 * n ** 5 / t / 1e12, 3),
+            "tensor": {"achieved": round(mma / t / 1e12, 1), "peak": bf16, "unit": "TFLOP/s",
+                       "frac": round(mma / t / 1e12 / bf16, 4), "flops_per_launch": mma,
+                       "peak_kind": "measured" if pk else "fallback"},
+            "hbm": {"achieved": round(byt / t / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(byt / t / 1e9 / hbm, 4), "bytes_per_launch": byt},
+            "rotate_ms": round(1e3 * min(tr), 3), "rotate_backward_ms": round(1e3 * min(tb), 3)}
 
 
 # ----------------------------------------------------------------------------

@@ -338,6 +338,21 @@ hci_status hci_solve_batch(int count, const int* norb, const int* nalpha, const 
 hci_status hci_rotate(int norb, const double* kappa, const double* h, const double* eri, double* U,
                       double* h_out, double* eri_out, void* stream);
 
+/* One quarter transform of the rotation above (Sec. III.A), the n^5 part
+ * of hci_rotate and hci_rotate_backward:
+ *   out[J*n + p] = sum_a in[a*n^3 + J] * M[a*n + p],   J < n^3, p < n,
+ * i.e. the summed index a leaves the front and p joins at the back (four
+ * calls with M = U give (pq|rs)').  in and out are n^4 doubles, M is n*n,
+ * all device pointers; in and out must not overlap.  Computed on the bf16
+ * tensor cores as exact products of 7-bit digits of each row of in and each
+ * column of M (scaled by their largest binary exponents), summed exactly
+ * and rounded once to FP64: the error is at most about 2^-55 (2^-52 for
+ * n > 48) of max_a |in[a][J]| * max_a |M[a][p]|.  Stream-ordered; with
+ * check != 0 the call synchronises the stream and returns HCI_ERR_CUDA if
+ * the launch gave up waiting for its products (never expected), which the
+ * rotation entry points check after every call anyway. */
+hci_status hci_qtrans(int norb, const double* in, const double* M, double* out, int check, void* stream);
+
 /* Backward of E(h', eri') through the rotation, Eq. (vdedk2): given
  * dE/dh' = rdm1 and dE/d(pq|rs)' = rdm2/2 (Hellmann-Feynman at fixed V and
  * converged c), returns

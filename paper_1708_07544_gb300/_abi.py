@@ -30,7 +30,8 @@ EXPORTS = ["hci_create", "hci_destroy", "hci_last_error", "hci_build_lists", "hc
            "hci_sigma", "hci_davidson", "hci_rdm12", "hci_solve", "hci_rotate", "hci_rotate_backward",
            "hci_stats", "hci_profile", "hci_timers", "hci_launch_count", "hci_rotate_noalloc",
            "hci_solve_batch", "hci_pt2", "hci_zvector", "hci_relaxed_rdm12", "hci_davidson_roots",
-           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode", "hci_spin_square", "hci_solve_from", "hci_set_spin_parity"]
+           "hci_solve_roots", "hci_pt2_stochastic", "hci_set_sigma_mode", "hci_spin_square", "hci_solve_from", "hci_set_spin_parity",
+           "hci_qtrans"]
 PHASES = ["lists", "walk", "dedup", "merge", "graph", "sigma", "davidson", "rdm", "singles", "graph_space",
           "graph_rows", "graph_merge", "rdm_diag", "hdiag"]
 STATS = ["graph_nnz", "last_candidates", "sigma_calls", "sigma_rows", "sigma_nnz", "select_calls",
@@ -86,6 +87,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.hci_rotate.argtypes = [I, V, V, V, V, V, V, V]
     L.hci_rotate_backward.argtypes = [I, V, V, V, V, V, V, V, V, V]
     L.hci_rotate_noalloc.argtypes = [I, V, V, V, V, V, V, V]
+    L.hci_qtrans.argtypes = [I, V, V, V, I, V]
     L.hci_solve_batch.argtypes = [I, V, V, V, V, V, V, D, I, D, I, I, V, V, V, V, V]
     L.hci_stats.argtypes = [V, V, I]
     L.hci_profile.argtypes = [V, I]
@@ -364,6 +366,17 @@ def hci_rotate(kappa, h, eri, stream=None):
     _check(L.hci_rotate(n, _ptr(kappa.contiguous()), _ptr(h.contiguous()), _ptr(eri.contiguous()), _ptr(U),
                         _ptr(h2), _ptr(e2), _stream_ptr(stream)), None)
     return U, h2, e2
+
+
+def hci_qtrans(inp, M, out=None, check=True, stream=None):
+    """One quarter transform out[J*n + p] = sum_a inp[a*n^3 + J] M[a*n + p]."""
+    L = load()
+    n = M.shape[0]
+    if out is None:
+        out = torch.empty_like(inp)
+    _check(L.hci_qtrans(n, _ptr(inp.contiguous()), _ptr(M.contiguous()), _ptr(out), 1 if check else 0,
+                        _stream_ptr(stream)), None)
+    return out
 
 
 def hci_rotate_backward(kappa, h, eri, rdm1, rdm2, want_dh=True, want_deri=True, want_dkappa=True, stream=None):

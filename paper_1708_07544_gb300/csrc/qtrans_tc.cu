@@ -13,29 +13,35 @@
 //
 //  * every row J of the left operand (the n values in[a][J] that are summed)
 //    and every column p of U is put in fixed point against its own largest
-//    binary exponent E: v = sign * sum_{s=1..8} d_s 2^(-7 s) * 2^(E - 1022)
-//    with integer digits 0 <= d_s < 128 (56 bits; the part below 2^-56 of
-//    the largest entry is dropped);
-//  * a digit is exactly a bf16, the product of two digits is below 2^14,
-//    and a sum of such products over K <= 64 entries and up to 8 digit
-//    pairs stays below 2^23, so the FP32 accumulation of the tensor cores is
-//    exact; the digit pairs (s, t) of one level L = s + t accumulate into
-//    one tensor-memory column block;
-//  * levels 2..10 are kept (2..9 when n > 48, where 9 blocks of 64 columns
-//    would not fit the 512 columns of tensor memory); the pairs of higher
-//    levels weigh at most about 2^-63 (2^-56) of the largest term;
+//    binary exponent E: x = v 2^(1077 - E), a signed integer |x| < 2^55
+//    (the part below 2^-55 of the largest entry is dropped), written in
+//    seven balanced base-256 digits, x = sum_{s=1..7} d_s 256^(7-s) with
+//    -128 <= d_s <= 127 (the bytes of x + 0x80808080808080, less 128;
+//    the leading digit takes the carry into bit 56 and reaches 128);
+//  * a digit is exactly a bf16, the product of two digits is at most 2^14
+//    in magnitude, and a sum of such products over K <= 64 entries and up
+//    to 7 digit pairs stays below 2^23, so the FP32 accumulation of the
+//    tensor cores is exact; the digit pairs (s, t) of one level L = s + t
+//    accumulate into one block of n (rounded up to 16) tensor-memory
+//    columns;
+//  * levels 2..9 are kept (8 blocks, at most 512 columns); the pairs of
+//    the higher levels weigh at most about 2^-64 of the largest term;
 //  * the epilogue reads the level sums, combines them exactly in 128-bit
 //    integers and rounds once to FP64 (round to nearest even), scaled by
 //    2^(E_J + E_p); results below the FP64 normal range are returned as 0.
 //
-// The error against the exact sum is thus about 2^-55 of
-// max_a |in[a][J]| * max_a |M[a][p]| (levels to 10), of the order of an
-// FP64 dot product's rounding error.
+// The error against the exact sum is thus about 2^-55 n of
+// max_a |in[a][J]| * max_a |M[a][p]| at worst (the digit truncation), of
+// the order of an FP64 dot product's rounding error, but normwise: an
+// entry far below the rest of its row keeps an absolute error of that size
+// where an FP64 dot product's error is componentwise.
 //
-// Layout: one CTA per SM (persistent), 128 threads; thread m owns row
-// J0 + m of the current tile of 128 rows in the split and in the epilogue
-// (the four warps read tensor-memory lanes 32w..32w+31, the rows of the
-// M = 128 accumulator).  The digits sit in shared memory in the canonical
+// Layout: one CTA per SM (persistent), 16 warps.  In the split four
+// threads share a row of the current tile of 128 rows (each takes every
+// fourth group of 8 entries; the row's exponent is the maximum of their
+// four partial maxima); in the epilogue warp w reads tensor-memory lanes
+// 32 (w mod 4) .. + 31 (the rows of the M = 128 accumulator) and every
+// fourth group of 8 columns.  The digits sit in shared memory in the canonical
 // K-major layout without swizzle (8 x 16-byte core matrices); U's digits
 // are made once per CTA.  The output tile (128 x n doubles, contiguous in
 // global memory) is staged in shared memory and written coalesced.
@@ -46,7 +52,9 @@
 namespace {
 
 constexpr int QTC_M = 128;        // rows (J) per tile = accumulator lanes
-constexpr int QTC_S = 8;          // digits per operand entry
+constexpr int QTC_PARTS = 4;      // threads per row in the split, warps per lane group in the epilogue
+constexpr int QTC_THREADS = QTC_M * QTC_PARTS;
+constexpr int QTC_S = 7;          // balanced base-256 digits per operand entry
 constexpr int QTC_TMEM_COLS = 512;
 constexpr long QTC_WAIT_LIMIT = 1L << 20;   // mbarrier polls before giving up
 
@@ -129,37 +137,44 @@ __device__ __forceinline__ uint32_t core_off(int row, int kgrp, int kg) {
   return (uint32_t)(((row >> 3) * kg + kgrp) * 128 + (row & 7) * 16);
 }
 
-// bf16 bits of the integer 0 <= c < 128 with the given sign bit: the FP32
-// value of c, made exactly with one FP32 subtraction, has at most 7
-// significant bits, so its upper half is c in bf16
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t c, uint32_t sign16) {
-  const float f = __uint_as_float(0x4B000000u | c) - 8388608.0f;
-  return (__float_as_uint(f) >> 16) | sign16;
-}
-
-// fixed point of one FP64 entry against the exponent e of its row (or
-// column): 56 bits, value = fx 2^(e - 1078); the sign in bit 15 of *sign16
-__device__ __forceinline__ uint64_t to_fixed(double v, int e, uint32_t* sign16) {
-  const uint64_t b = (uint64_t)__double_as_longlong(v);
-  const int ev = (int)((b >> 52) & 0x7FF);
-  *sign16 = (uint32_t)(b >> 48) & 0x8000u;
-  if (ev == 0) return 0;   // zero (subnormals count as zero)
-  const uint64_t m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 3;
-  const int sh = e - ev;
-  return sh < 57 ? (m >> sh) : 0ull;
-}
-
 __device__ __forceinline__ int biased_exp(double v) {
   return (int)(((uint64_t)__double_as_longlong(v) >> 52) & 0x7FF);
 }
 
-// eight bf16 digits of slice s (1-based) of eight consecutive entries
-__device__ __forceinline__ uint4 pack_slice(const uint64_t (&fx)[8], const uint32_t (&sg)[8], int s) {
-  const int sh = 56 - 7 * s;
-  uint32_t h[8];
+// fixed point of one FP64 entry against the exponent e of its row (or
+// column), x = v 2^(1077 - e) truncated (|x| < 2^55), returned as
+// x + 0x80808080808080: its bytes 5..0 and its bits 48 and up, less 128,
+// are the balanced digits d_7..d_2 and d_1 of x
+constexpr uint64_t QTC_BIAS = 0x0080808080808080ull;
+__device__ __forceinline__ uint64_t to_digits(double v, int e) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int ev = (int)((b >> 52) & 0x7FF);
+  if (ev == 0) return QTC_BIAS;   // zero (subnormals count as zero)
+  const uint64_t m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2;
+  const int sh = e - ev;
+  const uint64_t x = sh < 56 ? (m >> sh) : 0ull;
+  return ((int64_t)b < 0 ? QTC_BIAS - x : QTC_BIAS + x);
+}
+
+// bf16 of digit s (1-based) of eight consecutive entries, packed in pairs:
+// the byte b of y placed under the FP32 exponent of 2^23 gives 2^23 + b,
+// less 2^23 + 128 the digit, exactly, with at most 8 significant bits, so
+// the upper half of the FP32 value is the digit in bf16.  The leading digit
+// takes all of y >> 48 (0 .. 256): x up to 2^55 - 1 carries into bit 56,
+// so d_1 ranges over -128 .. 128, still exact in bf16 and still at most
+// 2^14 in any digit product.
+__device__ __forceinline__ uint4 pack_slice(const uint64_t (&y)[8], int s) {
+  const int byte = 7 - s;                       // 6 .. 0
+  const unsigned sel = (7u << 12) | (5u << 8) | (4u << 4) | (unsigned)(byte & 3);
+  uint32_t f[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) h[i] = digit_bf16((uint32_t)(fx[i] >> sh) & 127u, sg[i]);
-  return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t w = byte >= 4 ? (uint32_t)(y[i] >> 32) : (uint32_t)y[i];
+    const uint32_t bits = s == 1 ? (0x4B000000u | (uint32_t)(y[i] >> 48)) : __byte_perm(w, 0x4B000000u, sel);
+    f[i] = __float_as_uint(__uint_as_float(bits) - 8388736.0f);
+  }
+  return make_uint4(__byte_perm(f[0], f[1], 0x7632), __byte_perm(f[2], f[3], 0x7632),
+                    __byte_perm(f[4], f[5], 0x7632), __byte_perm(f[6], f[7], 0x7632));
 }
 
 // S 2^e2 rounded to the nearest FP64 (ties to even); 0 below the normal range
@@ -184,35 +199,69 @@ template <int NP>
 struct QtcCfg {
   static constexpr int KP = NP;                         // padded n along K
   static constexpr int KG = KP / 8;                     // core matrices along K
-  static constexpr int LV = NP <= 48 ? 9 : 8;           // levels kept: 2 .. LV + 1
+  static constexpr int LV = 8;                          // levels kept: 2 .. 9
+  static constexpr int CS = 256 / NP < QTC_S ? 256 / NP : QTC_S;   // digit slices of U per MMA (N <= 256)
   static constexpr int A_SLICE = QTC_M * KP * 2;        // bytes of one digit slice of a tile
   static constexpr int B_SLICE = NP * KP * 2;
   static constexpr int A_BYTES = QTC_S * A_SLICE;
   static constexpr int B_BYTES = QTC_S * B_SLICE;
   static constexpr int OFF_B = A_BYTES;
-  static constexpr int OFF_COLEXP = OFF_B + B_BYTES;
+  static constexpr int OFF_ROWEXP = OFF_B + B_BYTES;    // 4 partial maxima per row
+  static constexpr int OFF_COLEXP = OFF_ROWEXP + QTC_PARTS * QTC_M * 4;
   static constexpr int OFF_MBAR = OFF_COLEXP + 64 * 4;
   static constexpr int OFF_SLOT = OFF_MBAR + 8;
   static constexpr int BYTES = OFF_SLOT + 8;
   // one CTA per SM, so that each CTA's tensor-memory allocation is served at once
   static constexpr int SMEM = (BYTES + 1024 > 120 * 1024 ? BYTES + 1024 : 120 * 1024);
   static_assert(LV * NP <= QTC_TMEM_COLS, "level blocks exceed tensor memory");
+  static_assert(LV == 8, "the epilogue combines levels 2..9");
   static_assert(QTC_M * (NP + 1) * 8 <= A_BYTES, "output staging exceeds the digit buffer");
 };
 
+// One tile's digit products (issued by one thread).  Digit pair (s, t)
+// adds into the block of level s + t; U's digit slices lie one after the
+// other along N with the same stride as its 8-row groups, so one MMA takes
+// CS consecutive slices t0 .. t0 + CS - 1 of U against slice s of the tile
+// and writes CS consecutive level blocks.  The first MMA into each block
+// overwrites it: slice s = 1 reaches levels 2 .. 8, level 9 is first
+// reached by (s, t) = (2, 7).
 template <int NP>
-__global__ void __launch_bounds__(QTC_M, 1) k_qtrans_tc(int n, const double* __restrict__ in,
-                                                       const double* __restrict__ M, double* __restrict__ out,
-                                                       int64_t ntiles) {
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t As_a, uint32_t Bs_a) {
+  using C = QtcCfg<NP>;
+  constexpr uint32_t SBO = C::KG * 128;
+  auto issue = [&](int s, int t0, int cnt, bool acc0) {
+#pragma unroll
+    for (int kk = 0; kk < C::KP / 16; ++kk) {
+      const uint64_t ad = smem_desc(As_a + (s - 1) * C::A_SLICE + kk * 256, 128, SBO);
+      const uint64_t bd = smem_desc(Bs_a + (t0 - 1) * C::B_SLICE + kk * 256, 128, SBO);
+      mma_bf16(tmem + (uint32_t)((s + t0 - 2) * NP), ad, bd, mma_idesc(cnt * NP), (kk > 0 || acc0) ? 1 : 0);
+    }
+  };
+#pragma unroll 1
+  for (int s = 1; s <= QTC_S; ++s) {
+    int tmax = C::LV + 1 - s < QTC_S ? C::LV + 1 - s : QTC_S;
+    if (s == 2) {
+      issue(2, QTC_S, 1, false);
+      tmax = QTC_S - 1;
+    }
+    for (int t0 = 1; t0 <= tmax; t0 += C::CS) issue(s, t0, tmax - t0 + 1 < C::CS ? tmax - t0 + 1 : C::CS, s > 1);
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const double* __restrict__ in,
+                                                             const double* __restrict__ M, double* __restrict__ out,
+                                                             int64_t ntiles) {
   using C = QtcCfg<NP>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* As = sm;
   uint8_t* Bs = sm + C::OFF_B;
+  int* rowexp = reinterpret_cast<int*>(sm + C::OFF_ROWEXP);
   int* colexp = reinterpret_cast<int*>(sm + C::OFF_COLEXP);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + C::OFF_MBAR);
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + C::OFF_SLOT);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t N3 = (int64_t)n * n * n;
   const uint32_t mbar_a = smem_u32(mbar);
 
@@ -235,17 +284,15 @@ __global__ void __launch_bounds__(QTC_M, 1) k_qtrans_tc(int n, const double* __r
     colexp[p] = e;
 #pragma unroll 1
     for (int g = 0; g < C::KG; ++g) {
-      uint64_t fx[8];
-      uint32_t sg[8];
+      uint64_t y[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int a = g * 8 + i;
-        fx[i] = (p < n && a < n) ? to_fixed(M[a * n + p], e, &sg[i]) : 0ull;
-        if (!(p < n && a < n)) sg[i] = 0;
+        y[i] = (p < n && a < n) ? to_digits(M[a * n + p], e) : QTC_BIAS;
       }
 #pragma unroll
       for (int s = 1; s <= QTC_S; ++s)
-        *reinterpret_cast<uint4*>(Bs + (s - 1) * C::B_SLICE + core_off(p, g, C::KG)) = pack_slice(fx, sg, s);
+        *reinterpret_cast<uint4*>(Bs + (s - 1) * C::B_SLICE + core_off(p, g, C::KG)) = pack_slice(y, s);
     }
   }
   fence_proxy_async();
@@ -254,50 +301,52 @@ __global__ void __launch_bounds__(QTC_M, 1) k_qtrans_tc(int n, const double* __r
   fence_after_sync();
   const uint32_t tmem = *slot;
   const uint32_t As_a = smem_u32(As), Bs_a = smem_u32(Bs);
-  constexpr uint32_t idesc = mma_idesc(NP);
-  bool failed = false;
   uint32_t phase = 0;
+  // split: thread (row m, part q) takes the K groups q, q + 4, ... of row m
+  const int m_split = tid & (QTC_M - 1), q_split = tid >> 7;
+  // epilogue: warp w reads accumulator lanes 32 (w & 3) .. + 31 (its rows)
+  // and the column groups (w >> 2), (w >> 2) + 4, ...
+  const int m_epi = ((warp & 3) << 5) + lane, q_epi = warp >> 2;
+  constexpr int GPT = (C::KG + QTC_PARTS - 1) / QTC_PARTS;   // K groups per thread at most
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t J0 = tile * QTC_M;
-    const int64_t J = J0 + tid;
-    const bool valid = J < N3;
-    // this thread's row: load, exponent, digits
-    double v[NP];
+    {
+      const int64_t J = J0 + m_split;
+      const bool valid = J < N3;
+      double v[GPT][8];
+      int e = 0;
 #pragma unroll
-    for (int a = 0; a < NP; ++a) v[a] = (valid && a < n) ? __ldg(in + (int64_t)a * N3 + J) : 0.0;
-    int e = 0;
+      for (int j = 0; j < GPT; ++j) {
+        const int g = q_split + j * QTC_PARTS;
 #pragma unroll
-    for (int a = 0; a < NP; ++a) e = max(e, biased_exp(v[a]));
+        for (int i = 0; i < 8; ++i) {
+          const int a = g * 8 + i;
+          v[j][i] = (g < C::KG && valid && a < n) ? __ldg(in + (int64_t)a * N3 + J) : 0.0;
+          e = max(e, biased_exp(v[j][i]));
+        }
+      }
+      rowexp[q_split * QTC_M + m_split] = e;
+      __syncthreads();
 #pragma unroll
-    for (int g = 0; g < C::KG; ++g) {
-      uint64_t fx[8];
-      uint32_t sg[8];
+      for (int q = 0; q < QTC_PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_split]);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) fx[i] = to_fixed(v[g * 8 + i], e, &sg[i]);
+      for (int j = 0; j < GPT; ++j) {
+        const int g = q_split + j * QTC_PARTS;
+        if (g >= C::KG) break;
+        uint64_t y[8];
 #pragma unroll
-      for (int s = 1; s <= QTC_S; ++s)
-        *reinterpret_cast<uint4*>(As + (s - 1) * C::A_SLICE + core_off(tid, g, C::KG)) = pack_slice(fx, sg, s);
+        for (int i = 0; i < 8; ++i) y[i] = to_digits(v[j][i], e);
+#pragma unroll
+        for (int s = 1; s <= QTC_S; ++s)
+          *reinterpret_cast<uint4*>(As + (s - 1) * C::A_SLICE + core_off(m_split, g, C::KG)) = pack_slice(y, s);
+      }
     }
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-#pragma unroll 1
-      for (int li = 0; li < C::LV; ++li) {
-        const int L = li + 2;
-        int acc = 0;
-        for (int s = (L - QTC_S > 1 ? L - QTC_S : 1); s <= (L - 1 < QTC_S ? L - 1 : QTC_S); ++s) {
-          const int t = L - s;
-#pragma unroll
-          for (int kk = 0; kk < C::KP / 16; ++kk) {
-            const uint64_t ad = smem_desc(As_a + (s - 1) * C::A_SLICE + kk * 256, 128, C::KG * 128);
-            const uint64_t bd = smem_desc(Bs_a + (t - 1) * C::B_SLICE + kk * 256, 128, C::KG * 128);
-            mma_bf16(tmem + (uint32_t)(li * NP), ad, bd, idesc, acc);
-            acc = 1;
-          }
-        }
-      }
+      issue_products<NP>(tmem, As_a, Bs_a);
       mma_commit(mbar_a);
     }
     bool ok = mbar_wait_bounded(mbar_a, phase);
@@ -306,50 +355,55 @@ __global__ void __launch_bounds__(QTC_M, 1) k_qtrans_tc(int n, const double* __r
       mbar_wait_bounded(mbar_a, phase);   // let products still in flight finish
     }
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
+    if (__syncthreads_or(!ok)) break;
     fence_after_sync();
     // epilogue: the level sums of this row, combined exactly and rounded;
     // staged in the (now free) digit buffer as rows of n + 1 doubles
-    double* stage = reinterpret_cast<double*>(As);
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    {
+      double* stage = reinterpret_cast<double*>(As);
+      int e = 0;
+#pragma unroll
+      for (int q = 0; q < QTC_PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_epi]);
+      const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-    for (int cc = 0; cc < NP / 8; ++cc) {
-      uint32_t r[C::LV][8];
+      for (int cc = q_epi; cc < NP / 8; cc += QTC_PARTS) {
+        uint32_t r[C::LV][8];
 #pragma unroll
-      for (int li = 0; li < C::LV; ++li) tmem_ld8(lane_base + (uint32_t)(li * NP + cc * 8), r[li]);
-      tmem_wait_ld();
+        for (int li = 0; li < C::LV; ++li) tmem_ld8(lane_base + (uint32_t)(li * NP + cc * 8), r[li]);
+        tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int p = cc * 8 + j;
-        if (p >= n) break;
-        // levels split in two exact 64-bit Horner sums (each level sum is
-        // an integer below 2^23 in magnitude)
-        constexpr int NLO = C::LV < 5 ? C::LV : 5;
-        long long hi = 0, lo = 0;
+        for (int j = 0; j < 8; ++j) {
+          const int p = cc * 8 + j;
+          if (p >= n) break;
+          // S = sum_L D_L 256^(9 - L), as two exact 64-bit Horner sums
+          // over levels 2..5 and 6..9 (each level sum is an integer below
+          // 2^23 in magnitude); the product is S 2^(E_J + E_p - 2114)
+          long long hi = 0, lo = 0;
 #pragma unroll
-        for (int li = 0; li < C::LV - NLO; ++li) hi = hi * 128 + __float2int_rn(__uint_as_float(r[li][j]));
+          for (int li = 0; li < 4; ++li) hi = hi * 256 + __float2int_rn(__uint_as_float(r[li][j]));
 #pragma unroll
-        for (int li = C::LV - NLO; li < C::LV; ++li) lo = lo * 128 + __float2int_rn(__uint_as_float(r[li][j]));
-        const __int128 S = ((__int128)hi << (7 * NLO)) + (__int128)lo;
-        const int e2 = e + colexp[p] - 2044 - 7 * (C::LV + 1);
-        stage[tid * (n + 1) + p] = (e == 0 || colexp[p] == 0) ? 0.0 : round_scaled(S, e2);
+          for (int li = 4; li < 8; ++li) lo = lo * 256 + __float2int_rn(__uint_as_float(r[li][j]));
+          const __int128 S = ((__int128)hi << 32) + (__int128)lo;
+          const int ce = colexp[p];
+          const int e2 = e + ce - 2114;
+          stage[m_epi * (n + 1) + p] = (e == 0 || ce == 0) ? 0.0 : round_scaled(S, e2);
+        }
       }
     }
     fence_before_sync();
     __syncthreads();
     // the tile's rows are contiguous in out: write them coalesced
-    const int64_t rows = (N3 - J0) < QTC_M ? (N3 - J0) : QTC_M;
-    const int cnt = (int)rows * n;
-    for (int i = tid; i < cnt; i += QTC_M) {
-      const int m = i / n, p = i - m * n;
-      out[J0 * n + i] = stage[m * (n + 1) + p];
+    {
+      const double* stage = reinterpret_cast<const double*>(As);
+      const int64_t rows = (N3 - J0) < QTC_M ? (N3 - J0) : QTC_M;
+      const int cnt = (int)rows * n;
+      for (int i = tid; i < cnt; i += QTC_THREADS) {
+        const int m = i / n, p = i - m * n;
+        out[J0 * n + i] = stage[m * (n + 1) + p];
+      }
     }
     __syncthreads();
   }
-  (void)failed;
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -379,7 +433,7 @@ hci_status launch(cudaStream_t st, int n, const double* in, const double* M, dou
   const int64_t N3 = (int64_t)n * n * n;
   const int64_t ntiles = (N3 + QTC_M - 1) / QTC_M;
   const int grid = (int)(ntiles < g_qtc_nsm[dev] ? ntiles : g_qtc_nsm[dev]);
-  HCI_LAUNCH(k_qtrans_tc<NP>, grid, QTC_M, C::SMEM, st)(n, in, M, out, ntiles);
+  HCI_LAUNCH(k_qtrans_tc<NP>, grid, QTC_THREADS, C::SMEM, st)(n, in, M, out, ntiles);
   return cudaGetLastError() == cudaSuccess ? HCI_OK : HCI_ERR_CUDA;
 }
 

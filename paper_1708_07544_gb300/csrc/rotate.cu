@@ -338,6 +338,17 @@ extern "C" hci_status hci_rotate_backward(int norb, const double* kappa, const d
   return HCI_OK;
 }
 
+extern "C" hci_status hci_qtrans(int norb, const double* in, const double* M, double* out, int check,
+                                 void* stream) {
+  const int n = norb;
+  if (n < 1 || n > HCI_MAXORB) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_qtrans: norb=%d outside [1,64]", n);
+  if (!in || !M || !out) return hci_fail(nullptr, HCI_ERR_INVALID, "hci_qtrans: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  QTRANS("hci_qtrans", in, M, out);
+  if (check) QTRANS_CHECK("hci_qtrans");
+  return HCI_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free rotation.
 //
