@@ -26,8 +26,8 @@
 //    columns;
 //  * levels 2..9 are kept (8 blocks, at most 512 columns); the pairs of
 //    the higher levels weigh at most about 2^-64 of the largest term;
-//  * the epilogue reads the level sums, combines them exactly in 128-bit
-//    integers and rounds once to FP64 (round to nearest even), scaled by
+//  * the epilogue reads the level sums, combines them exactly in 64-bit
+//    integers (an 80-bit sum in two words) and rounds once to FP64 (round to nearest even), scaled by
 //    2^(E_J + E_p); results below the FP64 normal range are returned as 0.
 //
 // The error against the exact sum is thus about 2^-55 n of
@@ -41,7 +41,7 @@
 // fourth group of 8 entries; the row's exponent is the maximum of their
 // four partial maxima); in the epilogue warp w reads tensor-memory lanes
 // 32 (w mod 4) .. + 31 (the rows of the M = 128 accumulator) and every
-// fourth group of 8 columns.  The digits sit in shared memory in the canonical
+// fourth group of 4 columns.  The digits sit in shared memory in the canonical
 // K-major layout without swizzle (8 x 16-byte core matrices); U's digits
 // are made once per CTA.  The output tile (128 x n doubles, contiguous in
 // global memory) is staged in shared memory and written coalesced.
@@ -122,10 +122,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
   return false;
 }
 
-// 32 lanes x 8 columns of 32 bits: thread t gets lane (base lane + t)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+// 32 lanes x 4 columns of 32 bits: thread t gets lane (base lane + t)
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr)
                : "memory");
 }
@@ -177,19 +177,33 @@ __device__ __forceinline__ uint4 pack_slice(const uint64_t (&y)[8], int s) {
                     __byte_perm(f[4], f[5], 0x7632), __byte_perm(f[6], f[7], 0x7632));
 }
 
-// S 2^e2 rounded to the nearest FP64 (ties to even); 0 below the normal range
-__device__ __forceinline__ double round_scaled(__int128 S, int e2) {
-  if (S == 0) return 0.0;
-  const unsigned long long sign = S < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned __int128 m = S < 0 ? (unsigned __int128)(-S) : (unsigned __int128)S;
-  const unsigned long long mh = (unsigned long long)(m >> 64), ml = (unsigned long long)m;
-  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
-  m <<= lz;   // leading one at bit 127
-  const unsigned long long top = (unsigned long long)(m >> 64), rest = (unsigned long long)m;
-  unsigned long long mant = top >> 11;   // 53 bits
-  const unsigned long long rb = top & 0x7FFull;
-  if (rb > 0x400ull || (rb == 0x400ull && (rest != 0ull || (mant & 1ull)))) ++mant;
-  const int e = 127 - lz + e2;   // exponent of the leading one
+// (T 2^32 + b) 2^e2 rounded to the nearest FP64 (ties to even), for
+// |T| < 2^47 and 0 <= b < 2^32; 0 below the normal range.  The magnitude
+// (at most 79 bits) is normalised into one 64-bit word: exactly when it is
+// below 2^63, else its top 64 bits with the rest of b as sticky bits.
+__device__ __forceinline__ double round_tb(long long T, uint32_t b, int e2) {
+  if (T == 0 && b == 0u) return 0.0;
+  const unsigned long long sign = T < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long Tm = T < 0 ? (unsigned long long)(-T) - (b != 0u ? 1ull : 0ull) : (unsigned long long)T;
+  const uint32_t bm = T < 0 ? 0u - b : b;
+  unsigned long long X;
+  int e;
+  bool sticky;
+  if ((Tm >> 31) == 0ull) {
+    const unsigned long long Y = (Tm << 32) | bm;
+    const int lz = __clzll((long long)Y);
+    X = Y << lz;
+    e = 63 - lz + e2;
+    sticky = false;
+  } else {
+    const int lz = __clzll((long long)Tm);   // 17 .. 32
+    X = (Tm << lz) | (unsigned long long)(bm >> (32 - lz));
+    sticky = (bm & ((1u << (32 - lz)) - 1u)) != 0u;
+    e = 95 - lz + e2;
+  }
+  unsigned long long mant = X >> 11;   // 53 bits
+  const unsigned long long rb = X & 0x7FFull;
+  if (rb > 0x400ull || (rb == 0x400ull && (sticky || (mant & 1ull)))) ++mant;
   if (e < -1022) return __longlong_as_double((long long)sign);
   if (e > 1023) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
   return __longlong_as_double((long long)(sign | (((unsigned long long)(e + 1022) << 52) + mant)));
@@ -309,23 +323,33 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
   const int m_epi = ((warp & 3) << 5) + lane, q_epi = warp >> 2;
   constexpr int GPT = (C::KG + QTC_PARTS - 1) / QTC_PARTS;   // K groups per thread at most
 
+  // this thread's entries of a tile: K groups q_split, q_split + 4, ...
+  // of row m_split, loaded one tile ahead so that the loads of the next
+  // tile are in flight during this tile's products and epilogue
+  double v[GPT][8];
+  auto load_tile = [&](int64_t tile) {
+    const int64_t J = tile * QTC_M + m_split;
+    const bool valid = tile < ntiles && J < N3;
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int g = q_split + j * QTC_PARTS;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int a = g * 8 + i;
+        v[j][i] = (g < C::KG && valid && a < n) ? __ldg(in + (int64_t)a * N3 + J) : 0.0;
+      }
+    }
+  };
+  load_tile(blockIdx.x);
+
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t J0 = tile * QTC_M;
     {
-      const int64_t J = J0 + m_split;
-      const bool valid = J < N3;
-      double v[GPT][8];
       int e = 0;
 #pragma unroll
-      for (int j = 0; j < GPT; ++j) {
-        const int g = q_split + j * QTC_PARTS;
+      for (int j = 0; j < GPT; ++j)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int a = g * 8 + i;
-          v[j][i] = (g < C::KG && valid && a < n) ? __ldg(in + (int64_t)a * N3 + J) : 0.0;
-          e = max(e, biased_exp(v[j][i]));
-        }
-      }
+        for (int i = 0; i < 8; ++i) e = max(e, biased_exp(v[j][i]));
       rowexp[q_split * QTC_M + m_split] = e;
       __syncthreads();
 #pragma unroll
@@ -349,10 +373,15 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
       issue_products<NP>(tmem, As_a, Bs_a);
       mma_commit(mbar_a);
     }
-    bool ok = mbar_wait_bounded(mbar_a, phase);
-    if (!ok) {
-      atomicExch(&g_qtc_timeout, 1);
-      mbar_wait_bounded(mbar_a, phase);   // let products still in flight finish
+    load_tile(tile + gridDim.x);
+    // one warp polls the barrier; the others wait at the block barrier
+    bool ok = true;
+    if (warp == 0) {
+      ok = mbar_wait_bounded(mbar_a, phase);
+      if (!ok) {
+        atomicExch(&g_qtc_timeout, 1);
+        mbar_wait_bounded(mbar_a, phase);   // let products still in flight finish
+      }
     }
     phase ^= 1u;
     if (__syncthreads_or(!ok)) break;
@@ -366,27 +395,28 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
       for (int q = 0; q < QTC_PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_epi]);
       const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-      for (int cc = q_epi; cc < NP / 8; cc += QTC_PARTS) {
-        uint32_t r[C::LV][8];
+      for (int cc = q_epi; cc < NP / 4; cc += QTC_PARTS) {
+        uint32_t r[C::LV][4];
 #pragma unroll
-        for (int li = 0; li < C::LV; ++li) tmem_ld8(lane_base + (uint32_t)(li * NP + cc * 8), r[li]);
+        for (int li = 0; li < C::LV; ++li) tmem_ld4(lane_base + (uint32_t)(li * NP + cc * 4), r[li]);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int p = cc * 8 + j;
+        for (int j = 0; j < 4; ++j) {
+          const int p = cc * 4 + j;
           if (p >= n) break;
-          // S = sum_L D_L 256^(9 - L), as two exact 64-bit Horner sums
-          // over levels 2..5 and 6..9 (each level sum is an integer below
-          // 2^23 in magnitude); the product is S 2^(E_J + E_p - 2114)
-          long long hi = 0, lo = 0;
+          // S = sum_L D_L 256^(9 - L) (each level sum D_L an integer below
+          // 2^23 in magnitude): pairs of levels in 32 bits, then levels
+          // 2..5 and 6..9 in 64 bits, S = hi 2^32 + lo = T 2^32 + b; the
+          // product is S 2^(E_J + E_p - 2114)
+          int d[8];
 #pragma unroll
-          for (int li = 0; li < 4; ++li) hi = hi * 256 + __float2int_rn(__uint_as_float(r[li][j]));
-#pragma unroll
-          for (int li = 4; li < 8; ++li) lo = lo * 256 + __float2int_rn(__uint_as_float(r[li][j]));
-          const __int128 S = ((__int128)hi << 32) + (__int128)lo;
+          for (int li = 0; li < 8; ++li) d[li] = __float2int_rn(__uint_as_float(r[li][j]));
+          const long long hi = (long long)(d[0] * 256 + d[1]) * 65536 + (d[2] * 256 + d[3]);
+          const long long lo = (long long)(d[4] * 256 + d[5]) * 65536 + (d[6] * 256 + d[7]);
+          const long long T = hi + (lo >> 32);
           const int ce = colexp[p];
           const int e2 = e + ce - 2114;
-          stage[m_epi * (n + 1) + p] = (e == 0 || ce == 0) ? 0.0 : round_scaled(S, e2);
+          stage[m_epi * (n + 1) + p] = (e == 0 || ce == 0) ? 0.0 : round_tb(T, (uint32_t)lo, e2);
         }
       }
     }
@@ -397,8 +427,10 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
       const double* stage = reinterpret_cast<const double*>(As);
       const int64_t rows = (N3 - J0) < QTC_M ? (N3 - J0) : QTC_M;
       const int cnt = (int)rows * n;
+      // i / n as (i ceil(2^20 / n)) >> 20, exact for i < 2^13, n <= 64
+      const uint32_t inv = ((1u << 20) + (uint32_t)n - 1u) / (uint32_t)n;
       for (int i = tid; i < cnt; i += QTC_THREADS) {
-        const int m = i / n, p = i - m * n;
+        const int m = (int)(((uint32_t)i * inv) >> 20), p = i - m * n;
         out[J0 * n + i] = stage[m * (n + 1) + p];
       }
     }
