@@ -39,9 +39,10 @@
 // Layout: one CTA per SM (persistent), 16 warps.  In the split four
 // threads share a row of the current tile of 128 rows (each takes every
 // fourth group of 8 entries; the row's exponent is the maximum of their
-// four partial maxima); in the epilogue warp w reads tensor-memory lanes
-// 32 (w mod 4) .. + 31 (the rows of the M = 128 accumulator) and every
-// fourth group of 4 columns.  The digits sit in shared memory in the canonical
+// partial maxima), and each thread's entries of the next tile are loaded
+// while the tensor cores work on this one; in the epilogue warp w reads
+// tensor-memory lanes 32 (w mod 4) .. + 31 (the rows of the M = 128
+// accumulator) and every fourth group of 4 columns.  The digits sit in shared memory in the canonical
 // K-major layout without swizzle (8 x 16-byte core matrices); U's digits
 // are made once per CTA.  The output tile (128 x n doubles, contiguous in
 // global memory) is staged in shared memory and written coalesced.
@@ -52,8 +53,6 @@
 namespace {
 
 constexpr int QTC_M = 128;        // rows (J) per tile = accumulator lanes
-constexpr int QTC_PARTS = 4;      // threads per row in the split, warps per lane group in the epilogue
-constexpr int QTC_THREADS = QTC_M * QTC_PARTS;
 constexpr int QTC_S = 7;          // balanced base-256 digits per operand entry
 constexpr int QTC_TMEM_COLS = 512;
 constexpr long QTC_WAIT_LIMIT = 1L << 20;   // mbarrier polls before giving up
@@ -214,6 +213,11 @@ struct QtcCfg {
   static constexpr int KP = NP;                         // padded n along K
   static constexpr int KG = KP / 8;                     // core matrices along K
   static constexpr int LV = 8;                          // levels kept: 2 .. 9
+  // threads per row in the split and warps per lane group in the epilogue
+  // (three, which shares the 6 entry groups and 12 column groups of
+  // n <= 48 evenly, measured slower: fewer warps hide less latency)
+  static constexpr int PARTS = 4;
+  static constexpr int THREADS = QTC_M * PARTS;
   static constexpr int CS = 256 / NP < QTC_S ? 256 / NP : QTC_S;   // digit slices of U per MMA (N <= 256)
   static constexpr int A_SLICE = QTC_M * KP * 2;        // bytes of one digit slice of a tile
   static constexpr int B_SLICE = NP * KP * 2;
@@ -221,7 +225,7 @@ struct QtcCfg {
   static constexpr int B_BYTES = QTC_S * B_SLICE;
   static constexpr int OFF_B = A_BYTES;
   static constexpr int OFF_ROWEXP = OFF_B + B_BYTES;    // 4 partial maxima per row
-  static constexpr int OFF_COLEXP = OFF_ROWEXP + QTC_PARTS * QTC_M * 4;
+  static constexpr int OFF_COLEXP = OFF_ROWEXP + 4 * QTC_M * 4;
   static constexpr int OFF_MBAR = OFF_COLEXP + 64 * 4;
   static constexpr int OFF_SLOT = OFF_MBAR + 8;
   static constexpr int BYTES = OFF_SLOT + 8;
@@ -263,7 +267,7 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t As_a, uin
 }
 
 template <int NP>
-__global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const double* __restrict__ in,
+__global__ void __launch_bounds__(QtcCfg<NP>::THREADS, 1) k_qtrans_tc(int n, const double* __restrict__ in,
                                                              const double* __restrict__ M, double* __restrict__ out,
                                                              int64_t ntiles) {
   using C = QtcCfg<NP>;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
   // epilogue: warp w reads accumulator lanes 32 (w & 3) .. + 31 (its rows)
   // and the column groups (w >> 2), (w >> 2) + 4, ...
   const int m_epi = ((warp & 3) << 5) + lane, q_epi = warp >> 2;
-  constexpr int GPT = (C::KG + QTC_PARTS - 1) / QTC_PARTS;   // K groups per thread at most
+  constexpr int GPT = (C::KG + C::PARTS - 1) / C::PARTS;   // K groups per thread at most
 
   // this thread's entries of a tile: K groups q_split, q_split + 4, ...
   // of row m_split, loaded one tile ahead so that the loads of the next
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
     const bool valid = tile < ntiles && J < N3;
 #pragma unroll
     for (int j = 0; j < GPT; ++j) {
-      const int g = q_split + j * QTC_PARTS;
+      const int g = q_split + j * C::PARTS;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int a = g * 8 + i;
@@ -353,10 +357,10 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
       rowexp[q_split * QTC_M + m_split] = e;
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < QTC_PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_split]);
+      for (int q = 0; q < C::PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_split]);
 #pragma unroll
       for (int j = 0; j < GPT; ++j) {
-        const int g = q_split + j * QTC_PARTS;
+        const int g = q_split + j * C::PARTS;
         if (g >= C::KG) break;
         uint64_t y[8];
 #pragma unroll
@@ -392,10 +396,10 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
       double* stage = reinterpret_cast<double*>(As);
       int e = 0;
 #pragma unroll
-      for (int q = 0; q < QTC_PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_epi]);
+      for (int q = 0; q < C::PARTS; ++q) e = max(e, rowexp[q * QTC_M + m_epi]);
       const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-      for (int cc = q_epi; cc < NP / 4; cc += QTC_PARTS) {
+      for (int cc = q_epi; cc < NP / 4; cc += C::PARTS) {
         uint32_t r[C::LV][4];
 #pragma unroll
         for (int li = 0; li < C::LV; ++li) tmem_ld4(lane_base + (uint32_t)(li * NP + cc * 4), r[li]);
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(QTC_THREADS, 1) k_qtrans_tc(int n, const doubl
       const int cnt = (int)rows * n;
       // i / n as (i ceil(2^20 / n)) >> 20, exact for i < 2^13, n <= 64
       const uint32_t inv = ((1u << 20) + (uint32_t)n - 1u) / (uint32_t)n;
-      for (int i = tid; i < cnt; i += QTC_THREADS) {
+      for (int i = tid; i < cnt; i += C::THREADS) {
         const int m = (int)(((uint32_t)i * inv) >> 20), p = i - m * n;
         out[J0 * n + i] = stage[m * (n + 1) + p];
       }
@@ -465,7 +469,7 @@ hci_status launch(cudaStream_t st, int n, const double* in, const double* M, dou
   const int64_t N3 = (int64_t)n * n * n;
   const int64_t ntiles = (N3 + QTC_M - 1) / QTC_M;
   const int grid = (int)(ntiles < g_qtc_nsm[dev] ? ntiles : g_qtc_nsm[dev]);
-  HCI_LAUNCH(k_qtrans_tc<NP>, grid, QTC_THREADS, C::SMEM, st)(n, in, M, out, ntiles);
+  HCI_LAUNCH(k_qtrans_tc<NP>, grid, C::THREADS, C::SMEM, st)(n, in, M, out, ntiles);
   return cudaGetLastError() == cudaSuccess ? HCI_OK : HCI_ERR_CUDA;
 }
 
