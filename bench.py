@@ -257,6 +257,7 @@ def gpu_arm(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
+    torch.cuda.nvtx.range_push("timed_steps")
     ev0.record()
     recs = []
     rec = {}
@@ -265,6 +266,7 @@ def gpu_arm(args):
         step(h_d, eri_d, k_d, rec)
         recs.append({k: rec[k] for k in ("timers", "stats", "nV", "E", "iters")})
     ev1.record()
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = _abi.hci_launch_count() - l0
     clk = clocks.stop()
