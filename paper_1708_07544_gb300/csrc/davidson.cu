@@ -151,9 +151,15 @@ __global__ void __launch_bounds__(JW * 32) k_jacobi(DavDev* d, int k) {
           const double apq = A[p][q], app = A[p][p], aqq = A[q][q];
           const double g = 100.0 * fabs(apq);
           if (!((fabs(app) + g == fabs(app) && fabs(aqq) + g == fabs(aqq)) || fabs(apq) < 1e-300)) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+            // tan of the rotation angle, t = sgn(tau) / (|tau| + sqrt(1 +
+            // tau^2)) with tau = (aqq - app) / (2 apq), written without the
+            // division for tau (one square root, one division and one
+            // reciprocal square root on this part's narrow FP64 pipe; the
+            // entries are Rayleigh quotients of normalised vectors, far
+            // from overflow)
+            const double dd = aqq - app, e2 = 2.0 * apq;
+            const double tt = copysign(1.0, dd) * e2 / (fabs(dd) + sqrt(dd * dd + e2 * e2));
+            c = rsqrt(1.0 + tt * tt);
             sn = tt * c;
             active = 1;
           }
