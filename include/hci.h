@@ -379,9 +379,8 @@ hci_status hci_rotate_backward(int norb, const double* kappa, const double* h, c
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it for the CUDA context that is current;
  * a call made in another context (after a device reset, or from a context
- * the caller created) looks the address up again.  Make the first call on a
- * device, and the first after a reset, before any stream capture.  All
- * calls share the array: calls that overlap on the GPU (other streams,
+ * the caller created) looks the address up again.  All calls share the
+ * array: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
  * Synchronises the stream. */
 hci_status hci_rotate_noalloc(int norb, const double* kappa, const double* h, const double* eri, double* U,
