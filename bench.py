@@ -487,7 +487,7 @@ def gpu_arm(args):
             lnV = int(lk.shape[0])
             form = "direct" if lst["sigma_direct"] else ("one orientation" if lst["graph_half"] else "both orientations")
             lnnz = lst["graph_nnz"]
-            large = {"workload": f"synthetic DF (44e,44o) at {hi.DF44_LARGE_SCALE_FACTOR} of the survey's scale, eps1=1e-4",
+            large = {"workload": f"synthetic DF (44e,44o), factor scale {hi.DF44_LARGE_SCALE_FACTOR} x sqrt(0.5/sum w_P^2), eps1=1e-4",
                      "nV": lnV, "E": lE, "selections": lit, "solve_s": round(t1 - t0, 3), "rdm_s": round(t2 - t1, 3),
                      "graph_form": form, "graph_nnz": lnnz, "sigma_calls": lst["sigma_calls"],
                      "sigma_ms": round(1e3 * min(lsig), 2),

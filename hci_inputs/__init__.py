@@ -274,7 +274,7 @@ def df_44o(scale: float | None = None) -> Instance:
     return df_instance(44, 176, 1707, decay=40.0, h_diag=hd, scale=sc, name="df_44o_44e")
 
 
-# A second (44e,44o) size at 0.235 of the survey's scale: with the bench's
+# A second (44e,44o) size at 0.235 of sqrt(0.5/sum w_P^2): with the bench's
 # kappa (seed 1709, sigma 0.01) the space converges to |V| = 1.03e7 at
 # eps1 = 1e-4 (3.2e10 connections), the ~1e7 determinants of the Fe(P)
 # (44o,44e) calculations the instance stands in for.
@@ -282,7 +282,8 @@ DF44_LARGE_SCALE_FACTOR = 0.235
 
 
 def df_44o_large() -> Instance:
-    """(44e,44o) as df_44o at DF44_LARGE_SCALE_FACTOR of the survey's scale."""
+    """(44e,44o) as df_44o with factor scale DF44_LARGE_SCALE_FACTOR x
+    sqrt(0.5/sum w_P^2) (df_44o uses DF44_SCALE_FACTOR x the same)."""
     w = np.exp(-np.arange(176) / 40.0)
     inst = df_44o(scale=DF44_LARGE_SCALE_FACTOR * math.sqrt(0.5 / float(np.sum(w ** 2))))
     inst.name = "df_44o_44e_large"
