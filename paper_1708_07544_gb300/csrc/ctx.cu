@@ -317,7 +317,7 @@ extern "C" hci_status hci_destroy(hci_ctx* ctx) {
                     &ctx->g_permb, &ctx->g_bkeys, &ctx->g_bkeys2, &ctx->g_nbr_ptr, &ctx->g_nbr, &ctx->g_cnt,
                     &ctx->d_vb, &ctx->d_wb, &ctx->d_diag, &ctx->d_small, &ctx->d_part,
                     &ctx->g_bnbr_ptr, &ctx->g_bnbr, &ctx->g_costa, &ctx->g_costb, &ctx->s_walkstat,
-                    &ctx->g_htab, &ctx->g_hval, &ctx->s_rdmw, &ctx->g_posb, &ctx->g_vb, &ctx->g_ba,
+                    &ctx->g_htab, &ctx->g_hval, &ctx->g_nscr, &ctx->s_rdmw, &ctx->g_posb, &ctx->g_vb, &ctx->g_ba,
                     &ctx->inc.pos_old, &ctx->inc.mark, &ctx->inc.flag, &ctx->inc.newrows, &ctx->inc.rpN,
                     &ctx->inc.cnt, &ctx->inc.keys_old, &ctx->inc.s2i_old, &ctx->inc.grow,
                     &ctx->inc.colN, &ctx->inc.valN, &ctx->inc.hist, &ctx->inc.tbase, &ctx->inc.T, &ctx->inc.T2,

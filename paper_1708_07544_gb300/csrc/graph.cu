@@ -602,11 +602,14 @@ __global__ void __launch_bounds__(256) k_row_values(const int32_t* __restrict__ 
 // distinct string with nocc electrons; count pass (out == nullptr) or fill
 // pass.  The nocc * (n - nocc) occupied -> empty pairs are enumerated from
 // per-warp occupied / empty lists, p-major, so each list is in (p, r) order.
+// With scr, the count pass also writes string g's list at scr + g L (L =
+// nocc (n - nocc), its largest possible length), for k_compact_nbrs.
 __global__ void __launch_bounds__(256) k_alpha_nbrs(int n, int nocc, const uint64_t* __restrict__ ua, int64_t nua,
                                                     const int64_t* __restrict__ ptr, int64_t* __restrict__ cnt,
                                                     int32_t* __restrict__ out,
                                                     const unsigned long long* __restrict__ tab,
-                                                    const int32_t* __restrict__ tval, uint64_t mask) {
+                                                    const int32_t* __restrict__ tval, uint64_t mask,
+                                                    int32_t* __restrict__ scr) {
   __shared__ int s_occ[8][HCI_MAXORB];
   __shared__ int s_vir[8][HCI_MAXORB];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -625,10 +628,24 @@ __global__ void __launch_bounds__(256) k_alpha_nbrs(int n, int nocc, const uint6
       const bool hit = idx >= 0;
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (out && hit) out[w + c + __popc(m & ((1u << lane) - 1u))] = idx;
+      if (scr && hit) scr[g * L + c + __popc(m & ((1u << lane) - 1u))] = idx;
       c += __popc(m);
     }
     if (!out && lane == 0) cnt[g] = c;
     __syncwarp();
+  }
+}
+
+// list of string g from its padded slot scr + g L to out + ptr[g]
+__global__ void __launch_bounds__(256) k_compact_nbrs(const int32_t* __restrict__ scr, int L,
+                                                      const int64_t* __restrict__ ptr, int64_t nua,
+                                                      int32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < nua; g += nwarps) {
+    const int64_t b = ptr[g], len = ptr[g + 1] - b;
+    for (int64_t k = lane; k < len; k += 32) out[b + k] = scr[g * L + k];
   }
 }
 
@@ -1290,18 +1307,29 @@ static hci_status build_space(hci_ctx* ctx, int64_t nV, GraphArgs& A) {
     HCI_TRY(ensure_buf(ctx, *ptrs[s], (size_t)(nu[s] + 1) * 8));
     HCI_TRY(ensure_buf(ctx, *costs[s], (size_t)(nu[s] + 1) * 8));
     const int gw = grid_for(nu[s] * 32, 256);
+    // one pass of hash look-ups when the padded lists (every string's
+    // largest possible list) take at most 1 GB, else a count pass and a
+    // fill pass
+    const int Lown = nel[s] * (n - nel[s]);
+    const size_t scr_bytes = (size_t)nu[s] * (size_t)(Lown > 0 ? Lown : 1) * 4;
+    const bool one_pass = scr_bytes <= ((size_t)1 << 30);
+    if (one_pass) HCI_TRY(ensure_buf(ctx, ctx->g_nscr, scr_bytes));
     HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, nel[s], uniq[s], nu[s], nullptr, bp<int64_t>(ctx->g_cnt), nullptr,
                                                    bp<unsigned long long>(ctx->g_htab), bp<int32_t>(ctx->g_hval),
-                                                   tsize - 1);
+                                                   tsize - 1, one_pass ? bp<int32_t>(ctx->g_nscr) : nullptr);
     HCI_TRY(scan_i64(ctx, bp<int64_t>(ctx->g_cnt), bp<int64_t>(*ptrs[s]), nu[s], dtot));
     HCI_LAUNCH(k_store_at, 1, 1, 0, ctx->st)(bp<int64_t>(*ptrs[s]), nu[s], dtot);
     int64_t nn = 0;
     HCI_CUDA(ctx, cudaMemcpyAsync(&nn, dtot, 8, cudaMemcpyDeviceToHost, ctx->st));
     HCI_CUDA(ctx, cudaStreamSynchronize(ctx->st));
     HCI_TRY(ensure_buf(ctx, *lists[s], (size_t)(nn + 1) * 4));
-    HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, nel[s], uniq[s], nu[s], bp<int64_t>(*ptrs[s]), nullptr,
-                                                   bp<int32_t>(*lists[s]), bp<unsigned long long>(ctx->g_htab),
-                                                   bp<int32_t>(ctx->g_hval), tsize - 1);
+    if (one_pass)
+      HCI_LAUNCH(k_compact_nbrs, gw, 256, 0, ctx->st)(bp<int32_t>(ctx->g_nscr), Lown, bp<int64_t>(*ptrs[s]), nu[s],
+                                                       bp<int32_t>(*lists[s]));
+    else
+      HCI_LAUNCH(k_alpha_nbrs, gw, 256, 0, ctx->st)(n, nel[s], uniq[s], nu[s], bp<int64_t>(*ptrs[s]), nullptr,
+                                                     bp<int32_t>(*lists[s]), bp<unsigned long long>(ctx->g_htab),
+                                                     bp<int32_t>(ctx->g_hval), tsize - 1, nullptr);
     HCI_LAUNCH(k_nbr_cost, gw, 256, 0, ctx->st)(bp<int64_t>(*ptrs[s]), bp<int32_t>(*lists[s]), gstart[s], nu[s],
                                                  Lside[s], bp<int64_t>(*costs[s]));
   }

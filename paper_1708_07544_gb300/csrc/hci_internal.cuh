@@ -131,6 +131,7 @@ struct hci_ctx {
   DevBuf ss_w, ss_draw, ss_draw2, ss_run, ss_src;                 // sampled perturbative correction
   DevBuf g_ua, g_ga, g_ia, g_ub, g_gb, g_ib, g_permb, g_bkeys, g_bkeys2, g_nbr_ptr, g_nbr, g_cnt;
   DevBuf g_bnbr_ptr, g_bnbr, g_costa, g_costb, g_htab, g_hval, g_posb, g_vb, g_ba;
+  DevBuf g_nscr;   // padded neighbour lists of the one-pass look-up
   IncScratch inc;
   bool incremental = true;
   int sigma_mode = HCI_SIGMA_AUTO;
