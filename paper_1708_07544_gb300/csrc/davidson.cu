@@ -26,15 +26,21 @@ struct DavDev {
   double ols[4];          // |r|^2, x . M^-1 r, x . M^-1 x (Olsen correction)
   int amax_idx;
   int kq;                 // size of Qp (0: none)
+  unsigned int ticket;    // blocks of the running k_dots that have finished
 };
 
-// partial[b][j] = sum over this block's elements of V_j . w (j < k); the
-// vectors come in groups of DOTS_GROUP (blockIdx.y = group), which keeps the
-// accumulators few and the kernel at full occupancy for any k
+// out[j] = V_j . w (j < k).  Each block writes partial[b][j], its share of
+// the sums; the vectors come in groups of DOTS_GROUP (blockIdx.y = group),
+// which keeps the accumulators few and the kernel at full occupancy for any
+// k.  The last block to finish (a ticket counter) sums the partials in a
+// fixed order (lanes over blocks, then a shuffle tree), so the
+// result does not depend on the order in which blocks finish; with
+// gcol >= 0 it also stores out[j] as G[j][gcol] = G[gcol][j], j <= gcol.
 constexpr int DOTS_GROUP = 8;
 
 __global__ void __launch_bounds__(DBLOCK) k_dots(const double* __restrict__ V, int64_t ld, int k,
-                                                 const double* __restrict__ w, int64_t n, double* __restrict__ partial) {
+                                                 const double* __restrict__ w, int64_t n, double* __restrict__ partial,
+                                                 double* __restrict__ out, DavDev* __restrict__ gd, int gcol) {
   const int j0 = blockIdx.y * DOTS_GROUP;
   const int kg = k - j0 < DOTS_GROUP ? k - j0 : DOTS_GROUP;
   const double* Vg = V + (int64_t)j0 * ld;
@@ -48,6 +54,7 @@ __global__ void __launch_bounds__(DBLOCK) k_dots(const double* __restrict__ V, i
       if (j < kg) acc[j] = fma(Vg[(int64_t)j * ld + i], wv, acc[j]);
   }
   __shared__ double red[DBLOCK / 32][DOTS_GROUP];
+  __shared__ bool s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < DOTS_GROUP; ++j) {
@@ -63,25 +70,26 @@ __global__ void __launch_bounds__(DBLOCK) k_dots(const double* __restrict__ V, i
     for (int w2 = 0; w2 < DBLOCK / 32; ++w2) s += red[w2][threadIdx.x];
     partial[(int64_t)blockIdx.x * LDG + j0 + threadIdx.x] = s;
   }
-}
-
-// out[j] = sum_b partial[b][j] in a fixed order
-__global__ void k_reduce(const double* __restrict__ partial, int nblocks, int k, double* __restrict__ out) {
-  int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (j >= k) return;
-  double s = 0.0;
-  for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * LDG + j];
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[j] = s;
-}
-
-// G[j][col] = G[col][j] = dots[j], j <= col
-__global__ void k_set_gcol(DavDev* d, int col) {
-  int j = threadIdx.x;
-  if (j <= col) {
-    d->G[j * LDG + col] = d->dots[j];
-    d->G[col * LDG + j] = d->dots[j];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&gd->ticket, 1u) == gridDim.x * gridDim.y - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nblocks = (int)gridDim.x;
+  for (int j = wid; j < k; j += DBLOCK / 32) {
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += __ldcg(partial + (int64_t)b * LDG + j);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      out[j] = s;
+      if (gcol >= 0 && j <= gcol) {
+        gd->G[j * LDG + gcol] = s;
+        gd->G[gcol * LDG + j] = s;
+      }
+    }
   }
+  if (threadIdx.x == 0) gd->ticket = 0u;
 }
 
 // Lowest eigenpair of the k x k subspace matrix by parallel-order Jacobi on
@@ -228,11 +236,12 @@ __global__ void __launch_bounds__(JW * 32) k_jacobi(DavDev* d, int k) {
 // (guarded away from zero); partial[b][0..2] = block sums of r^2, x t and
 // x M^-1 x for the Olsen correction.
 __global__ void __launch_bounds__(DBLOCK) k_ritz(const double* __restrict__ V, const double* __restrict__ W, int64_t ld,
-                                                 int k, const DavDev* __restrict__ d, const double* __restrict__ diag,
+                                                 int k, DavDev* __restrict__ d, const double* __restrict__ diag,
                                                  int64_t n, double* __restrict__ x, double* __restrict__ wy,
                                                  double* __restrict__ t, double* __restrict__ partial) {
   __shared__ double ys[LDG];
   __shared__ double red[3][DBLOCK / 32];
+  __shared__ bool s_last;
   if (threadIdx.x < LDG) ys[threadIdx.x] = d->y[threadIdx.x];
   __syncthreads();
   const double theta = d->theta;
@@ -270,6 +279,21 @@ __global__ void __launch_bounds__(DBLOCK) k_ritz(const double* __restrict__ V, c
     for (int w = 0; w < DBLOCK / 32; ++w) s += red[threadIdx.x][w];
     partial[(int64_t)blockIdx.x * LDG + threadIdx.x] = s;
   }
+  // the last block to finish sums the partials into ols[0..2] (as k_dots)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&d->ticket, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < 3) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (int64_t)b * LDG + wid);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) d->ols[wid] = s;
+  }
+  if (threadIdx.x == 0) d->ticket = 0u;
 }
 
 // The kk <= DAV_KEEP lowest Ritz vectors of the current subspace (ascending Ritz value)
@@ -415,6 +439,12 @@ __global__ void k_scale_const(double* __restrict__ x, int64_t n, double f) {
     x[i] *= f;
 }
 
+// y = f x (the normalised correction into its subspace slot)
+__global__ void k_scale_into(const double* __restrict__ x, int64_t n, double f, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+
 // argmax |x| (first index on ties): block partials then a final reduce
 __global__ void k_amax_part(const double* __restrict__ x, int64_t n, double* __restrict__ pv, int64_t* __restrict__ pi) {
   double bv = -1.0;
@@ -483,10 +513,10 @@ struct Dav {
   DavDev* d;
   int nblk;
 
-  hci_status dots(const double* Vb, int k, const double* w, double* out) {
+  // out[j] = Vb_j . w, j < k; with gcol >= 0 also column gcol of G
+  hci_status dots(const double* Vb, int k, const double* w, double* out, int gcol = -1) {
     const dim3 grid((unsigned)nblk, (unsigned)((k + DOTS_GROUP - 1) / DOTS_GROUP));
-    HCI_LAUNCH(k_dots, grid, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part);
-    HCI_LAUNCH(k_reduce, 1, 32 * LDG, 0, ctx->st)(part, nblk, k, out);
+    HCI_LAUNCH(k_dots, grid, DBLOCK, 0, ctx->st)(Vb, ld, k, w, n, part, out, d, gcol);
     HCI_CUDA(ctx, cudaGetLastError());
     return HCI_OK;
   }
@@ -586,8 +616,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
       }
     }
     for (int j = 0; j < kwarm; ++j) {
-      HCI_TRY(D.dots(D.V, j + 1, D.W + (int64_t)j * D.ld, D.d->dots));
-      HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, j);
+      HCI_TRY(D.dots(D.V, j + 1, D.W + (int64_t)j * D.ld, D.d->dots, j));
     }
   }
   // start vector, in the graph's internal order (after the kept vectors)
@@ -658,8 +687,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   int k = kwarm;
   if (add_start) {
     HCI_TRY(D.sigma(k));
-    HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots));
-    HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, k);
+    HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots, k));
     ++k;
   }
   bool converged = false;
@@ -668,7 +696,6 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   for (; it < maxit; ++it) {
     HCI_LAUNCH(k_jacobi, 1, JW * 32, 0, st)(D.d, k);
     HCI_LAUNCH(k_ritz, D.nblk, DBLOCK, 0, st)(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
-    HCI_LAUNCH(k_reduce, 1, 32 * 3, 0, st)(D.part, D.nblk, 3, D.d->ols);
     HCI_CUDA(ctx, cudaGetLastError());
     double hv[2];
     HCI_CUDA(ctx, cudaMemcpyAsync(&hv[0], &D.d->theta, 8, cudaMemcpyDeviceToHost, st));
@@ -688,8 +715,7 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
       HCI_CUDA(ctx, cudaMemcpyAsync(D.W, D.wy, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
       HCI_TRY(D.dots(D.V, 1, D.V, &D.d->nrm2));
       HCI_LAUNCH(k_scale_by, D.nblk, DBLOCK, 0, st)(D.V, D.W, nV, &D.d->nrm2);
-      HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots));
-      HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, 0);
+      HCI_TRY(D.dots(D.V, 1, D.W, D.d->dots, 0));
       k = 1;
     }
     HCI_LAUNCH(k_olsen, D.nblk, DBLOCK, 0, st)(D.d, diag, nV, D.x, D.t);
@@ -711,11 +737,9 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
       break;
     }
     double* slot = D.V + (int64_t)k * D.ld;
-    HCI_LAUNCH(k_scale_const, D.nblk, DBLOCK, 0, st)(D.t, nV, 1.0 / std::sqrt(nrm2));
-    HCI_CUDA(ctx, cudaMemcpyAsync(slot, D.t, (size_t)nV * 8, cudaMemcpyDeviceToDevice, st));
+    HCI_LAUNCH(k_scale_into, D.nblk, DBLOCK, 0, st)(D.t, nV, 1.0 / std::sqrt(nrm2), slot);
     HCI_TRY(D.sigma(k));
-    HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots));
-    HCI_LAUNCH(k_set_gcol, 1, 32, 0, st)(D.d, k);
+    HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots, k));
     ++k;
   }
   if (iters) *iters = it + (converged ? 1 : 0);
