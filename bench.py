@@ -25,6 +25,11 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The batched solve runs one stream per in-flight instance (16 at the
+# autotuned setting); with the default 8 hardware work queues pairs of
+# streams share one and their kernels wait on each other.  Read when the
+# process creates its CUDA context, so it is set before torch touches CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
