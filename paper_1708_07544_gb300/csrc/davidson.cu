@@ -27,6 +27,7 @@ struct DavDev {
   int amax_idx;
   int kq;                 // size of Qp (0: none)
   unsigned int ticket;    // blocks of the running k_dots that have finished
+  int stall;              // a correction fell inside the subspace (k_scale_unit)
 };
 
 // out[j] = V_j . w (j < k).  Each block writes partial[b][j], its share of
@@ -439,10 +440,16 @@ __global__ void k_scale_const(double* __restrict__ x, int64_t n, double f) {
     x[i] *= f;
 }
 
-// y = f x (the normalised correction into its subspace slot)
-__global__ void k_scale_into(const double* __restrict__ x, int64_t n, double f, double* __restrict__ y) {
+// y = x / sqrt(|x|^2) with |x|^2 = d->nrm2 read on the device (the
+// normalised correction into its subspace slot); a correction of norm^2 at
+// most 1e-26 lies in the subspace: y = 0 and d->stall = 1
+__global__ void k_scale_unit(const double* __restrict__ x, int64_t n, DavDev* __restrict__ d, double* __restrict__ y) {
+  const double nrm2 = d->nrm2;
+  const bool ok = nrm2 > 1e-26;
+  const double f = ok ? 1.0 / sqrt(nrm2) : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = x[i] * f;
+    y[i] = ok ? x[i] * f : 0.0;
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) d->stall = 1;
 }
 
 // argmax |x| (first index on ties): block partials then a final reduce
@@ -693,16 +700,34 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
   bool converged = false;
   double theta = 0.0, rn = 0.0;
   int it = 0;
-  for (; it < maxit; ++it) {
+  // one host synchronisation per iteration: the Ritz value, the residual
+  // and whether the previous correction fell inside the subspace
+  auto ritz = [&](double& th, double& r, int& stall) -> hci_status {
     HCI_LAUNCH(k_jacobi, 1, JW * 32, 0, st)(D.d, k);
     HCI_LAUNCH(k_ritz, D.nblk, DBLOCK, 0, st)(D.V, D.W, D.ld, k, D.d, diag, nV, D.x, D.wy, D.t, D.part);
     HCI_CUDA(ctx, cudaGetLastError());
     double hv[2];
     HCI_CUDA(ctx, cudaMemcpyAsync(&hv[0], &D.d->theta, 8, cudaMemcpyDeviceToHost, st));
     HCI_CUDA(ctx, cudaMemcpyAsync(&hv[1], &D.d->ols[0], 8, cudaMemcpyDeviceToHost, st));
+    HCI_CUDA(ctx, cudaMemcpyAsync(&stall, &D.d->stall, 4, cudaMemcpyDeviceToHost, st));
     HCI_CUDA(ctx, cudaStreamSynchronize(st));
-    theta = hv[0];
-    rn = std::sqrt(hv[1]);
+    th = hv[0];
+    r = std::sqrt(hv[1]);
+    return HCI_OK;
+  };
+  for (; it < maxit; ++it) {
+    int stall = 0;
+    HCI_TRY(ritz(theta, rn, stall));
+    if (stall) {
+      // the last correction lay in the subspace (it was added as zeros):
+      // drop it, take the Ritz pair of the subspace before it and stop
+      --k;
+      HCI_TRY(ritz(theta, rn, stall));
+      if (!std::isfinite(theta) || !std::isfinite(rn))
+        return hci_fail(ctx, HCI_ERR_CUDA, "hci_davidson: non-finite Ritz value or residual");
+      converged = rn <= tol;
+      break;
+    }
     if (!std::isfinite(theta) || !std::isfinite(rn))
       return hci_fail(ctx, HCI_ERR_CUDA, "hci_davidson: non-finite Ritz value or residual");
     if (rn <= tol) {
@@ -730,14 +755,8 @@ static hci_status davidson_core(hci_ctx* ctx, const uint64_t* keys, int64_t nV, 
       }
     }
     HCI_TRY(D.dots(D.t, 1, D.t, &D.d->nrm2));
-    HCI_CUDA(ctx, cudaMemcpyAsync(&nrm2, &D.d->nrm2, 8, cudaMemcpyDeviceToHost, st));
-    HCI_CUDA(ctx, cudaStreamSynchronize(st));
-    if (!(nrm2 > 1e-26)) {
-      // the correction lies in the subspace: no further progress possible
-      break;
-    }
     double* slot = D.V + (int64_t)k * D.ld;
-    HCI_LAUNCH(k_scale_into, D.nblk, DBLOCK, 0, st)(D.t, nV, 1.0 / std::sqrt(nrm2), slot);
+    HCI_LAUNCH(k_scale_unit, D.nblk, DBLOCK, 0, st)(D.t, nV, D.d, slot);
     HCI_TRY(D.sigma(k));
     HCI_TRY(D.dots(D.V, k + 1, D.W + (int64_t)k * D.ld, D.d->dots, k));
     ++k;
