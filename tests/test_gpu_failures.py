@@ -9,7 +9,9 @@ trap or hang is ever caused):
   unrestricted run;
 * Davidson and the z-vector solve stopped at their iteration limit return
   HCI_ERR_NOT_CONVERGED with the last iterate (a normalised vector whose
-  Rayleigh quotient lies above the converged energy);
+  Rayleigh quotient lies above the converged energy); Davidson also stops,
+  with the exact pair, when its correction falls inside an exhausted
+  subspace;
 * checkpoint and resume of the selection loop (Sec. II.A: V^{mu+1} depends
   only on V^mu and c^mu): a state saved to host memory at some mu and
   resumed in a fresh context reaches the uninterrupted solve's space and
@@ -158,6 +160,29 @@ def test_davidson_stopped_at_its_limit(pkg, inst):
         with pytest.raises(pkg.HCIError) as ez:
             s.zvector(keys, c, E, rhs, tol=1e-13, maxit=1)
         assert ez.value.status == pkg._abi.HCI_ERR_NOT_CONVERGED
+
+
+def test_davidson_stops_when_the_subspace_is_exhausted(pkg, inst):
+    """With tol = 0 the residual test never succeeds; once the subspace
+    spans the whole (small) space the next correction lies inside it and
+    Davidson stops there (not at maxit) with the exact lowest eigenpair,
+    reported as HCI_ERR_NOT_CONVERGED."""
+    import oracle
+
+    keys = hi.random_det_keys(inst.norb, inst.nalpha, inst.nbeta, 12, seed=77)
+    want = np.linalg.eigvalsh(oracle.hamiltonian(inst, keys).toarray())[0]
+    kd = torch.from_numpy(np.ascontiguousarray(keys).view(np.int64).reshape(-1, 2)).cuda()
+    with _solver(pkg, inst) as s:
+        with pytest.raises(pkg.HCIError) as ei:
+            s.davidson(kd, None, tol=0.0, maxit=100)
+        assert ei.value.status == pkg._abi.HCI_ERR_NOT_CONVERGED
+        e, c, it = s.davidson(kd, None, tol=0.0, maxit=100, allow_unconverged=True)
+    assert it < 100
+    assert abs(e - want) < 1e-12
+    H = oracle.hamiltonian(inst, keys)
+    c = c.cpu().numpy()
+    assert abs(np.linalg.norm(c) - 1.0) < 1e-12
+    assert np.abs(H @ c - want * c).max() < 1e-10
 
 
 @pytest.mark.parametrize("stop", [1, 3])
