@@ -344,10 +344,11 @@ hci_status hci_rotate(int norb, const double* kappa, const double* h, const doub
  * i.e. the summed index a leaves the front and p joins at the back (four
  * calls with M = U give (pq|rs)').  in and out are n^4 doubles, M is n*n,
  * all device pointers; in and out must not overlap.  Computed on the bf16
- * tensor cores as exact products of 7-bit digits of each row of in and each
- * column of M (scaled by their largest binary exponents), summed exactly
- * and rounded once to FP64: the error is at most about 2^-55 (2^-52 for
- * n > 48) of max_a |in[a][J]| * max_a |M[a][p]|.  Stream-ordered; with
+ * tensor cores as exact products of the balanced base-256 digits of each
+ * row of in and each column of M (in fixed point against their largest
+ * binary exponents), summed exactly and rounded once to FP64: the error is
+ * at most about n 2^-55 of max_a |in[a][J]| * max_a |M[a][p]| (subnormal
+ * entries count as zero).  Stream-ordered; with
  * check != 0 the call synchronises the stream and returns HCI_ERR_CUDA if
  * the launch gave up waiting for its products (never expected), which the
  * rotation entry points check after every call anyway. */
