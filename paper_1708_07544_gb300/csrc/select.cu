@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
     __syncwarp();
     for (int base = 0; base < P; base += 32) {
       int t = base + lane;
-      bool emit = false;
+      bool emit = false, exact = false;
       ulonglong2 key = k;
       double term = 0.0, elem = 0.0;
       if (t < P) {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
           }
         } else if (A.accept_all || (s_bound[p * n + r] * absc > A.eps1 &&
                                     single_tight(A, spin, p, r, s, o, s_bound[p * n + r]) * absc > A.eps1)) {
-          atomicAdd(&A.walkstat[1], 1ull);
+          exact = true;
           double v = A.h[p * n + r];
           const double* js = A.jk_same + ((int64_t)p * n + r) * n;
           const double* jo = A.j_opp + ((int64_t)p * n + r) * n;
@@ -384,6 +384,9 @@ __global__ void __launch_bounds__(SEL_WARPS * 32) k_singles(WalkArgs A) {
           if (A.vals) emit = pt_keep(A, key, term);
         }
       }
+      // exact evaluations counted once per warp (one atomic, not 32)
+      const unsigned mex = __ballot_sync(0xffffffffu, exact);
+      if (lane == 0 && mex) atomicAdd(&A.walkstat[1], (unsigned long long)__popc(mex));
       warp_emit(emit, key, A.srcs ? elem : term, (int)i, A);
     }
   }
