@@ -27,8 +27,9 @@
 //  * levels 2..9 are kept (8 blocks, at most 512 columns); the pairs of
 //    the higher levels weigh at most about 2^-64 of the largest term;
 //  * the epilogue reads the level sums, combines them exactly in 64-bit
-//    integers (an 80-bit sum in two words) and rounds once to FP64 (round to nearest even), scaled by
-//    2^(E_J + E_p); results below the FP64 normal range are returned as 0.
+//    integers (an 80-bit sum in two words) and rounds once to FP64 (to
+//    nearest, ties to even), scaled by 2^(E_J + E_p); results below the
+//    FP64 normal range are returned as 0.
 //
 // The error against the exact sum is thus about 2^-55 n of
 // max_a |in[a][J]| * max_a |M[a][p]| at worst (the digit truncation), of
@@ -42,9 +43,9 @@
 // partial maxima), and each thread's entries of the next tile are loaded
 // while the tensor cores work on this one; in the epilogue warp w reads
 // tensor-memory lanes 32 (w mod 4) .. + 31 (the rows of the M = 128
-// accumulator) and every fourth group of 4 columns.  The digits sit in shared memory in the canonical
-// K-major layout without swizzle (8 x 16-byte core matrices); U's digits
-// are made once per CTA.  The output tile (128 x n doubles, contiguous in
+// accumulator) and every fourth group of 4 columns.  The digits sit in
+// shared memory in the canonical K-major layout without swizzle (8 x
+// 16-byte core matrices); U's digits are made once per CTA.  The output tile (128 x n doubles, contiguous in
 // global memory) is staged in shared memory and written coalesced.
 #include <cuda.h>
 
